@@ -1,0 +1,262 @@
+"""Pins for the oracle's eigSVD (Alg. 3) and dashSVD (Alg. 4 / Alg. 5).
+
+Nothing here compares the oracle with itself: each test checks it against a
+closed form, a different LAPACK routine (gesdd via numpy.linalg.svd, QR), brute
+force, or an inequality the paper proves (Prop. 1-3, Theorem 1, its Corollary).
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import datagen
+import oracle
+from oracle import metrics
+from oracle.dashsvd_ref import dashsvd, eigsvd
+
+
+def _sparse(m, n, density, seed):
+    rng = np.random.default_rng(seed)
+    A = sp.random(m, n, density=density, random_state=rng, data_rvs=rng.standard_normal, format="csr")
+    return A
+
+
+def _abs_col_cos(X, Y):
+    Xn = X / np.linalg.norm(X, axis=0)
+    Yn = Y / np.linalg.norm(Y, axis=0)
+    return np.abs(np.einsum("ij,ij->j", Xn, Yn))
+
+
+# ----------------------------------------------------------------- eigSVD
+
+
+def test_eigsvd_orthogonal_columns_closed_form():
+    C = np.zeros((5, 3))
+    C[0, 1] = 3.0
+    C[2, 0] = -2.0
+    C[4, 2] = 0.5
+    U, S, V, null = eigsvd(C)
+    np.testing.assert_allclose(S, [3.0, 2.0, 0.5], rtol=1e-15)
+    assert not null.any()
+    np.testing.assert_allclose(U @ np.diag(S) @ V.T, C, atol=1e-14)
+    # sign rule: largest |entry| of every V column is positive
+    assert np.all(V[np.argmax(np.abs(V), axis=0), range(3)] > 0)
+
+
+def test_eigsvd_matches_gesdd():
+    rng = np.random.default_rng(1)
+    C = rng.standard_normal((300, 40)) @ np.diag(np.logspace(0, -3, 40))
+    U, S, V, null = eigsvd(C)
+    Ur, Sr, Vtr = np.linalg.svd(C, full_matrices=False)
+    np.testing.assert_allclose(S, Sr, rtol=1e-9)
+    assert np.all(np.diff(S) <= 0)
+    assert np.min(_abs_col_cos(U, Ur)) > 1 - 1e-6
+    assert np.min(_abs_col_cos(V, Vtr.T)) > 1 - 1e-9
+    np.testing.assert_allclose(U.T @ U, np.eye(40), atol=1e-6)
+    np.testing.assert_allclose((U * S) @ V.T, C, atol=1e-12)
+
+
+def test_eigsvd_rank_deficient_null_columns():
+    rng = np.random.default_rng(2)
+    C = rng.standard_normal((100, 5)) @ rng.standard_normal((5, 12))
+    U, S, V, null = eigsvd(C)
+    assert null.sum() == 7 and not null[:5].any()
+    assert np.all(U[:, null] == 0)
+    np.testing.assert_allclose(U[:, ~null].T @ U[:, ~null], np.eye(5), atol=1e-10)
+    np.testing.assert_allclose(S[:5], np.linalg.svd(C, compute_uv=False)[:5], rtol=1e-11)
+
+
+# ----------------------------------------------------------------- dashSVD
+
+
+def test_full_width_subspace_gives_exact_svd():
+    """l = n: Q spans R^n after the first eigSVD, so the result is the exact SVD."""
+    A = _sparse(90, 14, 0.3, 3)
+    k, s = 9, 5
+    r = dashsvd(A, k, s, p_max=2, tol=0.0, seed=11)
+    Ur, Sr, Vtr = np.linalg.svd(A.toarray(), full_matrices=False)
+    np.testing.assert_allclose(r.S, Sr[:k], rtol=1e-12)
+    assert np.min(_abs_col_cos(r.U, Ur[:, :k])) > 1 - 1e-10
+    assert np.min(_abs_col_cos(r.V, Vtr[:k].T)) > 1 - 1e-10
+
+
+def test_wide_input_runs_on_transpose():
+    A = _sparse(14, 90, 0.3, 4)
+    k, s = 9, 5
+    r = dashsvd(A, k, s, p_max=1, tol=0.0, seed=12)
+    assert r.transposed and r.U.shape == (14, k) and r.V.shape == (90, k)
+    Ur, Sr, Vtr = np.linalg.svd(A.toarray(), full_matrices=False)
+    np.testing.assert_allclose(r.S, Sr[:k], rtol=1e-12)
+    assert np.min(_abs_col_cos(r.U, Ur[:, :k])) > 1 - 1e-10
+    assert np.min(_abs_col_cos(r.V, Vtr[:k].T)) > 1 - 1e-10
+
+
+def test_exact_low_rank_recovery_without_power_iteration():
+    rng = np.random.default_rng(5)
+    r_true = 5
+    A = rng.standard_normal((400, r_true)) @ rng.standard_normal((r_true, 150))
+    res = dashsvd(A, k=6, s=3, p_max=0, tol=0.0, seed=13)
+    sv = np.linalg.svd(A, compute_uv=False)
+    np.testing.assert_allclose(res.S[:r_true], sv[:r_true], rtol=1e-10)
+    assert res.S[r_true] < 1e-6 * sv[0]
+    Ur, _, Vtr = np.linalg.svd(A, full_matrices=False)
+    assert np.max(metrics.principal_angles(res.U[:, :r_true], Ur[:, :r_true])) < 1e-7
+    assert np.max(metrics.principal_angles(res.V[:, :r_true], Vtr[:r_true].T)) < 1e-7
+
+
+def test_singular_values_never_exceed_true_prop2():
+    A = _sparse(500, 200, 0.05, 6)
+    sv = np.linalg.svd(A.toarray(), compute_uv=False)
+    for p in range(5):
+        r = dashsvd(A, 20, 10, p_max=p, tol=0.0, seed=14)
+        assert np.all(r.S <= sv[:20] * (1 + 1e-12))
+
+
+def test_per_pass_invariants_prop1_prop3():
+    """Every pass: 0 <= alpha <= sigma_l(A)^2 / 2, alpha non-decreasing (Prop. 1, step 6)
+    and sigma_i(A Q_in) <= sqrt(Shat_i + alpha) <= sigma_i(A) (Prop. 3)."""
+    A = _sparse(600, 250, 0.04, 7)
+    k, s = 15, 10
+    l = k + s
+    sv = np.linalg.svd(A.toarray(), compute_uv=False)
+    r = dashsvd(A, k, s, p_max=8, tol=0.0, seed=15, keep_q=True)
+    assert len(r.trace) == 8
+    prev = 0.0
+    for rec in r.trace:
+        assert 0.0 <= rec.alpha_used <= sv[l - 1] ** 2 / 2 * (1 + 1e-12)
+        assert rec.alpha_next >= rec.alpha_used
+        assert rec.alpha_used >= prev
+        prev = rec.alpha_used
+        surrogate = np.sqrt(rec.S + rec.alpha_used)
+        lower = np.linalg.svd(A @ rec.Q_in, compute_uv=False)
+        assert np.all(lower <= surrogate * (1 + 1e-10))
+        assert np.all(surrogate <= sv[:l] * (1 + 1e-10))
+    assert r.trace[0].alpha_used == 0.0 and r.trace[1].alpha_used > 0.0
+
+
+def test_pve_stop_closed_form_full_width():
+    """With l = n every surrogate is exact (Shat_i + alpha = sigma_i^2), so under
+    reading R1 the test sees a zero change at j = 2 and stops there; taking
+    step 7 literally mixes in the shift change and cannot stop at j = 2."""
+    A = _sparse(120, 16, 0.3, 8)
+    r0 = dashsvd(A, 10, 6, p_max=10, tol=1e-6, seed=16, alpha_prev_mode=0)
+    assert r0.converged and r0.passes == 2
+    sv = np.linalg.svd(A.toarray(), compute_uv=False)
+    np.testing.assert_allclose(r0.trace[0].S + r0.trace[0].alpha_used, sv**2, rtol=1e-10)
+    r1 = dashsvd(A, 10, 6, p_max=10, tol=1e-6, seed=16, alpha_prev_mode=1)
+    assert r1.passes >= 3
+
+
+def test_first_pass_never_stops_and_tol_monotone():
+    A = _sparse(800, 300, 0.03, 9)
+    passes = []
+    for tol in [0.5, 1e-1, 1e-2, 1e-3, 1e-5]:
+        r = dashsvd(A, 20, 10, p_max=30, tol=tol, seed=17)
+        assert r.passes >= 2
+        passes.append(r.passes)
+    assert passes == sorted(passes)
+    assert passes[-1] > passes[0]
+
+
+def test_unshifted_mode_is_basic_power_iteration():
+    """alpha = 0 gives span(Q) = span((A^T A)^p A^T Omega) (Alg. 1, m >= n form);
+    the reference subspace is built here with QR instead of eigSVD."""
+    A = _sparse(300, 120, 0.05, 10).toarray()
+    k, s, p = 8, 4, 3
+    l = k + s
+    r = dashsvd(A, k, s, p_max=p, tol=0.0, seed=18, shift=False)
+    Om = oracle.gaussian_block(18, 300, l)
+    Q, _ = np.linalg.qr(A.T @ Om)
+    for _ in range(p):
+        Q, _ = np.linalg.qr(A.T @ (A @ Q))
+    assert np.max(metrics.principal_angles(r.Q, Q)) < 1e-7
+    r_shift = dashsvd(A, k, s, p_max=p, tol=0.0, seed=18)
+    assert np.max(metrics.principal_angles(r_shift.Q, Q)) > 1e-6
+
+
+def _theorem_case(seed, n=60, k=6, s=4, p=3):
+    sigma = 1.0 / np.sqrt(np.arange(1, n + 1))
+    A = datagen.dense_with_spectrum(n, n, sigma, seed)
+    r = dashsvd(A, k, s, p_max=p, tol=0.0, seed=seed + 100)
+    return A, sigma, r
+
+
+def test_theorem1_bound_holds():
+    """Theorem 1: ||A Q Q^T - A|| <= RHS with probability >= 1 - phi (here phi < 1e-3)."""
+    n, k, s, p, j = 60, 6, 4, 3, 3
+    l = k + s
+    beta, gamma = 3.0, 2.5
+    ph = metrics.phi(l, j, n, k, beta, gamma)
+    assert ph < 1e-3
+    held = 0
+    for seed in range(50):
+        A, sigma, r = _theorem_case(seed, n, k, s, p)
+        alphas = [rec.alpha_used for rec in r.trace]
+        rhs = metrics.theorem1_rhs(sigma, alphas, l, j, n, k, beta, gamma)
+        err = np.linalg.norm(A @ r.Q @ r.Q.T - A, 2)
+        held += err <= rhs
+        # Corollary: the shifted bound never exceeds the unshifted one (strictly
+        # smaller here because sigma_j > sigma_{k+1} and some alpha_c > 0)
+        assert rhs < metrics.lemma6_rhs(sigma, p, l, j, n, k, beta, gamma)
+    assert held >= 45
+
+
+def test_shift_not_worse_statistically():
+    """At equal p, the shifted run's eps_PVE is not worse than the unshifted one's
+    (the paper shows this on Dense1/Dense2 and six datasets, Fig. 1); checked as
+    a statistical property on 40 seeded cases per family."""
+    fams = {
+        "dense1": lambda sd: np.random.default_rng(sd).standard_normal((200, 200)),
+        "dense2": lambda sd: datagen.dense_with_spectrum(200, 200, 1 / np.sqrt(np.arange(1, 201)), sd),
+    }
+    k, s, p = 10, 5, 2
+    for name, mk in fams.items():
+        ok = 0
+        gains = []
+        for sd in range(40):
+            A = mk(sd)
+            sv = np.linalg.svd(A, compute_uv=False)
+            a = dashsvd(A, k, s, p_max=p, tol=0.0, seed=sd)
+            b = dashsvd(A, k, s, p_max=p, tol=0.0, seed=sd, shift=False)
+            ea = metrics.eps_pve(A, a.U, sv, k)
+            eb = metrics.eps_pve(A, b.U, sv, k)
+            ok += ea <= 1.05 * eb
+            gains.append(eb / ea)
+        assert ok >= 38, (name, ok)
+        assert np.median(gains) > 1.0, name
+
+
+def test_config1_shape_runs_and_meets_tolerance():
+    """The small workload (20000 x 10000 recipe at 1/10 scale): the run stops
+    by the PVE test and the true eps_PVE is of the order of the tolerance."""
+    A, prm = datagen.make_config(1, scale=0.1)
+    As = A.to_scipy()
+    r = dashsvd(As, prm["k"], prm["s"], p_max=prm["p_max"], tol=prm["tol"], seed=0x5EED)
+    assert r.converged and 2 <= r.passes <= prm["p_max"]
+    sv = np.linalg.svd(As.toarray(), compute_uv=False)
+    assert metrics.eps_pve(As, r.U, sv, prm["k"]) < 10 * prm["tol"]
+    assert metrics.eps_sigma(r.S, sv, prm["k"]) < 0.1
+
+
+# ------------------------------------------------------ planted mistakes
+
+
+def _mutant_no_sqrt(C, eps=oracle.EPS64):
+    U, S, V, null = eigsvd(C, eps)
+    return U, S**2, V, null
+
+
+def _mutant_ascending(C, eps=oracle.EPS64):
+    U, S, V, null = eigsvd(C, eps)
+    return U[:, ::-1], S[::-1], V[:, ::-1], null[::-1]
+
+
+@pytest.mark.parametrize("mutant", [_mutant_no_sqrt, _mutant_ascending])
+def test_pins_catch_planted_mistakes(monkeypatch, mutant):
+    """Plant a mistake in the oracle's eigSVD and check that a pin fails."""
+    import oracle.dashsvd_ref as ref
+
+    A = _sparse(90, 14, 0.3, 3)
+    Ur, Sr, Vtr = np.linalg.svd(A.toarray(), full_matrices=False)
+    monkeypatch.setattr(ref, "eigsvd", mutant)
+    r = ref.dashsvd(A, 9, 5, p_max=2, tol=0.0, seed=11)
+    assert not np.allclose(r.S, Sr[:9], rtol=1e-6)
