@@ -1,0 +1,398 @@
+#!/usr/bin/env python3
+"""Benchmark of the dashSVD hot path on GB300.
+
+Workload (one "step"): one full dashSVD run (Alg. 5: Gaussian block, A^T Omega,
+eigSVD, PVE-controlled shifted power iterations, final eigSVD of B = A Q) on
+the social-graph-shaped matrix: 1,000,000 x 1,000,000 binary CSR, power-law
+out-degrees (mean 15, max 50,000), Zipf(1.1) target popularity, 15.0M nnz;
+k = 100, s = 50, p_max = 20, PVE tol = 1e-2. Synthetic, seeded (datagen).
+
+Metric: seconds to reach the PVE tolerance (lower is better). `value` is the
+device time of one dashsvd_run with A resident in HBM (CUDA events on the
+launching stream, L2 flushed before each step); `e2e` is the same call with A
+copied from pinned host memory and U, S, V copied back inside the timed
+region. Per-kernel times for the roofline come from the step-level entry
+points on the same matrix, timed with CUDA events over repeated launches.
+
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+Multi-GPU: the path does not shard across GPUs here (replicas only): each rank
+solves its own copy and `value` is the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "s to PVE<=1e-2, k=100: chosen vs plain GPU form; SpMM GB/s vs HBM peak"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
+NUM_SMS_GB300 = 152
+FP32_LANES_PER_SM = 128
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        d["source"] = "measured"
+        return d
+    d = dict(PEAKS_FALLBACK)
+    d["source"] = "fallback"
+    return d
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (testing only)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-reps", type=int, default=20)
+    return ap.parse_args()
+
+
+def _workload(cfg: int, scale: float):
+    import datagen
+
+    A, prm = datagen.make_config(cfg, scale=scale)
+    desc = {
+        2: "social-graph CSR 1Mx1M binary, power-law out-degree mean 15 (max 50k), Zipf(1.1) targets",
+        3: "term-document CSR 500kx100k, lognormal row lengths mean 100, Zipf(1.1) columns",
+        1: "scaled-gaussian CSR 20000x10000, 20 nnz/row",
+        5: "recommender CSR 2Mx200k, power-law degrees mean 50, Zipf(1.2) items",
+    }[cfg]
+    name = f"{desc}; nnz={A.nnz}; k={prm['k']} s={prm['s']} p_max={prm['p_max']} tol={prm['tol']}"
+    if scale != 1.0:
+        name += f"; scaled x{scale}"
+    return A, prm, name
+
+
+def _save_npz(A) -> str:
+    import numpy as np
+
+    fd, path = tempfile.mkstemp(suffix=".npz")
+    os.close(fd)
+    np.savez(path, m=A.m, n=A.n, rowptr=A.rowptr, colidx=A.colidx, val=A.val)
+    return path
+
+
+def _oracle_leg(npz: str, k: int, s: int, reps: int, full=None, timeout=900):
+    cmd = [sys.executable, "-m", "oracle.timing", npz, str(k), str(s), str(reps)]
+    if full:
+        cmd += ["--full-run", *map(str, full)]
+    env = dict(os.environ)
+    ncpu = str(os.cpu_count() or 1)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = ncpu
+    r = subprocess.run(cmd, capture_output=True, text=True, cwd=ROOT, env=env, timeout=timeout)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# --------------------------------------------------------------- reference arm
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    A, prm, name = _workload(args.config, args.scale)
+    npz = _save_npz(A)
+    # pass count of a PVE-controlled oracle run on the same recipe at 1/10 scale
+    As, _, _ = _workload(args.config, args.scale * 0.1)
+    npz_small = _save_npz(As)
+    try:
+        small = _oracle_leg(npz_small, prm["k"], prm["s"], 1, full=(prm["p_max"], prm["tol"], 0x5EED))
+        passes = int(small["passes"])
+        leg = _oracle_leg(npz, prm["k"], prm["s"], args.warmup + args.steps)
+    finally:
+        os.unlink(npz)
+        os.unlink(npz_small)
+    t = leg["t_pass"][args.warmup:]
+    t_pass = statistics.median(t)
+    value = t_pass * (passes + 2)
+    sample = (f"per step one full-size power-iteration pass (2 sparse products + eigSVD, FP64 oracle); "
+              f"value = median pass time x (passes + 2) with passes = {passes} from the oracle's own "
+              f"PVE-controlled run on the same recipe at 1/10 scale")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_pass * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": name, "form": "FP64 CPU oracle"},
+        "cpu_baseline": {"value": value, "unit": "s", "cores": leg["threads"], "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------- our arm
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx.append(float(p[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, p[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _time_kernel(fn, reps, stream):
+    import torch
+
+    fn()
+    torch.cuda.synchronize()
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    s.record(stream)
+    for _ in range(reps):
+        fn()
+    e.record(stream)
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / 1e3 / reps
+
+
+def ours(args):
+    import numpy as np
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    A, prm, name = _workload(args.config, args.scale)
+    k, s, p_max, tol = prm["k"], prm["s"], prm["p_max"], prm["tol"]
+    l = k + s
+
+    # CPU baseline first (separate process, before this process touches CUDA)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        npz = _save_npz(A)
+        try:
+            cpu = _oracle_leg(npz, k, s, 2)
+        finally:
+            os.unlink(npz)
+
+    import torch
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    import paper_2404_09276_gb300 as ds
+
+    stream = torch.cuda.current_stream()
+    Ad = ds.CsrDevice.from_host(A)
+    U = torch.empty((A.m, k), dtype=torch.float32, device="cuda")
+    S = torch.empty((k,), dtype=torch.float32, device="cuda")
+    V = torch.empty((A.n, k), dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
+    h = ds.Handle(stream=stream)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    infos = []
+    for _ in range(args.warmup):
+        infos.append(h.run(Ad, k, s, p_max, tol, U, S, V)[3])
+    barrier()
+    clocks = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        infos.append(h.run(Ad, k, s, p_max, tol, U, S, V)[3])
+        ev[i][1].record(stream)
+    barrier()
+    clk = clocks.stop()
+    times = [a.elapsed_time(b) / 1e3 for a, b in ev]
+    t_step = sum(times) / len(times)
+    if world > 1:
+        t = torch.tensor([t_step], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_step = float(t.item())
+    info = infos[-1]
+    passes = info.passes
+    var_fwd, var_bwd = info.spmm_variant & 0xFF, (info.spmm_variant >> 8) & 0xFF
+    kpv = lambda v: 2 if v == 1 else 1  # noqa: E731  kernels per SpMM launch (merge path adds its fix-up)
+    launches_per_run = 5 + (1 + kpv(var_bwd) + 2 + 1 + 1) + passes * (kpv(var_fwd) + kpv(var_bwd) + 2 + 1 + 1) + \
+        (kpv(var_fwd) + 2 + 1 + 2)
+
+    # ---- end to end: A from pinned host memory, U, S, V back to pinned host memory
+    rp_h = torch.from_numpy(A.rowptr).pin_memory()
+    ci_h = torch.from_numpy(A.colidx).pin_memory()
+    va_h = torch.from_numpy(A.val).pin_memory()
+    U_h = torch.empty((A.m, k), dtype=torch.float32).pin_memory()
+    S_h = torch.empty((k,), dtype=torch.float32).pin_memory()
+    V_h = torch.empty((A.n, k), dtype=torch.float32).pin_memory()
+    Ae = ds.CsrDevice(A.m, A.n, torch.empty_like(Ad.rowptr), torch.empty_like(Ad.colidx), torch.empty_like(Ad.val))
+
+    def e2e_step():
+        Ae.rowptr.copy_(rp_h, non_blocking=True)
+        Ae.colidx.copy_(ci_h, non_blocking=True)
+        Ae.val.copy_(va_h, non_blocking=True)
+        h.run(Ae, k, s, p_max, tol, U, S, V)
+        U_h.copy_(U, non_blocking=True)
+        S_h.copy_(S, non_blocking=True)
+        V_h.copy_(V, non_blocking=True)
+
+    e2e_step()
+    barrier()
+    e2e_times = []
+    for i in range(max(1, min(args.steps, 3))):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_step()
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    h2d = A.rowptr.nbytes + A.colidx.nbytes + A.val.nbytes
+    d2h = (A.m * k + k + A.n * k) * 4
+
+    # ---- per-kernel times through the step-level entry points (same matrix, same shapes)
+    ld = ds.ld_for(l)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    Q = torch.randn((A.n, ld), device="cuda", generator=g)
+    Q[:, l:] = 0
+    Y = torch.empty((A.m, ld), device="cuda")
+    Z = torch.empty((A.n, ld), device="cuda")
+    W = torch.randn((l, ld), device="cuda", generator=g)
+    alpha = torch.tensor([0.5], dtype=torch.float64, device="cuda")
+    At = h.csr_transpose(Ad)
+    reps = args.kernel_reps
+    kt = {
+        "spmm_fwd": _time_kernel(lambda: h.spmm(Ad, Q, l, out=Y, variant=var_fwd), reps, stream),
+        "spmm_bwd": _time_kernel(lambda: h.spmm_shift(At, Y, l, alpha, Q, out=Z, variant=var_bwd), reps, stream),
+        "gram": _time_kernel(lambda: h.gram(Z, l), reps, stream),
+        "project": _time_kernel(lambda: h.project(Z, l, W, l, out=Q, ldo=ld), reps, stream),
+    }
+    t_eigsvd = _time_kernel(lambda: h.eigsvd(Z, l), max(3, reps // 4), stream)
+    kt["eig"] = max(0.0, t_eigsvd - kt["gram"] - kt["project"])
+    csr_bytes = 4 * (A.m + 1) + 8 * A.nnz
+    bytes_fwd = csr_bytes + 4 * A.n * l + 4 * A.m * ld
+    bytes_bwd = csr_bytes + 4 * A.m * l + 4 * A.n * l + 4 * A.n * ld
+    per_run = {
+        "spmm_fwd": (passes + 1) * kt["spmm_fwd"],
+        "spmm_bwd": (passes + 1) * kt["spmm_bwd"],
+        "gram": (passes + 2) * kt["gram"],
+        "project": (passes + 3) * kt["project"],
+        "eig": (passes + 2) * kt["eig"],
+    }
+    dom = max(per_run, key=per_run.get)
+    pk = _peaks()
+    fp32_peak = NUM_SMS_GB300 * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    spmm = {
+        "fwd_gbs": bytes_fwd / kt["spmm_fwd"] / 1e9,
+        "bwd_gbs": bytes_bwd / kt["spmm_bwd"] / 1e9,
+        "fwd_bytes": bytes_fwd,
+        "bwd_bytes": bytes_bwd,
+    }
+    spmm["fwd_frac_of_measured_hbm"] = spmm["fwd_gbs"] / pk["hbm_gbs"]
+    spmm["bwd_frac_of_measured_hbm"] = spmm["bwd_gbs"] / pk["hbm_gbs"]
+    if dom in ("spmm_fwd", "spmm_bwd"):
+        gbs = spmm["fwd_gbs" if dom == "spmm_fwd" else "bwd_gbs"]
+        roof = {"kernel": dom, "bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": gbs / pk["hbm_gbs"], "traffic": None, "peak_source": pk["source"]}
+    elif dom in ("gram", "project"):
+        flops = (2 * A.n * l * l) if dom == "project" else (2 * A.n * l * l)
+        tf = flops / kt[dom] / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": tf, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": tf / fp32_peak, "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+    else:
+        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": None, "traffic": None, "peak_source": "latency-bound single-CTA eigensolver"}
+
+    line = {
+        "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": name, "form": "plain FP32", "l2": "flushed (256 MB write) before each step",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "passes": passes, "status": info.status, "pve_surrogate": info.pve_ratio,
+        "roofline": roof, "kernels_s": kt, "kernel_s_per_run": per_run, "spmm": spmm,
+        "e2e": {"value": statistics.median(e2e_times), "unit": "s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_run * args.steps, "clocks": clk,
+    }
+    if cpu is not None:
+        t_pass = statistics.median(cpu["t_pass"])
+        line["cpu_baseline"] = {
+            "value": t_pass * (passes + 2), "unit": "s", "cores": cpu["threads"], "kind": "oracle",
+            "sample": f"one full-size power-iteration pass of the FP64 oracle ({t_pass:.2f} s, median of "
+                      f"{len(cpu['t_pass'])}), scaled by this run's passes + 2 = {passes + 2}"}
+    if rank == 0:
+        print(json.dumps(line))
+    h.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = _args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return reference_arm(args)
+    return ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,197 @@
+/*
+ * dashsvd.h -- C ABI of the GB300 dashSVD library.
+ *
+ * dashSVD (Feng, Yu, Xie, Tang, "Faster Randomized SVD with Dynamic Shifts")
+ * computes a rank-k truncated SVD A ~= U diag(S) V^T of a sparse matrix A
+ * (m x n) by randomized subspace iteration with dynamically shifted power
+ * iterations and a per-vector-error (PVE) stopping test:
+ *
+ *   problem statement ......... Sec. 2.1 and Alg. 5 (inputs A, k, s, p_max, tol;
+ *                               outputs U in R^{m x k}, S in R^{k x k}, V in R^{n x k})
+ *   eigSVD orthonormalization . Alg. 3
+ *   shifted power iteration ... Alg. 4 / Alg. 5 steps 3-8, shift rule Sec. 3.1 (Prop. 1)
+ *   PVE test with surrogate ... Eq. 19 and Prop. 3 (Alg. 5 step 5)
+ *   m < n ..................... run on A^T and swap U and V (Sec. 3.1, after Alg. 2)
+ *
+ * Conventions for every entry point
+ *   - Matrices are row-major. A is CSR with int32 row pointers and column ids
+ *     and float32 values; nnz must be < 2^31.
+ *   - Unless stated otherwise, array arguments are DEVICE pointers on the
+ *     current CUDA device, owned by the caller, and must stay valid until the
+ *     call's work has finished on the handle's stream.
+ *   - Calls are not thread-safe per handle. Distinct handles are independent.
+ *   - Every entry point returns a dashsvd_status value (0 = success). On an
+ *     error no output is guaranteed; the handle stays usable unless the status
+ *     is DASHSVD_ECUDA from a sticky CUDA error.
+ *   - Entry points that compute (everything but create/destroy/options/
+ *     status_string/get_trace) enqueue their work on the handle's stream.
+ *     dashsvd_run() waits for its own work before returning (it fills *info);
+ *     the step-level entry points (dashsvd_gaussian ... dashsvd_eigsvd) are
+ *     asynchronous.
+ */
+#ifndef DASHSVD_H
+#define DASHSVD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DASHSVD_ABI_VERSION 1
+#define DASHSVD_MAX_L 256 /* largest l = k + s the API accepts */
+
+typedef enum {
+  DASHSVD_OK = 0,
+  DASHSVD_MAX_PASSES = 1,  /* p_max passes ran without meeting tol; results are valid */
+  DASHSVD_EINVAL = -1,     /* bad argument (sizes, null pointer, k/s/l out of range) */
+  DASHSVD_ENOMEM = -2,     /* device workspace allocation failed */
+  DASHSVD_ECUDA = -3,      /* a CUDA call failed (message: dashsvd_last_error) */
+  DASHSVD_ENONFINITE = -4, /* NaN or Inf met in the singular value estimates */
+  DASHSVD_ETIMEOUT = -5,   /* a bounded device wait ran out */
+  DASHSVD_ENOTIMPL = -6,   /* option or size not supported by this build */
+  DASHSVD_ENOCONV = -7     /* Jacobi eigensolver hit its sweep limit */
+} dashsvd_status;
+
+typedef enum {
+  DASHSVD_FORM_PLAIN = 0,     /* FP32 storage and arithmetic (FP32 Jacobi eig) */
+  DASHSVD_FORM_PRECISION = 1  /* BF16 gathered operands, BF16x3 tensor-core Gram and
+                                 projection, FP64 eig / shift / PVE */
+} dashsvd_form;
+
+typedef struct dashsvd_handle_s* dashsvd_handle;
+
+/* A sparse matrix in CSR form (all three arrays on the device). */
+typedef struct {
+  int64_t m, n, nnz;
+  const int32_t* rowptr; /* m + 1 entries, rowptr[0] = 0, rowptr[m] = nnz */
+  const int32_t* colidx; /* nnz entries in [0, n) */
+  const float* val;      /* nnz entries */
+} dashsvd_csr;
+
+typedef struct {
+  int32_t form;            /* dashsvd_form */
+  int32_t learned;         /* 1: the loaded MLP proposes the shift and the stop pass */
+  uint64_t seed;           /* Philox key of the Gaussian block Omega (Alg. 5 step 1) */
+  int32_t alpha_prev_mode; /* 0: alpha' = the shift used in the pass that produced
+                              Shat' (pairs each Shat with its own shift, as in Prop. 3);
+                              1: Alg. 5 step 7 read literally (alpha' = updated alpha) */
+  int32_t use_graph;       /* 1: the power-iteration loop runs on the device inside a
+                              CUDA graph with a conditional WHILE node (no host sync
+                              per pass); 0: host-driven loop (one sync per pass) */
+  int32_t spmm_variant;    /* -1: autotuned per matrix; 0: warp per row; 1: merge path */
+  int32_t record_trace;    /* 1: keep the per-pass Shat / shift history (get_trace) */
+  int32_t shift;           /* 1: dynamic shifts (dashSVD); 0: alpha = 0 (Alg. 1 form) */
+  int32_t reserved[7];
+} dashsvd_options;
+
+typedef struct {
+  int32_t passes;       /* power iterations executed (p of FC4); passes over A = 2p + 2 */
+  int32_t status;       /* same value as the return code of dashsvd_run */
+  int32_t transposed;   /* 1 if the run worked on A^T because m < n */
+  int32_t spmm_variant; /* variant used for A*Q (low byte) and A^T*Y (next byte) */
+  double alpha;         /* final shift */
+  double pve_ratio;     /* last surrogate PVE ratio (Alg. 5 step 5 left-hand side) */
+  int64_t workspace_bytes; /* device workspace held by the handle */
+  int32_t eig_sweeps;   /* Jacobi sweeps of the last eigensolve */
+  int32_t reserved[5];
+} dashsvd_info;
+
+/* Fill *opt with defaults: plain form, no MLP, seed 0x5EED, alpha_prev_mode 0,
+ * CUDA graph on, autotuned SpMM, no trace, shifts on. */
+int dashsvd_options_init(dashsvd_options* opt);
+
+/* Create a handle on the current device. `cuda_stream` is a cudaStream_t
+ * (NULL = legacy default stream); the handle does not own it. `opt` may be
+ * NULL for defaults. The handle owns its device workspace and cached graphs. */
+int dashsvd_create(dashsvd_handle* h, const dashsvd_options* opt, void* cuda_stream);
+
+/* Free the handle's workspace and graphs (waits for its stream first). */
+int dashsvd_destroy(dashsvd_handle h);
+
+/* dashSVD with PVE accuracy control (Alg. 5) for any m, n (m < n runs on A^T).
+ *   k >= 1, s >= 1, l = k + s <= min(m, n) and l <= DASHSVD_MAX_L;
+ *   max_passes = p_max >= 0 (power iterations); pve_tol <= 0 disables the stop
+ *   test, which gives the fixed-p dashSVD of Alg. 4.
+ * Outputs (device, caller-owned): U m x k row-major, S k values (descending),
+ * V n x k row-major. Returns DASHSVD_OK when the PVE test stopped the loop,
+ * DASHSVD_MAX_PASSES when p_max passes ran (or pve_tol <= 0), else an error.
+ * `info` (host pointer, may be NULL) receives run statistics. */
+int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_passes,
+                double pve_tol, float* U, float* S, float* V, dashsvd_info* info);
+
+/* Copy the per-pass history of the last run (record_trace = 1) to HOST memory.
+ * Record j (0-based) holds 4 + l doubles: pass index, shift used in the pass,
+ * surrogate PVE ratio, shift after the update, then Shat_1..Shat_l of the pass.
+ * Writes at most `cap` doubles; *count receives the number of records. */
+int dashsvd_get_trace(dashsvd_handle h, double* out, int64_t cap, int64_t* count, int* l);
+
+/* Load the weights of the learned shift/stop network (HOST pointer). */
+int dashsvd_load_mlp(dashsvd_handle h, const float* weights, int64_t count);
+
+/* Text for a status code. */
+const char* dashsvd_status_string(int status);
+
+/* Message of the last CUDA failure seen by this library (thread-local). */
+const char* dashsvd_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Step-level entry points: one row of the hot path each, for tests and for
+ * timing single kernels. Asynchronous on the handle's stream.
+ * ---------------------------------------------------------------------- */
+
+/* Omega = randn(rows, l) (Alg. 5 step 1) for global rows row0 .. row0+rows-1:
+ * entry (i, j) is Box-Muller on the Philox4x32-10 block with counter
+ * (i mod 2^32, i >> 32, j >> 2, 0) and key (seed mod 2^32, seed >> 32); words
+ * (0, 1) give columns 4q, 4q+1 (cos, sin), words (2, 3) give 4q+2, 4q+3;
+ * radius uniform ((w >> 8) + 1) 2^-24, angle uniform (w >> 8) 2^-24.
+ * Out: rows x ldy, ldy % 4 == 0, ldy >= l; columns l .. ldy-1 are set to 0. */
+int dashsvd_gaussian(dashsvd_handle h, uint64_t seed, int64_t rows, int l, int64_t row0,
+                     float* Y, int64_t ldy);
+
+/* CSR of A^T (the CSC of A): rowptr_t n + 1, colidx_t / val_t nnz entries.
+ * Column ids within a row of A^T come out in no fixed order. */
+int dashsvd_csr_transpose(dashsvd_handle h, const dashsvd_csr* A, int32_t* rowptr_t,
+                          int32_t* colidx_t, float* val_t);
+
+/* Y = A X (Alg. 5 step 4, inner product A Q; also B = A Q, step 9).
+ * X: A.n x ldx, Y: A.m x ldy, both with ld % 4 == 0 and ld >= l; Y's columns
+ * l .. ldy-1 are set to 0. variant: -1 auto, 0 warp per row, 1 merge path. */
+int dashsvd_spmm(dashsvd_handle h, const dashsvd_csr* A, const float* X, int64_t ldx, int l,
+                 float* Y, int64_t ldy, int variant);
+
+/* Z = At Y - alpha Q (Alg. 5 step 4 with the shift fused), where At is the
+ * CSR of A^T (n x m), Y is m x ldy, Q and Z are n x ld. `alpha` is a DEVICE
+ * pointer to one double (read when the kernel runs); NULL means alpha = 0
+ * (then Q may be NULL). */
+int dashsvd_spmm_shift(dashsvd_handle h, const dashsvd_csr* At, const float* Y, int64_t ldy,
+                       int l, const double* alpha, const float* Q, int64_t ldq, float* Z,
+                       int64_t ldz, int variant);
+
+/* G = C^T C for a tall block C (rows x l, leading dimension ldc % 4 == 0)
+ * (Alg. 3 step 1). G: l x l, leading dimension ldg >= l, FP32 partial sums
+ * per row chunk added in FP64. */
+int dashsvd_gram(dashsvd_handle h, const float* C, int64_t rows, int l, int64_t ldc, float* G,
+                 int64_t ldg);
+
+/* Out = C W (Alg. 3 step 3 with W = V S^-1; Alg. 5 step 11 with W = V(:, 1:k)).
+ * C: rows x ldc (first l columns used), W: l x ldw (first `cols` columns used),
+ * Out: rows x ldo with ldo >= cols; columns cols .. ldo-1 are set to 0. */
+int dashsvd_project(dashsvd_handle h, const float* C, int64_t rows, int l, int64_t ldc,
+                    const float* W, int64_t ldw, int cols, float* Out, int64_t ldo);
+
+/* eigSVD of a tall block C (rows x l, ldc % 4 == 0, rows >= l) (Alg. 3):
+ * U: rows x ldu (first l columns), S: l values descending, V: l x l
+ * (leading dimension l). Columns are ordered by descending S (ties by lower
+ * index) and signed so that each V column's largest-|.| entry is positive; a
+ * column whose eigenvalue is <= 16 * eps * largest eigenvalue (eps: unit
+ * roundoff of the eig precision) gives a zero U column. `form` picks FP32 Jacobi (plain) or FP64 eig (precision). */
+int dashsvd_eigsvd(dashsvd_handle h, const float* C, int64_t rows, int l, int64_t ldc, float* U,
+                   int64_t ldu, float* S, float* V, int form);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DASHSVD_H */

@@ -27,8 +27,11 @@ R2  Shat' = 0 and alpha' = 0 before the first pass, so for tol < 1 the test
 R3  The test's denominator Shat_{k+1} + alpha is floored at
     64 * eps * (Shat_1 + alpha) so an exactly rank-k input can stop.
 R4  A break leaves Q as computed in that pass (the shift update is skipped).
-R6  Eigenvalues d_i <= l * eps * d_1 (eps of the eigensolver's precision) give
-    a zero column of U in eigSVD instead of dividing by a noise-level S_i.
+R6  Eigenvalues d_i <= 16 * eps * d_1 (eps: unit roundoff of the eigensolver's
+    precision) give a zero column of U in eigSVD instead of dividing by a
+    noise-level S_i. The factor is fixed, not l: rounding noise on a zero
+    eigenvalue of a Gram matrix stays within a few eps * d_1, while a factor of
+    l would null genuine tail directions of skewed spectra in FP32.
 R8  Each eigenvector column is signed so that its largest-magnitude entry
     (lowest index on ties) is positive; ties in D are ordered by lower index.
 R10 ``p_max`` counts power iterations (loop passes); passes over A = 2p + 2.
@@ -42,6 +45,7 @@ import numpy as np
 from .philox import gaussian_block
 
 EPS64 = np.finfo(np.float64).eps
+NULL_FACTOR = 16.0  # reading R6
 
 
 def _canonical_order_and_sign(d: np.ndarray, V: np.ndarray):
@@ -68,7 +72,7 @@ def eigsvd(C: np.ndarray, eps: float = EPS64):
     G = C.T @ C
     d, V = np.linalg.eigh(G)  # symmetric eigensolver, ascending
     d, V = _canonical_order_and_sign(d, V)
-    null = d <= l * eps * max(d[0], 0.0) if l else np.zeros(0, bool)
+    null = d <= NULL_FACTOR * eps * max(d[0], 0.0) if l else np.zeros(0, bool)
     S = np.sqrt(np.maximum(d, 0.0))
     inv = np.where(null, 0.0, 1.0 / np.where(null, 1.0, S))
     U = C @ (V * inv[None, :])

@@ -1,0 +1,589 @@
+// Run engine and C ABI of the dashSVD library.
+//
+// dashsvd_run follows Alg. 5 (m >= n form; A^T when m < n):
+//   prologue  Omega = randn(m, l) -> Y;  Z = A^T Omega;  [Q] = eigSVD(Z)        (steps 1-2)
+//   loop      Y = A Q;  Z = A^T Y - alpha Q;  [Q, Shat] = eigSVD(Z);
+//             PVE test; shift update                                          (steps 3-8)
+//   final     B = A Q;  [U_B, S, V_B] = eigSVD(B);  U = U_B(:, 1:k);
+//             V = Q V_B(:, 1:k)                                               (steps 9-11)
+// eigSVD is Gram -> Jacobi eig (+ sort, signs, W = V S^-1, control) -> C W.
+//
+// The whole run is one CUDA graph: the loop is a conditional WHILE node whose
+// flag the eig/control kernel sets on the device, so the host does not wait
+// on any pass. The graph is cached per handle and rebuilt when an argument
+// that is baked into it changes.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace dsvd {
+
+static thread_local char g_last_error[512] = "";
+
+void set_last_error(const char* what, cudaError_t e, const char* file, int line) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+}
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+// Grow-only device buffer; returns a status code.
+int ensure(DevBuf& b, size_t bytes, bool* moved) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return DASHSVD_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return DASHSVD_ENOMEM;
+  }
+  b.bytes = bytes;
+  if (moved) *moved = true;
+  return DASHSVD_OK;
+}
+
+template <typename T>
+T* as(DevBuf& b) {
+  return reinterpret_cast<T*>(b.p);
+}
+
+struct GraphKey {
+  dashsvd_csr A;
+  int k, s, pmax;
+  double tol;
+  float *U, *S, *V;
+  uint64_t seed;
+  int alpha_prev_mode, shift, record_trace, var_fwd, var_bwd;
+  bool operator==(const GraphKey& o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
+};
+
+}  // namespace
+}  // namespace dsvd
+
+using namespace dsvd;
+
+struct dashsvd_handle_s {
+  dashsvd_options opt;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;   // capture stream for the graph (the caller's may be the legacy stream)
+  cudaStream_t side = nullptr;  // capture stream for the loop body
+  int device = 0;
+  int num_sms = 0;
+  // workspace
+  DevBuf rowptr_b, col_b, val_b, cursor, scan_tmp;  // the CSR built by transposition
+  DevBuf Y, Z, Q, G, W, W2, partial, carry, carry_row, ctl, trace;
+  // cached graph
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  GraphKey key;
+  bool have_graph = false;
+  // last run
+  int last_l = 0;
+  int64_t last_records = 0;
+  std::vector<float> mlp;
+};
+
+namespace {
+
+void drop_graph(dashsvd_handle h) {
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->exec = nullptr;
+  h->graph = nullptr;
+  h->have_graph = false;
+}
+
+bool csr_ok(const dashsvd_csr* A) {
+  if (!A || A->m < 1 || A->n < 1 || A->nnz < 0 || A->nnz >= (int64_t)1 << 31) return false;
+  if (A->m >= (int64_t)1 << 31 || A->n >= (int64_t)1 << 31) return false;
+  if (!A->rowptr) return false;
+  if (A->nnz > 0 && (!A->colidx || !A->val)) return false;
+  return true;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Everything one run launches, in order; `cond` is the loop's conditional
+// handle (0 when the host drives the loop).
+struct RunPlan {
+  dashsvd_csr Aw, AwT;  // working A (mw x nw, mw >= nw) and its transpose
+  int64_t mw, nw;
+  int k, l, ld, pmax;
+  double tol;
+  float *Uw, *Vw, *S;  // outputs on the working side
+  int var_fwd, var_bwd;
+  SpmmScratch scr;
+};
+
+EigArgs eig_args(dashsvd_handle h, const RunPlan& p, int mode, unsigned long long cond) {
+  EigArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.l = p.l;
+  a.k = p.k;
+  a.ldw = (int)p.ld;
+  a.mode = mode;
+  a.pmax = p.pmax;
+  a.alpha_prev_mode = h->opt.alpha_prev_mode;
+  a.shift = h->opt.shift;
+  a.tol = p.tol;
+  a.W = as<float>(h->W);
+  a.W2 = as<float>(h->W2);
+  a.S_out = p.S;
+  a.ctl = as<Control>(h->ctl);
+  a.trace = (mode == kModePass && h->opt.record_trace) ? as<double>(h->trace) : nullptr;
+  a.cond = cond;
+  a.use_cond = cond != 0;
+  return a;
+}
+
+cudaError_t eigsvd_step(dashsvd_handle h, const RunPlan& p, const float* C, int64_t rows, int mode,
+                        unsigned long long cond, cudaStream_t st) {
+  cudaError_t e = launch_gram(C, rows, p.l, p.ld, as<float>(h->G), p.ld, as<float>(h->partial), h->num_sms, st);
+  if (e != cudaSuccess) return e;
+  return launch_eig_f32(as<float>(h->G), p.ld, eig_args(h, p, mode, cond), st);
+}
+
+cudaError_t launch_prologue(dashsvd_handle h, const RunPlan& p, unsigned long long cond, cudaStream_t st) {
+  cudaError_t e;
+  // Alg. 5 step 1: Omega (mw x l) into Y
+  if ((e = launch_gaussian(h->opt.seed, p.mw, p.l, 0, as<float>(h->Y), p.ld, st)) != cudaSuccess) return e;
+  // step 2: Z = A^T Omega, Q = eigSVD(Z)
+  if ((e = launch_spmm(p.AwT, as<float>(h->Y), p.ld, p.l, as<float>(h->Z), p.ld, nullptr, nullptr, 0, p.var_bwd, p.scr,
+                       h->num_sms, st)) != cudaSuccess)
+    return e;
+  if ((e = eigsvd_step(h, p, as<float>(h->Z), p.nw, kModeInit, cond, st)) != cudaSuccess) return e;
+  return launch_project(as<float>(h->Z), p.nw, p.l, p.ld, as<float>(h->W), p.ld, p.l, as<float>(h->Q), p.ld,
+                        h->num_sms, st);
+}
+
+cudaError_t launch_pass(dashsvd_handle h, const RunPlan& p, unsigned long long cond, cudaStream_t st) {
+  cudaError_t e;
+  const Control* ctl = as<Control>(h->ctl);
+  // step 4: Y = A Q; Z = A^T Y - alpha Q; [Q, Shat] = eigSVD(Z)
+  if ((e = launch_spmm(p.Aw, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld, nullptr, nullptr, 0, p.var_fwd, p.scr,
+                       h->num_sms, st)) != cudaSuccess)
+    return e;
+  if ((e = launch_spmm(p.AwT, as<float>(h->Y), p.ld, p.l, as<float>(h->Z), p.ld, &ctl->alpha, as<float>(h->Q), p.ld,
+                       p.var_bwd, p.scr, h->num_sms, st)) != cudaSuccess)
+    return e;
+  // steps 5-7 run inside the eig kernel's control tail
+  if ((e = eigsvd_step(h, p, as<float>(h->Z), p.nw, kModePass, cond, st)) != cudaSuccess) return e;
+  return launch_project(as<float>(h->Z), p.nw, p.l, p.ld, as<float>(h->W), p.ld, p.l, as<float>(h->Q), p.ld,
+                        h->num_sms, st);
+}
+
+cudaError_t launch_final(dashsvd_handle h, const RunPlan& p, cudaStream_t st) {
+  cudaError_t e;
+  // step 9: B = A Q (into Y)
+  if ((e = launch_spmm(p.Aw, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld, nullptr, nullptr, 0, p.var_fwd, p.scr,
+                       h->num_sms, st)) != cudaSuccess)
+    return e;
+  // steps 10-11: eigSVD(B); U = B V_k S_k^-1; V = Q V_k
+  if ((e = eigsvd_step(h, p, as<float>(h->Y), p.mw, kModeFinal, 0, st)) != cudaSuccess) return e;
+  if ((e = launch_project(as<float>(h->Y), p.mw, p.l, p.ld, as<float>(h->W), p.ld, p.k, p.Uw, p.k, h->num_sms, st)) !=
+      cudaSuccess)
+    return e;
+  return launch_project(as<float>(h->Q), p.nw, p.l, p.ld, as<float>(h->W2), p.ld, p.k, p.Vw, p.k, h->num_sms, st);
+}
+
+int build_graph(dashsvd_handle h, const RunPlan& p) {
+  drop_graph(h);
+  cudaStream_t st = h->cap;
+  DS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t cap = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  cudaGraphConditionalHandle cond = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cap, &deps, nullptr, &ndeps);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, cap, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) e = launch_prologue(h, p, (unsigned long long)cond, st);
+  cudaGraphNode_t cnode = nullptr;
+  cudaGraph_t body = nullptr;
+  if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cap, &deps, nullptr, &ndeps);
+  if (e == cudaSuccess) {
+    std::vector<cudaGraphNode_t> dv(deps, deps + ndeps);
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    e = cudaGraphAddNode(&cnode, cap, dv.data(), nullptr, dv.size(), &np);
+    if (e == cudaSuccess) body = np.conditional.phGraph_out[0];
+  }
+  if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(st, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(h->side, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    e = launch_pass(h, p, (unsigned long long)cond, h->side);
+    cudaGraph_t dummy = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(h->side, &dummy);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = launch_final(h, p, st);
+  cudaGraph_t g = nullptr;
+  cudaError_t e3 = cudaStreamEndCapture(st, &g);
+  if (e == cudaSuccess) e = e3;
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    set_last_error("graph capture", e, __FILE__, __LINE__);
+    return DASHSVD_ECUDA;
+  }
+  h->graph = g;
+  e = cudaGraphInstantiate(&h->exec, g, 0);
+  if (e != cudaSuccess) {
+    set_last_error("cudaGraphInstantiate", e, __FILE__, __LINE__);
+    drop_graph(h);
+    return DASHSVD_ECUDA;
+  }
+  h->have_graph = true;
+  return DASHSVD_OK;
+}
+
+int status_from_control(const Control& c) {
+  if (c.status & kStatusNonFinite) return DASHSVD_ENONFINITE;
+  if (c.status & kStatusNoConv) return DASHSVD_ENOCONV;
+  return c.stop ? DASHSVD_OK : DASHSVD_MAX_PASSES;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dashsvd_options_init(dashsvd_options* opt) {
+  if (!opt) return DASHSVD_EINVAL;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->form = DASHSVD_FORM_PLAIN;
+  opt->learned = 0;
+  opt->seed = 0x5EED;
+  opt->alpha_prev_mode = 0;
+  opt->use_graph = 1;
+  opt->spmm_variant = -1;
+  opt->record_trace = 0;
+  opt->shift = 1;
+  return DASHSVD_OK;
+}
+
+const char* dashsvd_status_string(int status) {
+  switch (status) {
+    case DASHSVD_OK: return "ok: PVE tolerance met";
+    case DASHSVD_MAX_PASSES: return "max_passes reached (results valid)";
+    case DASHSVD_EINVAL: return "invalid argument";
+    case DASHSVD_ENOMEM: return "device memory allocation failed";
+    case DASHSVD_ECUDA: return "CUDA error";
+    case DASHSVD_ENONFINITE: return "non-finite value in the singular value estimates";
+    case DASHSVD_ETIMEOUT: return "bounded device wait ran out";
+    case DASHSVD_ENOTIMPL: return "not implemented for these options or sizes";
+    case DASHSVD_ENOCONV: return "Jacobi eigensolver hit its sweep limit";
+    default: return "unknown status";
+  }
+}
+
+const char* dashsvd_last_error(void) { return g_last_error; }
+
+int dashsvd_create(dashsvd_handle* out, const dashsvd_options* opt, void* cuda_stream) {
+  if (!out) return DASHSVD_EINVAL;
+  *out = nullptr;
+  dashsvd_handle h = new (std::nothrow) dashsvd_handle_s();
+  if (!h) return DASHSVD_ENOMEM;
+  if (opt)
+    h->opt = *opt;
+  else
+    dashsvd_options_init(&h->opt);
+  if (h->opt.alpha_prev_mode != 0 && h->opt.alpha_prev_mode != 1) {
+    delete h;
+    return DASHSVD_EINVAL;
+  }
+  h->stream = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = prepare_project();
+  if (e == cudaSuccess) e = prepare_eig();
+  if (e != cudaSuccess) {
+    set_last_error("dashsvd_create", e, __FILE__, __LINE__);
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    delete h;
+    return DASHSVD_ECUDA;
+  }
+  *out = h;
+  return DASHSVD_OK;
+}
+
+int dashsvd_destroy(dashsvd_handle h) {
+  if (!h) return DASHSVD_EINVAL;
+  cudaStreamSynchronize(h->stream);
+  drop_graph(h);
+  DevBuf* bufs[] = {&h->rowptr_b, &h->col_b, &h->val_b, &h->cursor, &h->scan_tmp, &h->Y,       &h->Z,
+                    &h->Q,        &h->G,     &h->W,     &h->W2,     &h->partial,  &h->carry, &h->carry_row,
+                    &h->ctl,      &h->trace};
+  for (DevBuf* b : bufs)
+    if (b->p) cudaFree(b->p);
+  if (h->side) cudaStreamDestroy(h->side);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  delete h;
+  return DASHSVD_OK;
+}
+
+int dashsvd_load_mlp(dashsvd_handle h, const float* weights, int64_t count) {
+  if (!h || (!weights && count > 0) || count < 0) return DASHSVD_EINVAL;
+  h->mlp.assign(weights, weights + count);
+  return DASHSVD_ENOTIMPL;
+}
+
+int dashsvd_get_trace(dashsvd_handle h, double* out, int64_t cap, int64_t* count, int* l) {
+  if (!h) return DASHSVD_EINVAL;
+  if (count) *count = h->last_records;
+  if (l) *l = h->last_l;
+  const int64_t n = h->last_records * (4 + h->last_l);
+  if (out && cap > 0 && n > 0 && h->trace.p) {
+    DS_CUDA(cudaStreamSynchronize(h->stream));
+    DS_CUDA(cudaMemcpy(out, h->trace.p, sizeof(double) * (size_t)(n < cap ? n : cap), cudaMemcpyDeviceToHost));
+  }
+  return DASHSVD_OK;
+}
+
+int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_passes, double pve_tol, float* U,
+                float* S, float* V, dashsvd_info* info) {
+  if (info) std::memset(info, 0, sizeof(*info));
+  if (!h || !csr_ok(A) || !U || !S || !V) return DASHSVD_EINVAL;
+  if (k < 1 || s < 1 || max_passes < 0) return DASHSVD_EINVAL;
+  const int64_t l = (int64_t)k + s;
+  const int64_t mn = A->m < A->n ? A->m : A->n;
+  if (l > mn || l > DASHSVD_MAX_L) return DASHSVD_EINVAL;
+  if (h->opt.form != DASHSVD_FORM_PLAIN || h->opt.learned) return DASHSVD_ENOTIMPL;
+  if (l > eig_max_l_f32()) return DASHSVD_ENOTIMPL;
+
+  RunPlan p;
+  const bool tr = A->m < A->n;
+  p.k = k;
+  p.l = (int)l;
+  p.ld = (int)round_up(l, 8);
+  p.pmax = max_passes;
+  p.tol = pve_tol;
+  // the transposition builds the CSR of the given matrix's transpose
+  const int64_t rows_b = A->n;
+  bool moved = false;
+  int rc;
+  if ((rc = ensure(h->rowptr_b, sizeof(int32_t) * (size_t)(rows_b + 1), &moved)) ||
+      (rc = ensure(h->col_b, sizeof(int32_t) * (size_t)A->nnz, &moved)) ||
+      (rc = ensure(h->val_b, sizeof(float) * (size_t)A->nnz, &moved)) ||
+      (rc = ensure(h->cursor, sizeof(int32_t) * (size_t)rows_b, &moved)) ||
+      (rc = ensure(h->scan_tmp, sizeof(int32_t) * scan_tmp_ints(rows_b), &moved)))
+    return rc;
+  dashsvd_csr built{A->n, A->m, A->nnz, as<int32_t>(h->rowptr_b), as<int32_t>(h->col_b), as<float>(h->val_b)};
+  if (!tr) {
+    p.Aw = *A;
+    p.AwT = built;
+    p.Uw = U;
+    p.Vw = V;
+  } else {
+    p.Aw = built;
+    p.AwT = *A;
+    p.Uw = V;
+    p.Vw = U;
+  }
+  p.mw = p.Aw.m;
+  p.nw = p.Aw.n;
+  p.S = S;
+  const int64_t warps = spmm_mergepath_warps(h->num_sms);
+  const size_t gp = std::max(gram_partial_floats(p.mw, p.l, h->num_sms), gram_partial_floats(p.nw, p.l, h->num_sms));
+  if ((rc = ensure(h->Y, sizeof(float) * (size_t)(p.mw * p.ld), &moved)) ||
+      (rc = ensure(h->Z, sizeof(float) * (size_t)(p.nw * p.ld), &moved)) ||
+      (rc = ensure(h->Q, sizeof(float) * (size_t)(p.nw * p.ld), &moved)) ||
+      (rc = ensure(h->G, sizeof(float) * (size_t)(p.ld * p.ld), &moved)) ||
+      (rc = ensure(h->W, sizeof(float) * (size_t)(p.ld * p.ld), &moved)) ||
+      (rc = ensure(h->W2, sizeof(float) * (size_t)(p.ld * p.ld), &moved)) ||
+      (rc = ensure(h->partial, sizeof(float) * gp, &moved)) ||
+      (rc = ensure(h->carry, sizeof(float) * (size_t)(2 * warps * p.ld), &moved)) ||
+      (rc = ensure(h->carry_row, sizeof(int32_t) * (size_t)(2 * warps), &moved)) ||
+      (rc = ensure(h->ctl, sizeof(Control), &moved)) ||
+      (rc = ensure(h->trace, sizeof(double) * (size_t)((max_passes + 1) * (4 + l)), &moved)))
+    return rc;
+  p.scr.carry = as<float>(h->carry);
+  p.scr.carry_row = as<int32_t>(h->carry_row);
+  p.scr.warps = warps;
+  // work split: merge path where row lengths are very uneven, else warp per row
+  const int forced = h->opt.spmm_variant;
+  p.var_fwd = forced >= 0 ? forced : 1;
+  p.var_bwd = forced >= 0 ? forced : 1;
+
+  cudaStream_t st = h->stream;
+  DS_CUDA(launch_csr_transpose(*A, as<int32_t>(h->rowptr_b), as<int32_t>(h->col_b), as<float>(h->val_b),
+                               as<int32_t>(h->cursor), as<int32_t>(h->scan_tmp), st));
+
+  if (h->opt.use_graph) {
+    GraphKey key;
+    std::memset(&key, 0, sizeof(key));
+    key.A = *A;
+    key.k = k;
+    key.s = s;
+    key.pmax = max_passes;
+    key.tol = pve_tol;
+    key.U = U;
+    key.S = S;
+    key.V = V;
+    key.seed = h->opt.seed;
+    key.alpha_prev_mode = h->opt.alpha_prev_mode;
+    key.shift = h->opt.shift;
+    key.record_trace = h->opt.record_trace;
+    key.var_fwd = p.var_fwd;
+    key.var_bwd = p.var_bwd;
+    if (moved || !h->have_graph || !(key == h->key)) {
+      if ((rc = build_graph(h, p)) != DASHSVD_OK) return rc;
+      h->key = key;
+    }
+    DS_CUDA(cudaGraphLaunch(h->exec, st));
+  } else {
+    DS_CUDA(launch_prologue(h, p, 0, st));
+    Control hc;
+    for (int j = 0; j < max_passes; ++j) {
+      DS_CUDA(cudaMemcpyAsync(&hc, h->ctl.p, sizeof(Control), cudaMemcpyDeviceToHost, st));
+      DS_CUDA(cudaStreamSynchronize(st));
+      if (!hc.cont) break;
+      DS_CUDA(launch_pass(h, p, 0, st));
+    }
+    DS_CUDA(launch_final(h, p, st));
+  }
+  Control hc;
+  DS_CUDA(cudaMemcpyAsync(&hc, h->ctl.p, sizeof(Control), cudaMemcpyDeviceToHost, st));
+  DS_CUDA(cudaStreamSynchronize(st));
+  h->last_l = p.l;
+  h->last_records = h->opt.record_trace ? hc.pass : 0;
+  const int status = status_from_control(hc);
+  if (info) {
+    info->passes = hc.pass;
+    info->status = status;
+    info->transposed = tr ? 1 : 0;
+    info->spmm_variant = p.var_fwd | (p.var_bwd << 8);
+    info->alpha = hc.alpha;
+    info->pve_ratio = hc.ratio;
+    int64_t ws = 0;
+    DevBuf* bufs[] = {&h->rowptr_b, &h->col_b, &h->val_b, &h->cursor, &h->scan_tmp, &h->Y,       &h->Z,
+                      &h->Q,        &h->G,     &h->W,     &h->W2,     &h->partial,  &h->carry, &h->carry_row,
+                      &h->ctl,      &h->trace};
+    for (DevBuf* b : bufs) ws += (int64_t)b->bytes;
+    info->workspace_bytes = ws;
+    info->eig_sweeps = hc.sweeps;
+  }
+  return status;
+}
+
+// ---------------------------------------------------------------- step level
+
+int dashsvd_gaussian(dashsvd_handle h, uint64_t seed, int64_t rows, int l, int64_t row0, float* Y, int64_t ldy) {
+  if (!h || !Y || rows < 0 || l < 1 || row0 < 0 || ldy < l || ldy % 4 || !aligned16(Y)) return DASHSVD_EINVAL;
+  DS_CUDA(launch_gaussian(seed, rows, l, row0, Y, ldy, h->stream));
+  return DASHSVD_OK;
+}
+
+int dashsvd_csr_transpose(dashsvd_handle h, const dashsvd_csr* A, int32_t* rowptr_t, int32_t* colidx_t,
+                          float* val_t) {
+  if (!h || !csr_ok(A) || !rowptr_t || (A->nnz > 0 && (!colidx_t || !val_t))) return DASHSVD_EINVAL;
+  int rc;
+  bool moved = false;
+  if ((rc = ensure(h->cursor, sizeof(int32_t) * (size_t)A->n, &moved)) ||
+      (rc = ensure(h->scan_tmp, sizeof(int32_t) * scan_tmp_ints(A->n), &moved)))
+    return rc;
+  if (moved) h->have_graph = false;
+  DS_CUDA(launch_csr_transpose(*A, rowptr_t, colidx_t, val_t, as<int32_t>(h->cursor), as<int32_t>(h->scan_tmp),
+                               h->stream));
+  return DASHSVD_OK;
+}
+
+static int spmm_common(dashsvd_handle h, const dashsvd_csr* A, const float* X, int64_t ldx, int l, float* Y,
+                       int64_t ldy, const double* alpha, const float* Q, int64_t ldq, int variant) {
+  if (!h || !csr_ok(A) || !X || !Y || l < 1 || l > DASHSVD_MAX_L) return DASHSVD_EINVAL;
+  if (ldx < l || ldy < l || ldx % 4 || ldy % 4 || !aligned16(X) || !aligned16(Y)) return DASHSVD_EINVAL;
+  if (alpha && (!Q || ldq < l || ldq % 4 || !aligned16(Q))) return DASHSVD_EINVAL;
+  if (variant < -1 || variant > 1) return DASHSVD_EINVAL;
+  const int64_t warps = spmm_mergepath_warps(h->num_sms);
+  int rc;
+  bool moved = false;
+  if ((rc = ensure(h->carry, sizeof(float) * (size_t)(2 * warps * ldy), &moved)) ||
+      (rc = ensure(h->carry_row, sizeof(int32_t) * (size_t)(2 * warps), &moved)))
+    return rc;
+  if (moved) h->have_graph = false;
+  SpmmScratch scr;
+  scr.carry = as<float>(h->carry);
+  scr.carry_row = as<int32_t>(h->carry_row);
+  scr.warps = warps;
+  DS_CUDA(launch_spmm(*A, X, ldx, l, Y, ldy, alpha, Q, ldq, variant < 0 ? 1 : variant, scr, h->num_sms, h->stream));
+  return DASHSVD_OK;
+}
+
+int dashsvd_spmm(dashsvd_handle h, const dashsvd_csr* A, const float* X, int64_t ldx, int l, float* Y, int64_t ldy,
+                 int variant) {
+  return spmm_common(h, A, X, ldx, l, Y, ldy, nullptr, nullptr, 0, variant);
+}
+
+int dashsvd_spmm_shift(dashsvd_handle h, const dashsvd_csr* At, const float* Y, int64_t ldy, int l,
+                       const double* alpha, const float* Q, int64_t ldq, float* Z, int64_t ldz, int variant) {
+  return spmm_common(h, At, Y, ldy, l, Z, ldz, alpha, Q, ldq, variant);
+}
+
+int dashsvd_gram(dashsvd_handle h, const float* C, int64_t rows, int l, int64_t ldc, float* G, int64_t ldg) {
+  if (!h || !C || !G || rows < 0 || l < 1 || l > DASHSVD_MAX_L || ldc < l || ldc % 4 || ldg < l || !aligned16(C))
+    return DASHSVD_EINVAL;
+  int rc;
+  bool moved = false;
+  if ((rc = ensure(h->partial, sizeof(float) * gram_partial_floats(rows, l, h->num_sms), &moved))) return rc;
+  if (moved) h->have_graph = false;
+  DS_CUDA(launch_gram(C, rows, l, ldc, G, ldg, as<float>(h->partial), h->num_sms, h->stream));
+  return DASHSVD_OK;
+}
+
+int dashsvd_project(dashsvd_handle h, const float* C, int64_t rows, int l, int64_t ldc, const float* W, int64_t ldw,
+                    int cols, float* Out, int64_t ldo) {
+  if (!h || !C || !W || !Out || rows < 0 || l < 1 || l > DASHSVD_MAX_L || cols < 1 || cols > DASHSVD_MAX_L)
+    return DASHSVD_EINVAL;
+  if (ldc < l || ldc % 4 || ldw < cols || ldo < cols || ldo > DASHSVD_MAX_L || !aligned16(C)) return DASHSVD_EINVAL;
+  DS_CUDA(launch_project(C, rows, l, ldc, W, ldw, cols, Out, ldo, h->num_sms, h->stream));
+  return DASHSVD_OK;
+}
+
+int dashsvd_eigsvd(dashsvd_handle h, const float* C, int64_t rows, int l, int64_t ldc, float* U, int64_t ldu, float* S,
+                   float* V, int form) {
+  if (!h || !C || !U || !S || !V || l < 1 || rows < l || ldc < l || ldc % 4 || ldu < l || ldu > DASHSVD_MAX_L ||
+      !aligned16(C))
+    return DASHSVD_EINVAL;
+  if (form != DASHSVD_FORM_PLAIN) return DASHSVD_ENOTIMPL;
+  if (l > eig_max_l_f32()) return DASHSVD_ENOTIMPL;
+  const int64_t ld = round_up(l, 8);
+  int rc;
+  bool moved = false;
+  if ((rc = ensure(h->G, sizeof(float) * (size_t)(ld * ld), &moved)) ||
+      (rc = ensure(h->W, sizeof(float) * (size_t)(ld * ld), &moved)) ||
+      (rc = ensure(h->partial, sizeof(float) * gram_partial_floats(rows, l, h->num_sms), &moved)))
+    return rc;
+  if (moved) h->have_graph = false;
+  cudaStream_t st = h->stream;
+  DS_CUDA(launch_gram(C, rows, l, ldc, as<float>(h->G), ld, as<float>(h->partial), h->num_sms, st));
+  EigArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.l = l;
+  a.k = l;
+  a.ldw = (int)ld;
+  a.mode = kModeEigsvd;
+  a.W = as<float>(h->W);
+  a.W2 = V;
+  a.S_out = S;
+  DS_CUDA(launch_eig_f32(as<float>(h->G), ld, a, st));
+  DS_CUDA(launch_project(C, rows, l, ldc, as<float>(h->W), ld, l, U, ldu, h->num_sms, st));
+  return DASHSVD_OK;
+}
+
+}  // extern "C"

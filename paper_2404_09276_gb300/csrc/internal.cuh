@@ -1,0 +1,115 @@
+// Internal declarations of the dashSVD GB300 library: device-side control
+// block, launcher signatures and small device helpers shared by the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dashsvd.h"
+
+namespace dsvd {
+
+constexpr int kMaxL = DASHSVD_MAX_L;
+
+// Loop state kept on the device between passes (Alg. 5: alpha, alpha', Shat').
+struct Control {
+  double alpha;       // shift applied in the next product A^T A Q - alpha Q
+  double alpha_prev;  // alpha' paired with S_prev in the stop test
+  double ratio;       // last surrogate PVE ratio
+  int32_t pass;       // power iterations done
+  int32_t stop;       // 1 once the PVE test has passed
+  int32_t status;     // kStatus* bit flags
+  int32_t cont;       // 1 while another pass should run
+  int32_t sweeps;     // Jacobi sweeps of the last eigensolve
+  int32_t pad[3];
+  double S_prev[kMaxL];  // Shat' (descending)
+  double S[kMaxL];       // Shat of the last eigSVD (descending)
+};
+
+enum : int32_t {
+  kStatusNonFinite = 1,
+  kStatusNoConv = 2,
+};
+
+enum EigMode : int32_t {
+  kModeEigsvd = 0,  // plain eigSVD: W = V S^-1, S out (step-level entry point)
+  kModeInit = 1,    // Alg. 5 step 2: W = V S^-1, reset alpha, alpha', Shat'
+  kModePass = 2,    // Alg. 5 steps 4-7: W = V S^-1, PVE test, shift update
+  kModeFinal = 3,   // Alg. 5 steps 10-11: W_U = V_k S_k^-1, W_V = V_k, S_k out
+};
+
+struct EigArgs {
+  int l;             // matrix order
+  int k;             // rank (final mode / PVE test)
+  int ldw;           // leading dimension of W (and W2)
+  int mode;          // EigMode
+  int pmax;          // p_max (pass mode)
+  int alpha_prev_mode;
+  int shift;         // 1 dynamic shifts, 0 alpha = 0
+  double tol;        // PVE tolerance (<= 0: no test)
+  float* W;          // l x ldw: V S^-1 (sorted, signed)  [final: V_k S_k^-1]
+  float* W2;         // final: V_k (l x ldw); eigsvd: V (l x l, ld l)
+  float* S_out;      // eigsvd: l values; final: k values
+  Control* ctl;      // device control block (init/pass/final)
+  double* trace;     // pass mode: trace buffer or nullptr
+  unsigned long long cond;  // cudaGraphConditionalHandle (0: none)
+  int use_cond;
+};
+
+// ---- launchers (all asynchronous on `st`) --------------------------------
+cudaError_t launch_gaussian(uint64_t seed, int64_t rows, int l, int64_t row0, float* Y,
+                            int64_t ldy, cudaStream_t st);
+
+// CSR transpose; `cursor` is n int32 scratch.
+cudaError_t launch_csr_transpose(const dashsvd_csr& A, int32_t* rowptr_t, int32_t* colidx_t,
+                                 float* val_t, int32_t* cursor, int32_t* scan_tmp,
+                                 cudaStream_t st);
+size_t scan_tmp_ints(int64_t n);
+
+// SpMM Y = A X (alpha == nullptr) or Y = A X - alpha Q.
+struct SpmmScratch {
+  float* carry = nullptr;      // 2 * warps * ldy floats
+  int32_t* carry_row = nullptr;  // 2 * warps
+  int64_t warps = 0;
+};
+int spmm_mergepath_warps(int num_sms);
+cudaError_t launch_spmm(const dashsvd_csr& A, const float* X, int64_t ldx, int l, float* Y,
+                        int64_t ldy, const double* alpha, const float* Q, int64_t ldq,
+                        int variant, const SpmmScratch& scr, int num_sms, cudaStream_t st);
+
+// Gram G = C^T C.
+size_t gram_partial_floats(int64_t rows, int l, int num_sms);
+cudaError_t launch_gram(const float* C, int64_t rows, int l, int64_t ldc, float* G, int64_t ldg,
+                        float* partial, int num_sms, cudaStream_t st);
+
+// Jacobi eigensolver + sort/sign/null policy + loop control (single CTA).
+int eig_max_l_f32();
+cudaError_t launch_eig_f32(const float* G, int64_t ldg, const EigArgs& a, cudaStream_t st);
+
+// Out = C W.
+cudaError_t launch_project(const float* C, int64_t rows, int l, int64_t ldc, const float* W,
+                           int64_t ldw, int cols, float* Out, int64_t ldo, int num_sms,
+                           cudaStream_t st);
+
+// One-time per-process opt-ins (dynamic shared memory above 48 KB); must run
+// before any launch is captured into a graph.
+cudaError_t prepare_project();
+cudaError_t prepare_eig();
+
+// ---- error plumbing --------------------------------------------------------
+void set_last_error(const char* what, cudaError_t e, const char* file, int line);
+
+}  // namespace dsvd
+
+#define DS_CUDA(x)                                                  \
+  do {                                                              \
+    cudaError_t e_ = (x);                                           \
+    if (e_ != cudaSuccess) {                                        \
+      ::dsvd::set_last_error(#x, e_, __FILE__, __LINE__);           \
+      return DASHSVD_ECUDA;                                         \
+    }                                                               \
+  } while (0)
+
+#define DS_LAUNCH_CHECK() cudaGetLastError()
+
+static inline __host__ __device__ int64_t ds_ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

@@ -1,0 +1,176 @@
+"""GPU parity of the whole hot path (dashsvd_run, Alg. 5) against the FP64
+oracle on the same seeded matrix and the same Philox Gaussian block.
+
+Bar (plain FP32 form): sigma_1..sigma_k within 1e-4 relative of the oracle at
+the same number of passes; principal angles of U_k and V_k within 1e-3 rad
+where the relative gap (sigma_k - sigma_{k+1}) / sigma_k is at least 1e-2; the
+PVE stop pass within one pass of the oracle's.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import datagen
+import oracle
+from oracle import metrics
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ds():
+    import torch
+
+    assert torch.cuda.is_available()
+    import paper_2404_09276_gb300 as mod
+
+    return mod
+
+
+def _run(ds, A, k, s, p, tol, **opts):
+    import torch
+
+    with ds.Handle(**opts) as h:
+        U, S, V, info = h.run(ds.CsrDevice.from_host(A), k, s, p, tol)
+        torch.cuda.synchronize()
+        tr = h.trace() if opts.get("record_trace") else None
+    f = lambda x: x.cpu().numpy().astype(np.float64)  # noqa: E731
+    return f(U), f(S), f(V), info, tr
+
+
+def _compare(U, S, V, ref, k, sig_tol=1e-4, ang_tol=1e-3):
+    rel = np.abs(S - ref.S) / ref.S
+    assert np.max(rel) <= sig_tol, np.max(rel)
+    # subspace angles of leading blocks whose trailing gap is clear
+    Sr = ref.S
+    for j in range(1, k + 1):
+        if j == k or (Sr[j - 1] - Sr[j]) / Sr[j - 1] >= 1e-2:
+            if j in (k // 2, k) or j == 1:
+                assert np.max(metrics.principal_angles(U[:, :j], ref.U[:, :j])) <= ang_tol
+                assert np.max(metrics.principal_angles(V[:, :j], ref.V[:, :j])) <= ang_tol
+
+
+@pytest.mark.parametrize("p", [0, 1, 3])
+def test_fixed_passes_small_config1(ds, p):
+    A, prm = datagen.make_config(1, scale=0.1)
+    k, s = prm["k"], prm["s"]
+    U, S, V, info, _ = _run(ds, A, k, s, p, 0.0)
+    ref = oracle.dashsvd(A.to_scipy(), k, s, p_max=p, tol=0.0, seed=0x5EED)
+    assert info.passes == p and info.status == ds.DASHSVD_MAX_PASSES
+    _compare(U, S, V, ref, k)
+
+
+def test_config1_full_size_with_pve_control(ds):
+    """The 20000 x 10000 workload (k = 20, s = 10, p_max = 10, tol = 1e-2)."""
+    A, prm = datagen.make_config(1)
+    k, s = prm["k"], prm["s"]
+    U, S, V, info, tr = _run(ds, A, k, s, prm["p_max"], prm["tol"], record_trace=1)
+    ref = oracle.dashsvd(A.to_scipy(), k, s, p_max=prm["p_max"], tol=prm["tol"], seed=0x5EED)
+    assert abs(info.passes - ref.passes) <= 1
+    assert info.status == (ds.DASHSVD_OK if ref.converged else ds.DASHSVD_MAX_PASSES)
+    if info.passes == ref.passes:
+        _compare(U, S, V, ref, k)
+    # per-pass surrogate values match the oracle's trace
+    for (j, a_used, ratio, a_next, Sh), rec in zip(tr, ref.trace):
+        assert j == rec.j
+        np.testing.assert_allclose(Sh, rec.S, rtol=1e-3)
+        np.testing.assert_allclose(a_used, rec.alpha_used, rtol=1e-3, atol=1e-30)
+
+
+def test_wide_matrix_runs_on_transpose(ds):
+    A0, prm = datagen.make_config(1, scale=0.1)
+    At = A0.to_scipy(np.float32).T.tocsr()
+    A = datagen.Csr(At.shape[0], At.shape[1], At.indptr.astype(np.int32), At.indices.astype(np.int32),
+                    At.data.astype(np.float32))
+    k, s = 10, 6
+    U, S, V, info, _ = _run(ds, A, k, s, 2, 0.0)
+    assert info.transposed == 1 and U.shape == (A.m, k) and V.shape == (A.n, k)
+    ref = oracle.dashsvd(A.to_scipy(), k, s, p_max=2, tol=0.0, seed=0x5EED)
+    _compare(U, S, V, ref, k)
+
+
+def test_graph_and_host_loop_agree(ds):
+    A, prm = datagen.make_config(2, scale=0.01)
+    k, s = 16, 8
+    a = _run(ds, A, k, s, 6, 1e-2, use_graph=1)
+    b = _run(ds, A, k, s, 6, 1e-2, use_graph=0)
+    assert a[3].passes == b[3].passes
+    np.testing.assert_allclose(a[1], b[1], rtol=1e-5)
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_forced_spmm_variants(ds, variant):
+    A, prm = datagen.make_config(3, scale=0.005)
+    k, s = 12, 6
+    U, S, V, info, _ = _run(ds, A, k, s, 2, 0.0, spmm_variant=variant)
+    ref = oracle.dashsvd(A.to_scipy(), k, s, p_max=2, tol=0.0, seed=0x5EED)
+    _compare(U, S, V, ref, k)
+
+
+def test_modes_match_oracle(ds):
+    A, prm = datagen.make_config(1, scale=0.05)
+    k, s = 8, 4
+    for opts, ref_kw in [({"alpha_prev_mode": 1}, {"alpha_prev_mode": 1}), ({"shift": 0}, {"shift": False})]:
+        U, S, V, info, _ = _run(ds, A, k, s, 8, 1e-3, **opts)
+        ref = oracle.dashsvd(A.to_scipy(), k, s, p_max=8, tol=1e-3, seed=0x5EED, **ref_kw)
+        assert abs(info.passes - ref.passes) <= 1
+        if info.passes == ref.passes:
+            _compare(U, S, V, ref, k)
+
+
+def test_per_pass_invariants(ds):
+    """Prop. 1 (0 <= alpha <= sigma_l^2 / 2, non-decreasing) and the upper half of
+    Prop. 3 (sqrt(Shat_i + alpha) <= sigma_i(A)) on every pass of the GPU run."""
+    A, _ = datagen.make_config(2, scale=0.002)
+    k, s = 10, 5
+    l = k + s
+    sv = np.linalg.svd(A.to_dense(), compute_uv=False)
+    _, S, _, info, tr = _run(ds, A, k, s, 8, 0.0, record_trace=1)
+    assert len(tr) == 8
+    prev = 0.0
+    for j, a_used, ratio, a_next, Sh in tr:
+        assert 0.0 <= a_used <= sv[l - 1] ** 2 / 2 * (1 + 1e-4)
+        assert a_used >= prev and a_next >= a_used
+        prev = a_used
+        assert np.all(np.sqrt(Sh + a_used) <= sv[:l] * (1 + 1e-4))
+    assert np.all(S <= sv[:k] * (1 + 1e-5))
+
+
+def test_edge_cases(ds):
+    import torch
+
+    # full width l = n: exact SVD
+    rng = np.random.default_rng(0)
+    M = sp.random(300, 24, density=0.3, random_state=rng, format="csr", dtype=np.float32)
+    A = datagen.Csr(300, 24, M.indptr.astype(np.int32), M.indices.astype(np.int32), M.data.astype(np.float32))
+    U, S, V, info, _ = _run(ds, A, 16, 8, 1, 0.0)
+    sv = np.linalg.svd(M.toarray().astype(np.float64), compute_uv=False)
+    np.testing.assert_allclose(S, sv[:16], rtol=1e-5)
+    # k = 1, s = 1; empty rows and columns present
+    A2, _ = datagen.make_config(2, scale=0.002)
+    U, S, V, info, _ = _run(ds, A2, 1, 1, 3, 0.0)
+    ref = oracle.dashsvd(A2.to_scipy(), 1, 1, p_max=3, tol=0.0, seed=0x5EED)
+    np.testing.assert_allclose(S, ref.S, rtol=1e-4)
+    # argument errors and unsupported sizes
+    Ad = ds.CsrDevice.from_host(A2)
+    with ds.Handle() as h:
+        for k, s in [(0, 5), (5, 0), (A2.n, 1)]:
+            with pytest.raises(ds.DashSvdError) as ei:
+                h.run(Ad, k, s, 2, 0.0)
+            assert ei.value.status == ds.DASHSVD_EINVAL
+        with pytest.raises(ds.DashSvdError) as ei:
+            h.run(Ad, 200, 57, 2, 0.0)
+        assert ei.value.status == ds.DASHSVD_EINVAL
+    torch.cuda.synchronize()
+
+
+def test_nonfinite_input_reported(ds):
+    A, _ = datagen.make_config(1, scale=0.05)
+    A.val = A.val.copy()
+    A.val[5] = np.nan
+    import paper_2404_09276_gb300 as mod
+
+    with mod.Handle() as h:
+        with pytest.raises(mod.DashSvdError) as ei:
+            h.run(mod.CsrDevice.from_host(A), 5, 3, 2, 0.0)
+    assert ei.value.status == mod.DASHSVD_ENONFINITE
