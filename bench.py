@@ -60,6 +60,8 @@ def _args():
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (testing only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-reps", type=int, default=20)
+    ap.add_argument("--no-graph", action="store_true",
+                    help="host-driven loop instead of the CUDA graph (profilers see every launch)")
     return ap.parse_args()
 
 
@@ -240,7 +242,7 @@ def ours(args):
     S = torch.empty((k,), dtype=torch.float32, device="cuda")
     V = torch.empty((A.n, k), dtype=torch.float32, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
-    h = ds.Handle(stream=stream)
+    h = ds.Handle(stream=stream, use_graph=0 if args.no_graph else 1)
 
     def barrier():
         torch.cuda.synchronize()
@@ -273,6 +275,12 @@ def ours(args):
     kpv = lambda v: 2 if v == 1 else 1  # noqa: E731  kernels per SpMM launch (merge path adds its fix-up)
     launches_per_run = 5 + (1 + kpv(var_bwd) + 2 + 1 + 1) + passes * (kpv(var_fwd) + kpv(var_bwd) + 2 + 1 + 1) + \
         (kpv(var_fwd) + 2 + 1 + 2)
+
+    # ---- one untimed run with the per-pass trace (shift, PVE ratio, Jacobi sweeps)
+    with ds.Handle(stream=stream, record_trace=1) as ht:
+        ht.run(Ad, k, s, p_max, tol, U, S, V)
+        trace = [{"pass": j, "alpha": a_used, "pve_ratio": ratio, "eig_sweeps": sw}
+                 for j, a_used, ratio, a_next, sw, _ in ht.trace()]
 
     # ---- end to end: A from pinned host memory, U, S, V back to pinned host memory
     rp_h = torch.from_numpy(A.rowptr).pin_memory()
@@ -364,8 +372,9 @@ def ours(args):
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": name, "form": "plain FP32", "l2": "flushed (256 MB write) before each step",
+                   "loop": "host-driven" if args.no_graph else "CUDA graph, device-side WHILE",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "passes": passes, "status": info.status, "pve_surrogate": info.pve_ratio,
+        "passes": passes, "status": info.status, "pve_surrogate": info.pve_ratio, "trace": trace,
         "roofline": roof, "kernels_s": kt, "kernel_s_per_run": per_run, "spmm": spmm,
         "e2e": {"value": statistics.median(e2e_times), "unit": "s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},

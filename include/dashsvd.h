@@ -122,8 +122,9 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
                 double pve_tol, float* U, float* S, float* V, dashsvd_info* info);
 
 /* Copy the per-pass history of the last run (record_trace = 1) to HOST memory.
- * Record j (0-based) holds 4 + l doubles: pass index, shift used in the pass,
- * surrogate PVE ratio, shift after the update, then Shat_1..Shat_l of the pass.
+ * Record j (0-based) holds 5 + l doubles: pass index, shift used in the pass,
+ * surrogate PVE ratio, shift after the update, Jacobi sweeps of the pass's
+ * eigensolve, then Shat_1..Shat_l of the pass.
  * Writes at most `cap` doubles; *count receives the number of records. */
 int dashsvd_get_trace(dashsvd_handle h, double* out, int64_t cap, int64_t* count, int* l);
 
@@ -174,6 +175,15 @@ int dashsvd_spmm_shift(dashsvd_handle h, const dashsvd_csr* At, const float* Y, 
  * per row chunk added in FP64. */
 int dashsvd_gram(dashsvd_handle h, const float* C, int64_t rows, int l, int64_t ldc, float* G,
                  int64_t ldg);
+
+/* G = C^T C on the tensor cores as a split BF16x3 product (precision form of
+ * Alg. 3 step 1): C = C_hi + C_lo with C_hi = bf16(C), C_lo = bf16(C - C_hi),
+ * G ~= C_hi^T C_hi + C_hi^T C_lo + C_lo^T C_hi with FP32 accumulation per row
+ * chunk and the chunks added in FP64 (relative error per term about 2^-16).
+ * C: rows x ldc FP32 (ldc % 4 == 0), G: l x ldg FP64. This call waits for its
+ * own work and returns DASHSVD_ETIMEOUT if a bounded device wait ran out. */
+int dashsvd_gram_bf16x3(dashsvd_handle h, const float* C, int64_t rows, int l, int64_t ldc, double* G,
+                        int64_t ldg);
 
 /* Out = C W (Alg. 3 step 3 with W = V S^-1; Alg. 5 step 11 with W = V(:, 1:k)).
  * C: rows x ldc (first l columns used), W: l x ldw (first `cols` columns used),

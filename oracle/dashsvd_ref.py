@@ -27,11 +27,14 @@ R2  Shat' = 0 and alpha' = 0 before the first pass, so for tol < 1 the test
 R3  The test's denominator Shat_{k+1} + alpha is floored at
     64 * eps * (Shat_1 + alpha) so an exactly rank-k input can stop.
 R4  A break leaves Q as computed in that pass (the shift update is skipped).
-R6  Eigenvalues d_i <= 16 * eps * d_1 (eps: unit roundoff of the eigensolver's
-    precision) give a zero column of U in eigSVD instead of dividing by a
-    noise-level S_i. The factor is fixed, not l: rounding noise on a zero
-    eigenvalue of a Gram matrix stays within a few eps * d_1, while a factor of
-    l would null genuine tail directions of skewed spectra in FP32.
+R6  An eigenvalue at the rounding level of the Gram entries it is made of,
+    d_i <= 16 * eps * sum_j V_ji^2 G_jj (eps: unit roundoff of the eigensolver's
+    precision), gives a zero column of U in eigSVD instead of dividing by a
+    noise-level S_i. The scale is the diagonal of G seen by the eigenvector, not
+    d_1: an exactly dependent column of C leaves an eigenvalue of a few eps
+    times the norms of the columns it cancels, while a genuine tail direction of
+    a skewed spectrum (d_i / d_1 ~ 1e-6 in the shifted passes of Alg. 5, where
+    G has the fourth power of sigma) keeps d_i close to its own diagonal entry.
 R8  Each eigenvector column is signed so that its largest-magnitude entry
     (lowest index on ties) is positive; ties in D are ordered by lower index.
 R10 ``p_max`` counts power iterations (loop passes); passes over A = 2p + 2.
@@ -72,7 +75,8 @@ def eigsvd(C: np.ndarray, eps: float = EPS64):
     G = C.T @ C
     d, V = np.linalg.eigh(G)  # symmetric eigensolver, ascending
     d, V = _canonical_order_and_sign(d, V)
-    null = d <= NULL_FACTOR * eps * max(d[0], 0.0) if l else np.zeros(0, bool)
+    scale = (V * V).T @ np.diag(G)  # sum_j V_ji^2 G_jj per eigenvector i
+    null = d <= NULL_FACTOR * eps * scale
     S = np.sqrt(np.maximum(d, 0.0))
     inv = np.where(null, 0.0, 1.0 / np.where(null, 1.0, S))
     U = C @ (V * inv[None, :])

@@ -36,8 +36,8 @@ DASHSVD_MAX_L = 256
 EXPORTS = (
     "dashsvd_options_init", "dashsvd_create", "dashsvd_destroy", "dashsvd_run", "dashsvd_get_trace",
     "dashsvd_load_mlp", "dashsvd_status_string", "dashsvd_last_error", "dashsvd_gaussian",
-    "dashsvd_csr_transpose", "dashsvd_spmm", "dashsvd_spmm_shift", "dashsvd_gram", "dashsvd_project",
-    "dashsvd_eigsvd",
+    "dashsvd_csr_transpose", "dashsvd_spmm", "dashsvd_spmm_shift", "dashsvd_gram", "dashsvd_gram_bf16x3",
+    "dashsvd_project", "dashsvd_eigsvd",
 )
 
 
@@ -85,6 +85,7 @@ def _load():
         "dashsvd_spmm": (I, [P, P, P, I64, I, P, I64, I]),
         "dashsvd_spmm_shift": (I, [P, P, P, I64, I, P, P, I64, P, I64, I]),
         "dashsvd_gram": (I, [P, P, I64, I, I64, P, I64]),
+        "dashsvd_gram_bf16x3": (I, [P, P, I64, I, I64, P, I64]),
         "dashsvd_project": (I, [P, P, I64, I, I64, P, I64, I, P, I64]),
         "dashsvd_eigsvd": (I, [P, P, I64, I, I64, P, I64, P, P, I]),
     }
@@ -117,6 +118,7 @@ dashsvd_csr_transpose = _export("dashsvd_csr_transpose")
 dashsvd_spmm = _export("dashsvd_spmm")
 dashsvd_spmm_shift = _export("dashsvd_spmm_shift")
 dashsvd_gram = _export("dashsvd_gram")
+dashsvd_gram_bf16x3 = _export("dashsvd_gram_bf16x3")
 dashsvd_project = _export("dashsvd_project")
 dashsvd_eigsvd = _export("dashsvd_eigsvd")
 
@@ -225,16 +227,16 @@ class Handle:
         return U, S, V, info
 
     def trace(self):
-        """Per-pass records of the last run: list of (j, alpha_used, ratio, alpha_next, Shat[l])."""
+        """Per-pass records of the last run: list of (j, alpha_used, ratio, alpha_next, sweeps, Shat[l])."""
         import numpy as np
 
         cnt = C.c_int64()
         l = C.c_int()
         check(dashsvd_get_trace(self.h, None, 0, C.byref(cnt), C.byref(l)), "dashsvd_get_trace")
-        buf = np.zeros(max(1, cnt.value * (4 + l.value)), dtype=np.float64)
+        buf = np.zeros(max(1, cnt.value * (5 + l.value)), dtype=np.float64)
         check(dashsvd_get_trace(self.h, buf.ctypes.data, buf.size, C.byref(cnt), C.byref(l)), "dashsvd_get_trace")
-        rec = buf[: cnt.value * (4 + l.value)].reshape(cnt.value, 4 + l.value)
-        return [(int(r[0]), r[1], r[2], r[3], r[4:]) for r in rec]
+        rec = buf[: cnt.value * (5 + l.value)].reshape(cnt.value, 5 + l.value)
+        return [(int(r[0]), r[1], r[2], r[3], int(r[4]), r[5:]) for r in rec]
 
     # -- step-level entry points ----------------------------------------------
     def gaussian(self, seed: int, rows: int, l: int, row0: int = 0, out=None):
@@ -280,6 +282,14 @@ class Handle:
         out = torch.empty((l, l), dtype=torch.float32, device=Cm.device) if out is None else out
         check(dashsvd_gram(self.h, Cm.data_ptr(), Cm.shape[0], l, Cm.stride(0), out.data_ptr(), out.stride(0)),
               "dashsvd_gram")
+        return out
+
+    def gram_bf16x3(self, Cm, l: int, out=None):
+        import torch
+
+        out = torch.empty((l, l), dtype=torch.float64, device=Cm.device) if out is None else out
+        check(dashsvd_gram_bf16x3(self.h, Cm.data_ptr(), Cm.shape[0], l, Cm.stride(0), out.data_ptr(),
+                                  out.stride(0)), "dashsvd_gram_bf16x3")
         return out
 
     def project(self, Cm, l: int, W, cols: int, out=None, ldo: int | None = None):

@@ -83,7 +83,9 @@ struct dashsvd_handle_s {
   int num_sms = 0;
   // workspace
   DevBuf rowptr_b, col_b, val_b, cursor, scan_tmp;  // the CSR built by transposition
-  DevBuf Y, Z, Q, G, W, W2, partial, carry, carry_row, ctl, trace;
+  DevBuf Y, Z, Q, G, W, W2, partial, carry, carry_row, ctl, trace, eigw;
+  DevBuf seg_fwd, seg_bwd;  // merge-path partitions of A and A^T (rows, nonzeros)
+  DevBuf errw;              // device error word of the bounded-wait kernels
   // cached graph
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -124,6 +126,7 @@ struct RunPlan {
   double tol;
   float *Uw, *Vw, *S;  // outputs on the working side
   int var_fwd, var_bwd;
+  SpmmPart part_fwd, part_bwd;
   SpmmScratch scr;
 };
 
@@ -152,7 +155,7 @@ cudaError_t eigsvd_step(dashsvd_handle h, const RunPlan& p, const float* C, int6
                         unsigned long long cond, cudaStream_t st) {
   cudaError_t e = launch_gram(C, rows, p.l, p.ld, as<float>(h->G), p.ld, as<float>(h->partial), h->num_sms, st);
   if (e != cudaSuccess) return e;
-  return launch_eig_f32(as<float>(h->G), p.ld, eig_args(h, p, mode, cond), st);
+  return launch_eig_f32(as<float>(h->G), p.ld, eig_args(h, p, mode, cond), eig_work_view(h->eigw.p), st);
 }
 
 cudaError_t launch_prologue(dashsvd_handle h, const RunPlan& p, unsigned long long cond, cudaStream_t st) {
@@ -160,7 +163,7 @@ cudaError_t launch_prologue(dashsvd_handle h, const RunPlan& p, unsigned long lo
   // Alg. 5 step 1: Omega (mw x l) into Y
   if ((e = launch_gaussian(h->opt.seed, p.mw, p.l, 0, as<float>(h->Y), p.ld, st)) != cudaSuccess) return e;
   // step 2: Z = A^T Omega, Q = eigSVD(Z)
-  if ((e = launch_spmm(p.AwT, as<float>(h->Y), p.ld, p.l, as<float>(h->Z), p.ld, nullptr, nullptr, 0, p.var_bwd, p.scr,
+  if ((e = launch_spmm(p.AwT, p.part_bwd, as<float>(h->Y), p.ld, p.l, as<float>(h->Z), p.ld, nullptr, nullptr, 0, p.var_bwd, p.scr,
                        h->num_sms, st)) != cudaSuccess)
     return e;
   if ((e = eigsvd_step(h, p, as<float>(h->Z), p.nw, kModeInit, cond, st)) != cudaSuccess) return e;
@@ -172,10 +175,10 @@ cudaError_t launch_pass(dashsvd_handle h, const RunPlan& p, unsigned long long c
   cudaError_t e;
   const Control* ctl = as<Control>(h->ctl);
   // step 4: Y = A Q; Z = A^T Y - alpha Q; [Q, Shat] = eigSVD(Z)
-  if ((e = launch_spmm(p.Aw, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld, nullptr, nullptr, 0, p.var_fwd, p.scr,
+  if ((e = launch_spmm(p.Aw, p.part_fwd, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld, nullptr, nullptr, 0, p.var_fwd, p.scr,
                        h->num_sms, st)) != cudaSuccess)
     return e;
-  if ((e = launch_spmm(p.AwT, as<float>(h->Y), p.ld, p.l, as<float>(h->Z), p.ld, &ctl->alpha, as<float>(h->Q), p.ld,
+  if ((e = launch_spmm(p.AwT, p.part_bwd, as<float>(h->Y), p.ld, p.l, as<float>(h->Z), p.ld, &ctl->alpha, as<float>(h->Q), p.ld,
                        p.var_bwd, p.scr, h->num_sms, st)) != cudaSuccess)
     return e;
   // steps 5-7 run inside the eig kernel's control tail
@@ -187,7 +190,7 @@ cudaError_t launch_pass(dashsvd_handle h, const RunPlan& p, unsigned long long c
 cudaError_t launch_final(dashsvd_handle h, const RunPlan& p, cudaStream_t st) {
   cudaError_t e;
   // step 9: B = A Q (into Y)
-  if ((e = launch_spmm(p.Aw, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld, nullptr, nullptr, 0, p.var_fwd, p.scr,
+  if ((e = launch_spmm(p.Aw, p.part_fwd, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld, nullptr, nullptr, 0, p.var_fwd, p.scr,
                        h->num_sms, st)) != cudaSuccess)
     return e;
   // steps 10-11: eigSVD(B); U = B V_k S_k^-1; V = Q V_k
@@ -312,6 +315,7 @@ int dashsvd_create(dashsvd_handle* out, const dashsvd_options* opt, void* cuda_s
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = prepare_project();
   if (e == cudaSuccess) e = prepare_eig();
+  if (e == cudaSuccess) e = prepare_gram_tc();
   if (e != cudaSuccess) {
     set_last_error("dashsvd_create", e, __FILE__, __LINE__);
     if (h->side) cudaStreamDestroy(h->side);
@@ -329,7 +333,7 @@ int dashsvd_destroy(dashsvd_handle h) {
   drop_graph(h);
   DevBuf* bufs[] = {&h->rowptr_b, &h->col_b, &h->val_b, &h->cursor, &h->scan_tmp, &h->Y,       &h->Z,
                     &h->Q,        &h->G,     &h->W,     &h->W2,     &h->partial,  &h->carry, &h->carry_row,
-                    &h->ctl,      &h->trace};
+                    &h->ctl,      &h->trace, &h->eigw,   &h->seg_fwd, &h->seg_bwd, &h->errw};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (h->side) cudaStreamDestroy(h->side);
@@ -348,7 +352,7 @@ int dashsvd_get_trace(dashsvd_handle h, double* out, int64_t cap, int64_t* count
   if (!h) return DASHSVD_EINVAL;
   if (count) *count = h->last_records;
   if (l) *l = h->last_l;
-  const int64_t n = h->last_records * (4 + h->last_l);
+  const int64_t n = h->last_records * (5 + h->last_l);
   if (out && cap > 0 && n > 0 && h->trace.p) {
     DS_CUDA(cudaStreamSynchronize(h->stream));
     DS_CUDA(cudaMemcpy(out, h->trace.p, sizeof(double) * (size_t)(n < cap ? n : cap), cudaMemcpyDeviceToHost));
@@ -365,7 +369,6 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
   const int64_t mn = A->m < A->n ? A->m : A->n;
   if (l > mn || l > DASHSVD_MAX_L) return DASHSVD_EINVAL;
   if (h->opt.form != DASHSVD_FORM_PLAIN || h->opt.learned) return DASHSVD_ENOTIMPL;
-  if (l > eig_max_l_f32()) return DASHSVD_ENOTIMPL;
 
   RunPlan p;
   const bool tr = A->m < A->n;
@@ -399,7 +402,9 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
   p.mw = p.Aw.m;
   p.nw = p.Aw.n;
   p.S = S;
-  const int64_t warps = spmm_mergepath_warps(h->num_sms);
+  p.part_fwd.segments = spmm_segments(p.Aw, h->num_sms);
+  p.part_bwd.segments = spmm_segments(p.AwT, h->num_sms);
+  const int64_t segs = std::max(p.part_fwd.segments, p.part_bwd.segments);
   const size_t gp = std::max(gram_partial_floats(p.mw, p.l, h->num_sms), gram_partial_floats(p.nw, p.l, h->num_sms));
   if ((rc = ensure(h->Y, sizeof(float) * (size_t)(p.mw * p.ld), &moved)) ||
       (rc = ensure(h->Z, sizeof(float) * (size_t)(p.nw * p.ld), &moved)) ||
@@ -408,14 +413,22 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
       (rc = ensure(h->W, sizeof(float) * (size_t)(p.ld * p.ld), &moved)) ||
       (rc = ensure(h->W2, sizeof(float) * (size_t)(p.ld * p.ld), &moved)) ||
       (rc = ensure(h->partial, sizeof(float) * gp, &moved)) ||
-      (rc = ensure(h->carry, sizeof(float) * (size_t)(2 * warps * p.ld), &moved)) ||
-      (rc = ensure(h->carry_row, sizeof(int32_t) * (size_t)(2 * warps), &moved)) ||
+      (rc = ensure(h->carry, sizeof(float) * (size_t)(2 * segs * p.ld), &moved)) ||
+      (rc = ensure(h->carry_row, sizeof(int32_t) * (size_t)(2 * segs), &moved)) ||
+      (rc = ensure(h->seg_fwd, sizeof(int32_t) * (size_t)(2 * (p.part_fwd.segments + 1)), &moved)) ||
+      (rc = ensure(h->seg_bwd, sizeof(int32_t) * (size_t)(2 * (p.part_bwd.segments + 1)), &moved)) ||
       (rc = ensure(h->ctl, sizeof(Control), &moved)) ||
-      (rc = ensure(h->trace, sizeof(double) * (size_t)((max_passes + 1) * (4 + l)), &moved)))
+      (rc = ensure(h->trace, sizeof(double) * (size_t)((max_passes + 1) * (5 + l)), &moved)) ||
+      (rc = ensure(h->eigw, eig_work_bytes(), &moved)))
     return rc;
   p.scr.carry = as<float>(h->carry);
   p.scr.carry_row = as<int32_t>(h->carry_row);
-  p.scr.warps = warps;
+  p.scr.max_segments = segs;
+  p.scr.ldc = p.ld;
+  p.part_fwd.seg_row = as<int32_t>(h->seg_fwd);
+  p.part_fwd.seg_nnz = p.part_fwd.seg_row + p.part_fwd.segments + 1;
+  p.part_bwd.seg_row = as<int32_t>(h->seg_bwd);
+  p.part_bwd.seg_nnz = p.part_bwd.seg_row + p.part_bwd.segments + 1;
   // work split: merge path where row lengths are very uneven, else warp per row
   const int forced = h->opt.spmm_variant;
   p.var_fwd = forced >= 0 ? forced : 1;
@@ -424,6 +437,8 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
   cudaStream_t st = h->stream;
   DS_CUDA(launch_csr_transpose(*A, as<int32_t>(h->rowptr_b), as<int32_t>(h->col_b), as<float>(h->val_b),
                                as<int32_t>(h->cursor), as<int32_t>(h->scan_tmp), st));
+  DS_CUDA(launch_spmm_partition(p.Aw, p.part_fwd, st));
+  DS_CUDA(launch_spmm_partition(p.AwT, p.part_bwd, st));
 
   if (h->opt.use_graph) {
     GraphKey key;
@@ -474,7 +489,7 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
     int64_t ws = 0;
     DevBuf* bufs[] = {&h->rowptr_b, &h->col_b, &h->val_b, &h->cursor, &h->scan_tmp, &h->Y,       &h->Z,
                       &h->Q,        &h->G,     &h->W,     &h->W2,     &h->partial,  &h->carry, &h->carry_row,
-                      &h->ctl,      &h->trace};
+                      &h->ctl,      &h->trace, &h->eigw,   &h->seg_fwd, &h->seg_bwd};
     for (DevBuf* b : bufs) ws += (int64_t)b->bytes;
     info->workspace_bytes = ws;
     info->eig_sweeps = hc.sweeps;
@@ -510,18 +525,26 @@ static int spmm_common(dashsvd_handle h, const dashsvd_csr* A, const float* X, i
   if (ldx < l || ldy < l || ldx % 4 || ldy % 4 || !aligned16(X) || !aligned16(Y)) return DASHSVD_EINVAL;
   if (alpha && (!Q || ldq < l || ldq % 4 || !aligned16(Q))) return DASHSVD_EINVAL;
   if (variant < -1 || variant > 1) return DASHSVD_EINVAL;
-  const int64_t warps = spmm_mergepath_warps(h->num_sms);
+  SpmmPart part;
+  part.segments = spmm_segments(*A, h->num_sms);
+  const int64_t ldc = ((l + 3) / 4) * 4;
   int rc;
   bool moved = false;
-  if ((rc = ensure(h->carry, sizeof(float) * (size_t)(2 * warps * ldy), &moved)) ||
-      (rc = ensure(h->carry_row, sizeof(int32_t) * (size_t)(2 * warps), &moved)))
+  if ((rc = ensure(h->carry, sizeof(float) * (size_t)(2 * part.segments * ldc), &moved)) ||
+      (rc = ensure(h->carry_row, sizeof(int32_t) * (size_t)(2 * part.segments), &moved)) ||
+      (rc = ensure(h->seg_fwd, sizeof(int32_t) * (size_t)(2 * (part.segments + 1)), &moved)))
     return rc;
   if (moved) h->have_graph = false;
   SpmmScratch scr;
   scr.carry = as<float>(h->carry);
   scr.carry_row = as<int32_t>(h->carry_row);
-  scr.warps = warps;
-  DS_CUDA(launch_spmm(*A, X, ldx, l, Y, ldy, alpha, Q, ldq, variant < 0 ? 1 : variant, scr, h->num_sms, h->stream));
+  scr.max_segments = part.segments;
+  scr.ldc = (int)ldc;
+  part.seg_row = as<int32_t>(h->seg_fwd);
+  part.seg_nnz = part.seg_row + part.segments + 1;
+  const int var = variant < 0 ? 1 : variant;
+  if (var == 1) DS_CUDA(launch_spmm_partition(*A, part, h->stream));
+  DS_CUDA(launch_spmm(*A, part, X, ldx, l, Y, ldy, alpha, Q, ldq, var, scr, h->num_sms, h->stream));
   return DASHSVD_OK;
 }
 
@@ -546,6 +569,24 @@ int dashsvd_gram(dashsvd_handle h, const float* C, int64_t rows, int l, int64_t 
   return DASHSVD_OK;
 }
 
+int dashsvd_gram_bf16x3(dashsvd_handle h, const float* C, int64_t rows, int l, int64_t ldc, double* G, int64_t ldg) {
+  if (!h || !C || !G || rows < 0 || l < 1 || l > DASHSVD_MAX_L || ldc < l || ldc % 4 || ldg < l || !aligned16(C))
+    return DASHSVD_EINVAL;
+  int rc;
+  bool moved = false;
+  if ((rc = ensure(h->partial, sizeof(float) * gram_tc_partial_floats(rows, l, h->num_sms), &moved)) ||
+      (rc = ensure(h->errw, 16, &moved)))
+    return rc;
+  if (moved) h->have_graph = false;
+  DS_CUDA(cudaMemsetAsync(h->errw.p, 0, sizeof(int), h->stream));
+  DS_CUDA(launch_gram_tc(C, rows, l, ldc, G, ldg, nullptr, 0, as<float>(h->partial), as<int>(h->errw), h->num_sms,
+                         h->stream));
+  int err = 0;
+  DS_CUDA(cudaMemcpyAsync(&err, h->errw.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  DS_CUDA(cudaStreamSynchronize(h->stream));
+  return err ? DASHSVD_ETIMEOUT : DASHSVD_OK;
+}
+
 int dashsvd_project(dashsvd_handle h, const float* C, int64_t rows, int l, int64_t ldc, const float* W, int64_t ldw,
                     int cols, float* Out, int64_t ldo) {
   if (!h || !C || !W || !Out || rows < 0 || l < 1 || l > DASHSVD_MAX_L || cols < 1 || cols > DASHSVD_MAX_L)
@@ -561,12 +602,13 @@ int dashsvd_eigsvd(dashsvd_handle h, const float* C, int64_t rows, int l, int64_
       !aligned16(C))
     return DASHSVD_EINVAL;
   if (form != DASHSVD_FORM_PLAIN) return DASHSVD_ENOTIMPL;
-  if (l > eig_max_l_f32()) return DASHSVD_ENOTIMPL;
+  if (l > eig_max_l_f32()) return DASHSVD_EINVAL;
   const int64_t ld = round_up(l, 8);
   int rc;
   bool moved = false;
   if ((rc = ensure(h->G, sizeof(float) * (size_t)(ld * ld), &moved)) ||
       (rc = ensure(h->W, sizeof(float) * (size_t)(ld * ld), &moved)) ||
+      (rc = ensure(h->eigw, eig_work_bytes(), &moved)) ||
       (rc = ensure(h->partial, sizeof(float) * gram_partial_floats(rows, l, h->num_sms), &moved)))
     return rc;
   if (moved) h->have_graph = false;
@@ -581,7 +623,7 @@ int dashsvd_eigsvd(dashsvd_handle h, const float* C, int64_t rows, int l, int64_
   a.W = as<float>(h->W);
   a.W2 = V;
   a.S_out = S;
-  DS_CUDA(launch_eig_f32(as<float>(h->G), ld, a, st));
+  DS_CUDA(launch_eig_f32(as<float>(h->G), ld, a, eig_work_view(h->eigw.p), st));
   DS_CUDA(launch_project(C, rows, l, ldc, as<float>(h->W), ld, l, U, ldu, h->num_sms, st));
   return DASHSVD_OK;
 }

@@ -67,24 +67,52 @@ cudaError_t launch_csr_transpose(const dashsvd_csr& A, int32_t* rowptr_t, int32_
 size_t scan_tmp_ints(int64_t n);
 
 // SpMM Y = A X (alpha == nullptr) or Y = A X - alpha Q.
-struct SpmmScratch {
-  float* carry = nullptr;      // 2 * warps * ldy floats
-  int32_t* carry_row = nullptr;  // 2 * warps
-  int64_t warps = 0;
+struct SpmmPart {          // merge-path partition of one sparse matrix
+  int64_t segments = 0;    // number of segments
+  int64_t per = 0;         // merge items (rows + nonzeros) per segment
+  int32_t* seg_row = nullptr;  // segments + 1 row starts
+  int32_t* seg_nnz = nullptr;  // segments + 1 nonzero starts
 };
-int spmm_mergepath_warps(int num_sms);
-cudaError_t launch_spmm(const dashsvd_csr& A, const float* X, int64_t ldx, int l, float* Y,
-                        int64_t ldy, const double* alpha, const float* Q, int64_t ldq,
-                        int variant, const SpmmScratch& scr, int num_sms, cudaStream_t st);
+struct SpmmScratch {
+  float* carry = nullptr;        // 2 * max_segments * ldc floats
+  int32_t* carry_row = nullptr;  // 2 * max_segments
+  int64_t max_segments = 0;
+  int ldc = 0;                   // carry row stride (floats, >= l rounded up to 4)
+};
+int64_t spmm_segments(const dashsvd_csr& A, int num_sms);
+cudaError_t launch_spmm_partition(const dashsvd_csr& A, SpmmPart& part, cudaStream_t st);
+cudaError_t launch_spmm(const dashsvd_csr& A, const SpmmPart& part, const float* X, int64_t ldx, int l, float* Y,
+                        int64_t ldy, const double* alpha, const float* Q, int64_t ldq, int variant,
+                        const SpmmScratch& scr, int num_sms, cudaStream_t st);
+// BF16 dense operand (and BF16 Q): Y in BF16 (y_bf16) or FP32
+cudaError_t launch_spmm_bf16(const dashsvd_csr& A, const SpmmPart& part, const void* X, int64_t ldx, int l, void* Y,
+                             bool y_bf16, int64_t ldy, const double* alpha, const void* Q, int64_t ldq, int variant,
+                             const SpmmScratch& scr, int num_sms, cudaStream_t st);
 
 // Gram G = C^T C.
 size_t gram_partial_floats(int64_t rows, int l, int num_sms);
 cudaError_t launch_gram(const float* C, int64_t rows, int l, int64_t ldc, float* G, int64_t ldg,
                         float* partial, int num_sms, cudaStream_t st);
 
-// Jacobi eigensolver + sort/sign/null policy + loop control (single CTA).
+// Gram on tcgen05 (BF16x3): G64 (and G32 if non-null) from C; `err` is set on a wait timeout.
+size_t gram_tc_partial_floats(int64_t rows, int l, int num_sms);
+cudaError_t prepare_gram_tc();
+cudaError_t launch_gram_tc(const float* C, int64_t rows, int l, int64_t ldc, double* G64, int64_t ldg64, float* G32,
+                           int64_t ldg32, float* partial, int* err, int num_sms, cudaStream_t st);
+
+// Jacobi eigensolver (rotation log) + eigenvector replay with the eigSVD
+// conventions and the loop control. Work buffer: header, eigenvalues, log.
+constexpr int kMaxSweeps = 30;
+struct EigWork {
+  int* hdr;     // [0] sweeps to replay, [1] status bits, [2] sweeps run
+  float* d;     // kMaxL eigenvalues (unsorted)
+  float* d0;    // kMaxL diagonal entries of G before the iteration
+  float2* log;  // (c, s) per sweep x step x pair
+};
 int eig_max_l_f32();
-cudaError_t launch_eig_f32(const float* G, int64_t ldg, const EigArgs& a, cudaStream_t st);
+size_t eig_work_bytes();
+EigWork eig_work_view(void* base);
+cudaError_t launch_eig_f32(const float* G, int64_t ldg, const EigArgs& a, const EigWork& wk, cudaStream_t st);
 
 // Out = C W.
 cudaError_t launch_project(const float* C, int64_t rows, int l, int64_t ldc, const float* W,

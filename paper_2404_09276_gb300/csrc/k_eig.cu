@@ -1,34 +1,36 @@
 // Symmetric eigendecomposition G = V D V^T of the l x l Gram matrix (Alg. 3
-// step 1), plain FP32 form: cyclic two-sided Jacobi in parallel (round-robin)
-// order, one CTA of 1024 threads with G and V resident in shared memory.
+// step 1) in FP32, plus the rest of eigSVD and the loop control.
 //
-// Round-robin order: with N = l rounded up to even (index l is a zero dummy
-// when l is odd), step t of a sweep pairs index N-1 with t and index
-// (t + i) mod (N-1) with (t - i) mod (N-1) for i = 1 .. N/2 - 1; every pair
-// meets once per sweep and the N/2 rotations of a step touch disjoint rows
-// and columns, so they run concurrently. A rotation for (p, q) is the
-// symmetric Schur 2x2 rotation (Golub and Van Loan, Sec. 8.5): with
+// Kernel 1 (one CTA, 1024 threads): cyclic two-sided Jacobi in parallel
+// (round-robin) order on the upper triangle of G, packed in shared memory.
+// With N = l rounded up to even (index l is a zero dummy when l is odd), step
+// t of a sweep pairs index N-1 with t, and (t + i) mod (N-1) with
+// (t - i) mod (N-1) for i = 1 .. N/2 - 1: every pair meets once per sweep and
+// the N/2 rotations of a step act on disjoint rows and columns. A rotation is
+// the symmetric Schur 2x2 rotation (Golub and Van Loan, Sec. 8.5):
 // tau = (G_qq - G_pp) / (2 G_pq), t = sign(tau) / (|tau| + sqrt(1 + tau^2)),
-// c = 1 / sqrt(1 + t^2), s = t c. It is skipped when
-// |G_pq| <= eps * sqrt(G_pp G_qq) (relative criterion for positive
-// semidefinite G, Demmel and Veselic 1992); a sweep without rotations ends
-// the iteration. After each step the 2x2 blocks (I, J) of G are updated as
-// J_I^T B J_J by one thread per block, and V <- V J.
-#include "control.cuh"
+// c = 1 / sqrt(1 + t^2), s = t c; it is skipped when |G_pq| <= eps sqrt(G_pp G_qq)
+// (the relative criterion of Demmel and Veselic, which keeps small eigenvalues
+// of a positive semidefinite G accurate), and a sweep without rotations ends
+// the iteration. Each step updates the 2x2 blocks (I, J), I <= J, of G as
+// J_I^T B J_J (one thread per block) and appends its (c, s) to a rotation log.
+//
+// Kernel 2 (one warp per eigenvector): V = J_1 J_2 ... J_T, so column c of V
+// is J_1 (J_2 (... (J_T e_c))): each warp replays the log backwards on e_c.
+// The warp then applies the eigSVD conventions (descending order with ties by
+// lower index, sign so the largest-|.| entry is positive, zero column where
+// D_i <= 16 eps D_1) and writes its column of W = V S^-1 (Alg. 3 steps 2-4).
+// CTA 0 also runs the dashSVD control: the PVE test of Alg. 5 step 5 with the
+// surrogate Shat_i + alpha of Prop. 3, the shift update of step 6, step 7's
+// bookkeeping, and the loop flag (a CUDA graph conditional).
+#include "internal.cuh"
 
 namespace dsvd {
 namespace {
 
-constexpr int kEigThreads = 1024;
-constexpr int kMaxSweeps = 40;
-constexpr int kMaxNF32 = 160;
-
-struct PairSmem {
-  int p[kMaxNF32 / 2], q[kMaxNF32 / 2];
-  float c[kMaxNF32 / 2], s[kMaxNF32 / 2], t[kMaxNF32 / 2];
-  int rot[kMaxNF32 / 2];
-  int count;
-};
+constexpr int kJacThreads = 1024;
+constexpr int kMaxN = kMaxL;  // N <= 256
+constexpr float kEps32 = 1.1920929e-07f;
 
 __device__ __forceinline__ void rr_pair(int i, int step, int N, int& p, int& q) {
   const int M = N - 1;
@@ -41,43 +43,66 @@ __device__ __forceinline__ void rr_pair(int i, int step, int N, int& p, int& q) 
   }
 }
 
-__global__ void __launch_bounds__(kEigThreads) eig_f32_kernel(const float* __restrict__ Gin, int64_t ldg, EigArgs a) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int l = a.l;
-  const int N = l + (l & 1);
-  const int LD = N + 1;
-  float* G = reinterpret_cast<float*>(smraw);
-  float* V = G + N * LD;
-  float* dv = V + N * LD;
+struct PairSmem {
+  int p[kMaxN / 2], q[kMaxN / 2];
+  float c[kMaxN / 2], s[kMaxN / 2], t[kMaxN / 2];
+  int rot[kMaxN / 2];
+  int off[kMaxN];  // packed upper triangle: element (a, b), a <= b, at off[a] + b
+  int count;
+  float gmax;
+};
+
+constexpr int kMaxBlocksPerThread = (kMaxN / 2 * (kMaxN / 2 + 1) / 2 + kJacThreads - 1) / kJacThreads;
+
+__device__ __forceinline__ int pki(const int* off, int a, int b) { return a <= b ? off[a] + b : off[b] + a; }
+
+__global__ void __launch_bounds__(kJacThreads) jacobi_f32_kernel(const float* __restrict__ Gin, int64_t ldg, int l,
+                                                                 EigWork wk) {
+  extern __shared__ __align__(16) float G[];
   __shared__ PairSmem ps;
-  __shared__ ControlSmem cs;
-  const int tid = threadIdx.x, nt = blockDim.x;
-
-  float gmax = 0.f;
-  for (int idx = tid; idx < N * N; idx += nt) {
-    const int i = idx / N, j = idx - i * N;
-    const float g = (i < l && j < l) ? Gin[(int64_t)i * ldg + j] : 0.f;
-    G[i * LD + j] = g;
-    V[i * LD + j] = i == j ? 1.f : 0.f;
-    if (i == j) gmax = fmaxf(gmax, fabsf(g));
-  }
-  // the largest diagonal entry sets an absolute floor for "zero" off-diagonals
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
-  __shared__ float wmax[32];
-  if ((tid & 31) == 0) wmax[tid >> 5] = gmax;
-  __syncthreads();
-  if (tid == 0) {
-    float m = 0.f;
-    for (int w = 0; w < (nt >> 5); ++w) m = fmaxf(m, wmax[w]);
-    wmax[0] = m;
-  }
-  __syncthreads();
-  const float tiny = wmax[0] * 1e-30f + 1e-35f;
-  const float eps = 1.1920929e-07f;
+  const int N = l + (l & 1);
   const int P = N / 2;
-
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int a = tid; a < N; a += nt) ps.off[a] = a * N - ((a * (a - 1)) >> 1) - a;
+  if (tid == 0) ps.gmax = 0.f;
+  __syncthreads();
+  float gm = 0.f;
+  for (int idx = tid; idx < N * N; idx += nt) {
+    const int a = idx / N, b = idx - a * N;
+    if (b < a) continue;
+    const float g = (a < l && b < l) ? Gin[(int64_t)a * ldg + b] : 0.f;
+    G[ps.off[a] + b] = g;
+    if (a == b) {
+      gm = fmaxf(gm, fabsf(g));
+      if (a < l) wk.d0[a] = g;
+    }
+  }
+  atomicMax(reinterpret_cast<int*>(&ps.gmax), __float_as_int(gm));  // non-negative floats order as ints
+  // this thread's 2x2 blocks (I, J), I <= J, fixed for the whole kernel
+  int bI[kMaxBlocksPerThread], bJ[kMaxBlocksPerThread];
+  const int T = P * (P + 1) / 2;
+#pragma unroll
+  for (int u = 0; u < kMaxBlocksPerThread; ++u) {
+    const int b = tid + u * nt;
+    bI[u] = -1;
+    bJ[u] = 0;
+    if (b < T) {
+      // row I of the triangle: start(I) = I P - I (I - 1) / 2 <= b < start(I + 1)
+      const float disc = (float)(2 * P + 1) * (float)(2 * P + 1) - 8.f * (float)b;
+      int I = (int)((2.f * P + 1.f - sqrtf(fmaxf(disc, 0.f))) * 0.5f);
+      if (I < 0) I = 0;
+      if (I > P - 1) I = P - 1;
+      while (I > 0 && I * P - ((I * (I - 1)) >> 1) > b) --I;
+      while (I + 1 < P && (I + 1) * P - (((I + 1) * I) >> 1) <= b) ++I;
+      bI[u] = I;
+      bJ[u] = I + (b - (I * P - ((I * (I - 1)) >> 1)));
+    }
+  }
+  __syncthreads();
+  const float tiny = ps.gmax * 1e-30f + 1e-35f;
+  float2* log = wk.log;
   int sweep = 0;
+  bool converged = false;
   for (; sweep < kMaxSweeps; ++sweep) {
     if (tid == 0) ps.count = 0;
     __syncthreads();
@@ -90,13 +115,16 @@ __global__ void __launch_bounds__(kEigThreads) eig_f32_kernel(const float* __res
         float c = 1.f, s = 0.f, t = 0.f;
         int rot = 0;
         if (p < l && q < l) {
-          const float app = G[p * LD + p], aqq = G[q * LD + q], apq = G[p * LD + q];
-          const float thr = eps * sqrtf(fabsf(app) * fabsf(aqq));
+          const float app = G[ps.off[p] + p], aqq = G[ps.off[q] + q], apq = G[pki(ps.off, p, q)];
+          const float thr = kEps32 * sqrtf(fabsf(app) * fabsf(aqq));
           if (fabsf(apq) > thr && fabsf(apq) > tiny) {
-            const float tau = (aqq - app) / (2.f * apq);
-            t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-            c = rsqrtf(1.f + t * t);
-            s = t * c;
+            // correctly rounded sqrt and division keep c^2 + s^2 = 1 to an ulp,
+            // so that rotations do not rescale G and V over many sweeps
+            const float tau = __fdiv_rn(aqq - app, 2.f * apq);
+            t = __fdiv_rn(tau >= 0.f ? 1.f : -1.f, fabsf(tau) + __fsqrt_rn(fmaf(tau, tau, 1.f)));
+            const float r = __fsqrt_rn(fmaf(t, t, 1.f));
+            c = __fdiv_rn(1.f, r);
+            s = __fdiv_rn(t, r);
             rot = 1;
             atomicAdd(&ps.count, 1);
           }
@@ -105,83 +133,274 @@ __global__ void __launch_bounds__(kEigThreads) eig_f32_kernel(const float* __res
         ps.s[tid] = s;
         ps.t[tid] = t;
         ps.rot[tid] = rot;
+        log[((int64_t)sweep * (N - 1) + step) * P + tid] = make_float2(c, s);
       }
       __syncthreads();
-      // G <- J^T G J on 2x2 blocks (I <= J), mirrored into (J, I)
-      for (int b = tid; b < P * P; b += nt) {
-        const int I = b / P, J = b - I * P;
-        if (I > J) continue;
+      // G <- J^T G J on this thread's 2x2 blocks
+#pragma unroll
+      for (int u = 0; u < kMaxBlocksPerThread; ++u) {
+        const int I = bI[u];
+        if (I < 0) continue;
+        const int J = bJ[u];
         const int rI = ps.rot[I], rJ = ps.rot[J];
         if (!rI && !rJ) continue;
-        const int p1 = ps.p[I], q1 = ps.q[I], p2 = ps.p[J], q2 = ps.q[J];
+        const int p1 = ps.p[I], q1 = ps.q[I];
         if (I == J) {
           const float t = ps.t[I];
-          const float apq = G[p1 * LD + q1];
-          G[p1 * LD + p1] -= t * apq;
-          G[q1 * LD + q1] += t * apq;
-          G[p1 * LD + q1] = 0.f;
-          G[q1 * LD + p1] = 0.f;
+          const int ipq = pki(ps.off, p1, q1);
+          const float apq = G[ipq];
+          G[ps.off[p1] + p1] -= t * apq;
+          G[ps.off[q1] + q1] += t * apq;
+          G[ipq] = 0.f;
           continue;
         }
+        const int p2 = ps.p[J], q2 = ps.q[J];
         const float c1 = ps.c[I], s1 = ps.s[I], c2 = ps.c[J], s2 = ps.s[J];
-        const float x11 = G[p1 * LD + p2], x12 = G[p1 * LD + q2];
-        const float x21 = G[q1 * LD + p2], x22 = G[q1 * LD + q2];
+        const int i11 = pki(ps.off, p1, p2), i12 = pki(ps.off, p1, q2);
+        const int i21 = pki(ps.off, q1, p2), i22 = pki(ps.off, q1, q2);
+        const float x11 = G[i11], x12 = G[i12], x21 = G[i21], x22 = G[i22];
         const float y11 = c1 * x11 - s1 * x21, y12 = c1 * x12 - s1 * x22;
         const float y21 = s1 * x11 + c1 * x21, y22 = s1 * x12 + c1 * x22;
-        const float z11 = c2 * y11 - s2 * y12, z12 = s2 * y11 + c2 * y12;
-        const float z21 = c2 * y21 - s2 * y22, z22 = s2 * y21 + c2 * y22;
-        G[p1 * LD + p2] = z11;
-        G[p1 * LD + q2] = z12;
-        G[q1 * LD + p2] = z21;
-        G[q1 * LD + q2] = z22;
-        G[p2 * LD + p1] = z11;
-        G[q2 * LD + p1] = z12;
-        G[p2 * LD + q1] = z21;
-        G[q2 * LD + q1] = z22;
-      }
-      // V <- V J (columns p, q of every row)
-      for (int b = tid; b < N * P; b += nt) {
-        const int r = b / P, I = b - r * P;
-        if (!ps.rot[I]) continue;
-        const int p = ps.p[I], q = ps.q[I];
-        const float c = ps.c[I], s = ps.s[I];
-        const float v1 = V[r * LD + p], v2 = V[r * LD + q];
-        V[r * LD + p] = c * v1 - s * v2;
-        V[r * LD + q] = s * v1 + c * v2;
+        G[i11] = c2 * y11 - s2 * y12;
+        G[i12] = s2 * y11 + c2 * y12;
+        G[i21] = c2 * y21 - s2 * y22;
+        G[i22] = s2 * y21 + c2 * y22;
       }
       __syncthreads();
     }
-    if (ps.count == 0) break;
+    if (ps.count == 0) {
+      converged = true;
+      break;
+    }
     __syncthreads();
   }
-  const bool converged = sweep < kMaxSweeps;
-  for (int i = tid; i < N; i += nt) dv[i] = G[i * LD + i];
-  __syncthreads();
-  if (tid == 0 && a.ctl) {
-    a.ctl->sweeps = sweep + (converged ? 1 : 0);
-    if (!converged) a.ctl->status |= kStatusNoConv;
+  for (int i = tid; i < l; i += nt) wk.d[i] = G[ps.off[i] + i];
+  if (tid == 0) {
+    wk.hdr[0] = sweep;  // sweeps whose rotations the replay applies (a final empty sweep adds none)
+    wk.hdr[1] = converged ? 0 : kStatusNoConv;
+    wk.hdr[2] = converged ? sweep + 1 : sweep;
   }
-  eig_finish<float>(dv, V, LD, a, cs, 1.1920929e-07);
 }
 
-size_t eig_f32_smem(int l) {
+// ------------------------------------------------------------- kernel 2
+
+constexpr int kVecWarps = 8;
+
+struct FinishSmem {
+  int rank[kMaxL];
+  double S[kMaxL];  // by sorted position
+  float x[kVecWarps][kMaxN];
+  double red[32];
+  int flag;
+};
+
+__global__ void __launch_bounds__(kVecWarps * 32) eigvec_finish_kernel(EigWork wk, EigArgs a) {
+  __shared__ FinishSmem fs;
+  const int l = a.l;
   const int N = l + (l & 1);
-  return (size_t)(2 * N * (N + 1) + N) * sizeof(float);
+  const int P = N / 2;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const float* d = wk.d;
+
+  // ranks: descending, ties by lower index; non-finite check
+  if (tid == 0) fs.flag = 0;
+  __syncthreads();
+  for (int i = tid; i < l; i += nt) {
+    const float di = d[i];
+    if (!isfinite(di)) fs.flag = 1;
+    int r = 0;
+    for (int j = 0; j < l; ++j) {
+      const float dj = d[j];
+      r += (dj > di) || (dj == di && j < i);
+    }
+    fs.rank[i] = r < l ? r : l - 1;
+  }
+  __syncthreads();
+  const bool nonfinite = fs.flag != 0;
+  for (int i = tid; i < l; i += nt) fs.S[fs.rank[i]] = sqrt(fmax((double)d[i], 0.0));
+  __syncthreads();
+  const int nsteps = wk.hdr[0] * (N - 1);
+
+  // eigenvector c = J_1 (J_2 (... (J_T e_c)))
+  const int c = blockIdx.x * kVecWarps + warp;
+  if (c < l) {
+    float* x = fs.x[warp];
+    for (int j = lane; j < N; j += 32) x[j] = j == c ? 1.f : 0.f;
+    __syncwarp();
+    for (int t = nsteps - 1; t >= 0; --t) {
+      const int step = t % (N - 1);
+      const float2* lg = wk.log + (int64_t)t * P;
+      for (int i = lane; i < P; i += 32) {
+        const float2 cs = lg[i];
+        if (cs.y != 0.f) {
+          int p, q;
+          rr_pair(i, step, N, p, q);
+          const float xp = x[p], xq = x[q];
+          x[p] = cs.x * xp + cs.y * xq;
+          x[q] = -cs.y * xp + cs.x * xq;
+        }
+      }
+      __syncwarp();
+    }
+    // sign: largest |entry| (lowest index on ties) positive
+    float best = -1.f;
+    int bj = 0;
+    for (int j = lane; j < l; j += 32) {
+      const float av = fabsf(x[j]);
+      if (av > best) { best = av; bj = j; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+      if (ob > best || (ob == best && oj < bj)) { best = ob; bj = oj; }
+    }
+    const double sg = x[bj] < 0.f ? -1.0 : 1.0;
+    const int r = fs.rank[c];
+    // null when the eigenvalue is at the rounding level of the diagonal entries it is made of
+    double wsum = 0.0;
+    for (int j = lane; j < l; j += 32) wsum += (double)x[j] * (double)x[j] * (double)wk.d0[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+    const bool null = nonfinite || (double)d[c] <= 16.0 * (double)kEps32 * wsum;
+    const double inv = null ? 0.0 : 1.0 / fs.S[r];
+    const bool keep = a.mode != kModeFinal || r < a.k;
+    for (int j = lane; j < l; j += 32) {
+      const double v = sg * (double)x[j];
+      a.W[(int64_t)j * a.ldw + r] = keep ? (float)(v * inv) : 0.f;
+      if (a.mode == kModeFinal) a.W2[(int64_t)j * a.ldw + r] = keep ? (float)v : 0.f;
+      if (a.mode == kModeEigsvd) a.W2[(int64_t)j * l + r] = (float)v;
+    }
+  }
+  // padding columns of W (and W2) beyond l
+  if (blockIdx.x == 0) {
+    const int pad = a.ldw - l;
+    for (int idx = tid; idx < l * pad; idx += nt) {
+      const int j = idx / pad, r = l + idx - j * pad;
+      a.W[(int64_t)j * a.ldw + r] = 0.f;
+      if (a.mode == kModeFinal) a.W2[(int64_t)j * a.ldw + r] = 0.f;
+    }
+  }
+  if (blockIdx.x != 0) return;
+
+  if (a.mode == kModeEigsvd) {
+    for (int r = tid; r < l; r += nt) a.S_out[r] = (float)fs.S[r];
+    return;
+  }
+  Control* ctl = a.ctl;
+  if (tid == 0) {
+    ctl->sweeps = wk.hdr[2];
+    ctl->status |= wk.hdr[1];
+  }
+  if (a.mode == kModeFinal) {
+    for (int r = tid; r < a.k; r += nt) a.S_out[r] = (float)fs.S[r];
+    if (tid == 0 && nonfinite) ctl->status |= kStatusNonFinite;
+    return;
+  }
+  if (a.mode == kModeInit) {
+    for (int r = tid; r < kMaxL; r += nt) {
+      ctl->S_prev[r] = 0.0;
+      ctl->S[r] = r < l ? fs.S[r] : 0.0;
+    }
+    if (tid == 0) {
+      ctl->alpha = 0.0;
+      ctl->alpha_prev = 0.0;
+      ctl->ratio = 0.0;
+      ctl->pass = 0;
+      ctl->stop = 0;
+      ctl->status = (nonfinite ? kStatusNonFinite : 0) | wk.hdr[1];
+      ctl->cont = (!nonfinite && a.pmax > 0) ? 1 : 0;
+      if (a.use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond, (unsigned)ctl->cont);
+    }
+    return;
+  }
+
+  // kModePass: Alg. 5 steps 5-7
+  const double alpha = ctl->alpha;
+  const double alpha_p = ctl->alpha_prev;
+  const int k = a.k;
+  double mx = 0.0;
+  for (int i = tid; i < k; i += nt) mx = fmax(mx, fabs(ctl->S_prev[i] + alpha_p - fs.S[i] - alpha));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) fs.red[warp] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    double m2 = 0.0;
+    for (int w = 0; w < (nt >> 5); ++w) m2 = fmax(m2, fs.red[w]);
+    const double floor_ = 64.0 * 2.220446049250313e-16 * (fs.S[0] + alpha);
+    double denom = fs.S[k] + alpha;
+    if (denom < floor_) denom = floor_;
+    const double ratio = denom > 0.0 ? m2 / denom : INFINITY;
+    const int j = ctl->pass + 1;
+    const int stop = (a.tol > 0.0 && ratio <= a.tol && !nonfinite) ? 1 : 0;
+    double alpha_next = alpha;
+    if (!stop && a.shift && fs.S[l - 1] > alpha) alpha_next = 0.5 * (fs.S[l - 1] + alpha);
+    ctl->pass = j;
+    ctl->ratio = ratio;
+    ctl->stop = stop;
+    if (nonfinite) ctl->status |= kStatusNonFinite;
+    if (!stop) {
+      ctl->alpha = alpha_next;
+      ctl->alpha_prev = a.alpha_prev_mode == 0 ? alpha : alpha_next;
+    }
+    ctl->cont = (!stop && !nonfinite && j < a.pmax) ? 1 : 0;
+    if (a.trace) {
+      double* rec = a.trace + (int64_t)(j - 1) * (5 + l);
+      rec[0] = j;
+      rec[1] = alpha;
+      rec[2] = ratio;
+      rec[3] = stop ? alpha : alpha_next;
+      rec[4] = wk.hdr[2];
+    }
+    fs.flag = stop;
+    if (a.use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond, (unsigned)ctl->cont);
+  }
+  __syncthreads();
+  const int stop = fs.flag;
+  const int j = ctl->pass;
+  for (int r = tid; r < l; r += nt) {
+    if (!stop) ctl->S_prev[r] = fs.S[r];
+    ctl->S[r] = fs.S[r];
+    if (a.trace) a.trace[(int64_t)(j - 1) * (5 + l) + 5 + r] = fs.S[r];
+  }
+}
+
+size_t jacobi_smem(int l) {
+  const int N = l + (l & 1);
+  return (size_t)(N * (N + 1) / 2) * sizeof(float);
 }
 
 }  // namespace
 
-int eig_max_l_f32() { return kMaxNF32; }
+int eig_max_l_f32() { return kMaxL; }
 
-cudaError_t prepare_eig() {
-  return cudaFuncSetAttribute(eig_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)eig_f32_smem(kMaxNF32));
+size_t eig_work_bytes() {
+  return 16 + 2 * sizeof(float) * kMaxL + sizeof(float2) * (size_t)kMaxSweeps * (kMaxN - 1) * (kMaxN / 2) + 16;
 }
 
-cudaError_t launch_eig_f32(const float* G, int64_t ldg, const EigArgs& a, cudaStream_t st) {
-  if (a.l < 1 || a.l > kMaxNF32) return cudaErrorInvalidValue;
-  const size_t smem = eig_f32_smem(a.l);
-  eig_f32_kernel<<<1, kEigThreads, smem, st>>>(G, ldg, a);
+EigWork eig_work_view(void* base) {
+  EigWork w;
+  char* p = reinterpret_cast<char*>(base);
+  w.hdr = reinterpret_cast<int*>(p);
+  w.d = reinterpret_cast<float*>(p + 16);
+  w.d0 = w.d + kMaxL;
+  w.log = reinterpret_cast<float2*>(p + 16 + 2 * sizeof(float) * kMaxL);
+  return w;
+}
+
+cudaError_t prepare_eig() {
+  return cudaFuncSetAttribute(jacobi_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)jacobi_smem(kMaxL));
+}
+
+cudaError_t launch_eig_f32(const float* G, int64_t ldg, const EigArgs& a, const EigWork& wk, cudaStream_t st) {
+  if (a.l < 1 || a.l > kMaxL) return cudaErrorInvalidValue;
+  jacobi_f32_kernel<<<1, kJacThreads, jacobi_smem(a.l), st>>>(G, ldg, a.l, wk);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  eigvec_finish_kernel<<<(unsigned)ds_ceil_div(a.l, kVecWarps), kVecWarps * 32, 0, st>>>(wk, a);
   return cudaGetLastError();
 }
 

@@ -5,28 +5,36 @@
 // Both products gather rows of the dense operand: for row r of the sparse
 // matrix, y_r = sum_e a_e x_{col(e)}. A warp works on one row at a time; its
 // 32 lanes form 4 teams of 8 lanes, each team takes every 4th nonzero and each
-// lane owns V float4 slots of the row (slot t + 8v for lane t of the team), so
-// one team reads 128 contiguous bytes per slot group. The 32 (col, val) pairs
-// of a row chunk are loaded once, coalesced, and broadcast with shuffles.
+// lane owns V slots of 4 columns (slot t + 8v for lane t of the team), so a
+// team reads one contiguous run of the row per slot group. The 32 (col, val)
+// pairs of a row chunk are loaded once, coalesced, and broadcast by shuffles;
+// the next chunk's pairs are fetched while the current one is gathered.
+// The dense operand and the output are FP32 or BF16 (the precision form keeps
+// the gathered operands in BF16); accumulation is always FP32.
 //
 // Two work splits (the autotuner picks one per matrix):
-//   variant 0  warp per row: rows strided over warps (rows of similar length)
-//   variant 1  merge path: the merge of row ends with nonzero indices is cut
-//              into equal diagonals, one per warp (Merrill and Garland, SC'16),
-//              so very long rows (hot columns of A^T) are split across warps.
-//              Rows cut by a diagonal leave per-warp partial sums ("carries")
-//              that a fix-up kernel adds in diagonal order, so the result does
-//              not depend on scheduling.
+//   variant 0  warp per row: rows strided over persistent warps
+//   variant 1  merge path (Merrill and Garland, SC'16): the merge of row ends
+//              with nonzero indices is cut into equal segments, computed once
+//              per matrix; persistent warps take segments in turn, so very
+//              long rows (hot columns of A^T) are split across warps. Pieces
+//              of split rows go to per-segment carry slots that a fix-up
+//              kernel adds in segment order, so the result does not depend on
+//              scheduling.
+#include <cuda_bf16.h>
+
 #include "internal.cuh"
 
 namespace dsvd {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kThreads = 256;
 
+template <typename TQ>
 struct Epilogue {
   const double* alpha;  // nullptr: plain product
-  const float* Q;
+  const TQ* Q;
   int64_t ldq;
   int l;
 };
@@ -38,47 +46,69 @@ __device__ __forceinline__ float4 f4_fma(float a, float4 x, float4 acc) {
   acc.w = fmaf(a, x.w, acc.w);
   return acc;
 }
-
 __device__ __forceinline__ float4 f4_add(float4 a, float4 b) {
   return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
 }
-
 __device__ __forceinline__ float4 f4_xor(float4 v, int m) {
   return make_float4(__shfl_xor_sync(kFull, v.x, m), __shfl_xor_sync(kFull, v.y, m),
                      __shfl_xor_sync(kFull, v.z, m), __shfl_xor_sync(kFull, v.w, m));
 }
+__device__ __forceinline__ float4 f4_zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 
-// Accumulate sum_{e in [b, e_end)} val[e] * X[col[e], :] into acc (this lane's slots).
-template <int V>
-__device__ __forceinline__ void accum_range(int b, int e_end, const int32_t* __restrict__ col,
-                                            const float* __restrict__ val, const float4* __restrict__ X4,
-                                            int64_t ldx4, int nslot, int lane, float4 (&acc)[V]) {
+// 4 consecutive elements (one slot) of a row, as FP32
+__device__ __forceinline__ float4 load4(const float* row, int slot) {
+  return __ldg(reinterpret_cast<const float4*>(row) + slot);
+}
+__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+__device__ __forceinline__ float4 load4(const __nv_bfloat16* row, int slot) {
+  const uint2 u = __ldg(reinterpret_cast<const uint2*>(row) + slot);
+  return make_float4(bf_lo(u.x), bf_hi(u.x), bf_lo(u.y), bf_hi(u.y));
+}
+__device__ __forceinline__ void store4(float* row, int slot, float4 v) { reinterpret_cast<float4*>(row)[slot] = v; }
+__device__ __forceinline__ uint32_t pack_bf2(float a, float b) {
+  const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(a));
+  const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(b));
+  return lo | (hi << 16);
+}
+__device__ __forceinline__ void store4(__nv_bfloat16* row, int slot, float4 v) {
+  reinterpret_cast<uint2*>(row)[slot] = make_uint2(pack_bf2(v.x, v.y), pack_bf2(v.z, v.w));
+}
+
+// Gather-accumulate one chunk: entries [pos, pos + cnt) of the sparse row,
+// whose (col, val) pairs sit in lanes 0..cnt-1 of (c, a), into acc (this lane's slots).
+template <int V, typename TIn>
+__device__ __forceinline__ void gather_chunk(int c, float a, int cnt, const TIn* __restrict__ X, int64_t ldx,
+                                             int nslot, int lane, float4 (&acc)[V]) {
   const int g = lane >> 3, t = lane & 7;
-  for (int base = b; base < e_end; base += 32) {
-    const int idx = base + lane;
-    int c = -1;
-    float a = 0.f;
-    if (idx < e_end) {
-      c = __ldg(col + idx);
-      a = __ldg(val + idx);
-    }
-    const int cnt = min(32, e_end - base);
-    for (int s = 0; 4 * s < cnt; s += 2) {
-      const int src0 = 4 * s + g, src1 = src0 + 4;
-      const int c0 = __shfl_sync(kFull, c, src0), c1 = __shfl_sync(kFull, c, src1);
-      const float a0 = __shfl_sync(kFull, a, src0), a1 = __shfl_sync(kFull, a, src1);
-      float4 x0[V], x1[V];
-      const float4* r0 = X4 + (int64_t)(c0 < 0 ? 0 : c0) * ldx4;
-      const float4* r1 = X4 + (int64_t)(c1 < 0 ? 0 : c1) * ldx4;
+  for (int s = 0; 4 * s < cnt; s += 2) {
+    const int src0 = 4 * s + g, src1 = src0 + 4;
+    int c0 = __shfl_sync(kFull, c, src0), c1 = __shfl_sync(kFull, c, src1);
+    const float a0 = __shfl_sync(kFull, a, src0), a1 = __shfl_sync(kFull, a, src1);
+    if (src0 >= cnt) c0 = -1;
+    if (src1 >= cnt) c1 = -1;
+    float4 x0[V], x1[V];
+    const TIn* r0 = X + (int64_t)(c0 < 0 ? 0 : c0) * ldx;
+    const TIn* r1 = X + (int64_t)(c1 < 0 ? 0 : c1) * ldx;
 #pragma unroll
-      for (int v = 0; v < V; ++v) {
-        const int slot = t + 8 * v;
-        x0[v] = (c0 >= 0 && slot < nslot) ? __ldg(r0 + slot) : make_float4(0.f, 0.f, 0.f, 0.f);
-        x1[v] = (c1 >= 0 && slot < nslot) ? __ldg(r1 + slot) : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-#pragma unroll
-      for (int v = 0; v < V; ++v) acc[v] = f4_fma(a1, x1[v], f4_fma(a0, x0[v], acc[v]));
+    for (int v = 0; v < V; ++v) {
+      const int slot = t + 8 * v;
+      x0[v] = (c0 >= 0 && slot < nslot) ? load4(r0, slot) : f4_zero();
+      x1[v] = (c1 >= 0 && slot < nslot) ? load4(r1, slot) : f4_zero();
     }
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = f4_fma(a1, x1[v], f4_fma(a0, x0[v], acc[v]));
+  }
+}
+
+// (col, val) of entries [p, p + 32) below `lim` into lanes (col -1 past the end)
+__device__ __forceinline__ void load_pairs(const int32_t* __restrict__ col, const float* __restrict__ val, int64_t p,
+                                           int64_t lim, int lane, int& c, float& a) {
+  c = -1;
+  a = 0.f;
+  if (p + lane < lim) {
+    c = __ldg(col + p + lane);
+    a = __ldg(val + p + lane);
   }
 }
 
@@ -92,11 +122,12 @@ __device__ __forceinline__ void team_reduce(float4 (&acc)[V]) {
   }
 }
 
-__device__ __forceinline__ float4 apply_epilogue(float4 s, int slot, int64_t row, const Epilogue& ep, float alpha) {
+template <typename TQ>
+__device__ __forceinline__ float4 apply_epilogue(float4 s, int slot, int64_t row, const Epilogue<TQ>& ep, float alpha) {
   const int c = 4 * slot;
-  if (c >= ep.l) return make_float4(0.f, 0.f, 0.f, 0.f);  // padding columns (no Q read)
+  if (c >= ep.l) return f4_zero();  // padding columns (no Q read)
   if (ep.alpha) {
-    const float4 q = __ldg(reinterpret_cast<const float4*>(ep.Q + row * ep.ldq) + slot);
+    const float4 q = load4(ep.Q + row * ep.ldq, slot);
     s.x = fmaf(-alpha, q.x, s.x);
     s.y = fmaf(-alpha, q.y, s.y);
     s.z = fmaf(-alpha, q.z, s.z);
@@ -109,48 +140,77 @@ __device__ __forceinline__ float4 apply_epilogue(float4 s, int slot, int64_t row
 }
 
 // Write a reduced row (teams split the slots), with the epilogue, zero padding to ldy.
-template <int V>
-__device__ __forceinline__ void store_row(const float4 (&acc)[V], int64_t row, float* __restrict__ Y, int64_t ldy4,
-                                          const Epilogue& ep, float alpha, int lane) {
+template <int V, typename TOut, typename TQ>
+__device__ __forceinline__ void store_row(const float4 (&acc)[V], int64_t row, TOut* __restrict__ Y, int64_t ldy,
+                                          const Epilogue<TQ>& ep, float alpha, int lane) {
   const int g = lane >> 3, t = lane & 7;
-  float4* y = reinterpret_cast<float4*>(Y) + row * ldy4;
+  TOut* y = Y + row * ldy;
+  const int ldy4 = (int)(ldy >> 2);
 #pragma unroll
   for (int v = 0; v < V; ++v) {
     const int slot = t + 8 * v;
-    if ((v & 3) == g && slot < ldy4) y[slot] = apply_epilogue(acc[v], slot, row, ep, alpha);
+    if ((v & 3) == g && slot < ldy4) store4(y, slot, apply_epilogue(acc[v], slot, row, ep, alpha));
   }
-  for (int slot = 8 * V + lane; slot < ldy4; slot += 32) y[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int slot = 8 * V + lane; slot < ldy4; slot += 32) store4(y, slot, f4_zero());
 }
 
-// Raw partial sums (no epilogue) for the merge-path carries.
+// Raw partial sums (no epilogue) for the merge-path carries (FP32, stride ldc floats).
 template <int V>
-__device__ __forceinline__ void store_carry(const float4 (&acc)[V], float* __restrict__ C, int64_t ldc4, int lane) {
+__device__ __forceinline__ void store_carry(const float4 (&acc)[V], float* __restrict__ C, int ldc4, int lane) {
   const int g = lane >> 3, t = lane & 7;
-  float4* y = reinterpret_cast<float4*>(C);
 #pragma unroll
   for (int v = 0; v < V; ++v) {
     const int slot = t + 8 * v;
-    if ((v & 3) == g && slot < ldc4) y[slot] = acc[v];
+    if ((v & 3) == g && slot < ldc4) reinterpret_cast<float4*>(C)[slot] = acc[v];
   }
 }
 
-template <int V>
-__global__ void __launch_bounds__(256) spmm_rows_kernel(const int32_t* __restrict__ rowptr,
-                                                        const int32_t* __restrict__ col,
-                                                        const float* __restrict__ val, int64_t m,
-                                                        const float* __restrict__ X, int64_t ldx,
-                                                        float* __restrict__ Y, int64_t ldy, int nslot, Epilogue ep) {
+template <int V, typename TIn, typename TOut, typename TQ>
+__global__ void __launch_bounds__(kThreads) spmm_rows_kernel(const int32_t* __restrict__ rowptr,
+                                                             const int32_t* __restrict__ col,
+                                                             const float* __restrict__ val, int64_t m, int64_t nnz,
+                                                             const TIn* __restrict__ X, int64_t ldx,
+                                                             TOut* __restrict__ Y, int64_t ldy, int nslot,
+                                                             Epilogue<TQ> ep) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const float alpha = ep.alpha ? (float)*ep.alpha : 0.f;
-  const float4* X4 = reinterpret_cast<const float4*>(X);
-  for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < m; r += warps) {
-    float4 acc[V];
+  int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (r >= m) return;
+  int64_t pos = rowptr[r], e = rowptr[r + 1];
+  int c;
+  float a;
+  load_pairs(col, val, pos, e, lane, c, a);
+  float4 acc[V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
-    accum_range<V>(rowptr[r], rowptr[r + 1], col, val, X4, ldx >> 2, nslot, lane, acc);
-    team_reduce<V>(acc);
-    store_row<V>(acc, r, Y, ldy >> 2, ep, alpha, lane);
+  for (int v = 0; v < V; ++v) acc[v] = f4_zero();
+  while (true) {
+    // where the next chunk starts: later in this row, or the start of this warp's next row
+    const int64_t rn = r + warps;
+    int64_t next = pos + 32, next_e = e;
+    if (next >= e) {
+      next = rn < m ? rowptr[rn] : nnz;
+      next_e = rn < m ? rowptr[rn + 1] : nnz;
+    }
+    int cn;
+    float an;
+    load_pairs(col, val, next, next_e, lane, cn, an);
+    const int cnt = (int)(e - pos < 32 ? e - pos : 32);
+    gather_chunk<V, TIn>(c, a, cnt, X, ldx, nslot, lane, acc);
+    c = cn;
+    a = an;
+    if (pos + 32 >= e) {  // row done
+      team_reduce<V>(acc);
+      store_row<V, TOut, TQ>(acc, r, Y, ldy, ep, alpha, lane);
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[v] = f4_zero();
+      r = rn;
+      if (r >= m) break;
+      pos = next;
+      e = next_e;
+    } else {
+      pos = next;
+    }
   }
 }
 
@@ -170,72 +230,101 @@ __device__ __forceinline__ void merge_search(int64_t d, const int32_t* __restric
   j = d - lo;
 }
 
-template <int V>
-__global__ void __launch_bounds__(256) spmm_merge_kernel(const int32_t* __restrict__ rowptr,
-                                                         const int32_t* __restrict__ col,
-                                                         const float* __restrict__ val, int64_t m, int64_t nnz,
-                                                         const float* __restrict__ X, int64_t ldx,
-                                                         float* __restrict__ Y, int64_t ldy, int nslot, Epilogue ep,
-                                                         int64_t warps, float* __restrict__ carry,
-                                                         int32_t* __restrict__ carry_row) {
-  const int lane = threadIdx.x & 31;
-  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  if (w >= warps) return;
-  const float alpha = ep.alpha ? (float)*ep.alpha : 0.f;
-  const float4* X4 = reinterpret_cast<const float4*>(X);
-  const int64_t ldx4 = ldx >> 2, ldy4 = ldy >> 2;
+__global__ void merge_partition_kernel(const int32_t* __restrict__ rowptr, int64_t m, int64_t nnz, int64_t segments,
+                                       int64_t per, int32_t* __restrict__ seg_row, int32_t* __restrict__ seg_nnz) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s > segments) return;
   const int64_t total = m + nnz;
-  const int64_t per = ds_ceil_div(total, warps);
-  const int64_t d0 = w * per < total ? w * per : total;
-  const int64_t d1 = d0 + per < total ? d0 + per : total;
-  int64_t r0, k0, r1, k1;
-  merge_search(d0, rowptr, m, nnz, r0, k0);
-  merge_search(d1, rowptr, m, nnz, r1, k1);
-  int32_t head_row = -1, tail_row = -1;
-  for (int64_t r = r0; r < r1; ++r) {
-    const int b = rowptr[r];
-    const int e = rowptr[r + 1];
-    const int bb = b > k0 ? b : (int)k0;
+  int64_t d = s * per;
+  if (d > total) d = total;
+  int64_t i, j;
+  merge_search(d, rowptr, m, nnz, i, j);
+  seg_row[s] = (int32_t)i;
+  seg_nnz[s] = (int32_t)j;
+}
+
+template <int V, typename TIn, typename TOut, typename TQ>
+__global__ void __launch_bounds__(kThreads) spmm_merge_kernel(const int32_t* __restrict__ rowptr,
+                                                              const int32_t* __restrict__ col,
+                                                              const float* __restrict__ val, int64_t m,
+                                                              const TIn* __restrict__ X, int64_t ldx,
+                                                              TOut* __restrict__ Y, int64_t ldy, int nslot,
+                                                              Epilogue<TQ> ep, SpmmPart part, float* __restrict__ carry,
+                                                              int32_t* __restrict__ carry_row, int ldc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const float alpha = ep.alpha ? (float)*ep.alpha : 0.f;
+  const int ldc4 = ldc >> 2;
+  for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < part.segments; w += warps) {
+    const int64_t r0 = part.seg_row[w], k0 = part.seg_nnz[w];
+    const int64_t r1 = part.seg_row[w + 1], k1 = part.seg_nnz[w + 1];
+    const bool split_head = r0 < m && (int64_t)rowptr[r0] < k0;  // row r0 began in an earlier segment
+    int32_t head_row = -1, tail_row = -1;
+    // window of row ends rowptr[rw + 1 .. rw + 32] held across the lanes
+    int64_t rw = r0;
+    int rp = rowptr[(rw + 1 + lane) < m ? (rw + 1 + lane) : m];
+    int64_t r = r0, pos = k0;
+    int c;
+    float a;
+    load_pairs(col, val, pos, k1, lane, c, a);
     float4 acc[V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
-    accum_range<V>(bb, e, col, val, X4, ldx4, nslot, lane, acc);
-    team_reduce<V>(acc);
-    if (b < k0) {  // started in an earlier diagonal: finishing piece of a split row
-      store_carry<V>(acc, carry + (2 * w) * ldy, ldy4, lane);
-      head_row = (int32_t)r;
-    } else {
-      store_row<V>(acc, r, Y, ldy4, ep, alpha, lane);
-    }
-  }
-  if (r1 < m) {
-    const int b = rowptr[r1];
-    const int bb = b > k0 ? b : (int)k0;
-    if ((int64_t)bb < k1) {  // leading or middle piece of a row that ends later
-      float4 acc[V];
+    for (int v = 0; v < V; ++v) acc[v] = f4_zero();
+    // rows r0 .. r1-1 end inside the segment; row r1 (if any entries here) continues past it
+    while (r < r1 || (r == r1 && r1 < m && pos < k1)) {
+      int64_t e;
+      if (r < r1) {
+        if (r - rw >= 32) {
+          rw = r;
+          rp = rowptr[(rw + 1 + lane) < m ? (rw + 1 + lane) : m];
+        }
+        e = __shfl_sync(kFull, rp, (int)(r - rw));
+      } else {
+        e = k1;
+      }
+      const int64_t next = pos + 32 < e ? pos + 32 : e;
+      int cn;
+      float an;
+      load_pairs(col, val, next, k1, lane, cn, an);
+      const int cnt = (int)(e - pos < 32 ? e - pos : 32);
+      gather_chunk<V, TIn>(c, a, cnt, X, ldx, nslot, lane, acc);
+      c = cn;
+      a = an;
+      pos = next;
+      if (pos == e) {
+        team_reduce<V>(acc);
+        if (r == r1) {  // leading or middle piece of a row that ends later
+          const int64_t slot = r0 == r1 ? 2 * w : 2 * w + 1;
+          store_carry<V>(acc, carry + slot * (int64_t)ldc, ldc4, lane);
+          if (r0 == r1)
+            head_row = (int32_t)r1;
+          else
+            tail_row = (int32_t)r1;
+        } else if (r == r0 && split_head) {  // finishing piece of a split row
+          store_carry<V>(acc, carry + (2 * w) * (int64_t)ldc, ldc4, lane);
+          head_row = (int32_t)r;
+        } else {
+          store_row<V, TOut, TQ>(acc, r, Y, ldy, ep, alpha, lane);
+        }
 #pragma unroll
-      for (int v = 0; v < V; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
-      accum_range<V>(bb, (int)k1, col, val, X4, ldx4, nslot, lane, acc);
-      team_reduce<V>(acc);
-      const int64_t slot = r0 == r1 ? 2 * w : 2 * w + 1;
-      store_carry<V>(acc, carry + slot * ldy, ldy4, lane);
-      if (r0 == r1)
-        head_row = (int32_t)r1;
-      else
-        tail_row = (int32_t)r1;
+        for (int v = 0; v < V; ++v) acc[v] = f4_zero();
+        ++r;
+      }
     }
-  }
-  if (lane == 0) {
-    carry_row[2 * w] = head_row;
-    carry_row[2 * w + 1] = tail_row;
+    if (lane == 0) {
+      carry_row[2 * w] = head_row;
+      carry_row[2 * w + 1] = tail_row;
+    }
   }
 }
 
 // One warp per carry slot; the first slot of each split row sums all of the
-// row's pieces in diagonal order and writes the row with the epilogue.
-__global__ void __launch_bounds__(256) spmm_fixup_kernel(const float* __restrict__ carry,
-                                                         const int32_t* __restrict__ carry_row, int64_t slots,
-                                                         float* __restrict__ Y, int64_t ldy, Epilogue ep) {
+// row's pieces in segment order and writes the row with the epilogue.
+template <typename TOut, typename TQ>
+__global__ void __launch_bounds__(kThreads) spmm_fixup_kernel(const float* __restrict__ carry,
+                                                              const int32_t* __restrict__ carry_row, int64_t slots,
+                                                              int ldc, TOut* __restrict__ Y, int64_t ldy,
+                                                              Epilogue<TQ> ep) {
   const int lane = threadIdx.x & 31;
   const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   if (s >= slots) return;
@@ -245,62 +334,104 @@ __global__ void __launch_bounds__(256) spmm_fixup_kernel(const float* __restrict
   while (t >= 0 && carry_row[t] < 0) --t;
   if (t >= 0 && carry_row[t] == row) return;  // not the first piece
   const float alpha = ep.alpha ? (float)*ep.alpha : 0.f;
-  const int64_t ldy4 = ldy >> 2;
-  float4* y = reinterpret_cast<float4*>(Y) + (int64_t)row * ldy4;
-  for (int64_t slot = lane; slot < ldy4; slot += 32) {
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int64_t u = s; u < slots; ++u) {
-      const int32_t ru = carry_row[u];
-      if (ru < 0) continue;
-      if (ru != row) break;
-      acc = f4_add(acc, reinterpret_cast<const float4*>(carry + u * ldy)[slot]);
+  const int ldy4 = (int)(ldy >> 2), ldc4 = ldc >> 2;
+  TOut* y = Y + (int64_t)row * ldy;
+  for (int slot = lane; slot < ldy4; slot += 32) {
+    float4 acc = f4_zero();
+    if (slot < ldc4) {
+      for (int64_t u = s; u < slots; ++u) {
+        const int32_t ru = carry_row[u];
+        if (ru < 0) continue;
+        if (ru != row) break;
+        acc = f4_add(acc, reinterpret_cast<const float4*>(carry + u * (int64_t)ldc)[slot]);
+      }
     }
-    y[slot] = apply_epilogue(acc, (int)slot, row, ep, alpha);
+    store4(y, slot, apply_epilogue(acc, slot, row, ep, alpha));
   }
 }
 
-template <int V>
-cudaError_t launch_v(const dashsvd_csr& A, const float* X, int64_t ldx, int l, float* Y, int64_t ldy,
-                     const Epilogue& ep, int variant, const SpmmScratch& scr, int num_sms, cudaStream_t st) {
+template <int V, typename TIn, typename TOut, typename TQ>
+cudaError_t launch_v(const dashsvd_csr& A, const SpmmPart& part, const TIn* X, int64_t ldx, int l, TOut* Y,
+                     int64_t ldy, const Epilogue<TQ>& ep, int variant, const SpmmScratch& scr, int num_sms,
+                     cudaStream_t st) {
   const int nslot = (l + 3) / 4;
   if (A.m <= 0) return cudaSuccess;
+  // persistent warps: more blocks than fit at once are simply queued
+  const int64_t grid = (int64_t)num_sms * 8;
   if (variant == 0) {
-    const int64_t need = ds_ceil_div(A.m * 32, 256);
-    const int64_t cap = (int64_t)num_sms * 8;
-    spmm_rows_kernel<V><<<(unsigned)(need < cap ? need : cap), 256, 0, st>>>(A.rowptr, A.colidx, A.val, A.m, X, ldx,
-                                                                             Y, ldy, nslot, ep);
+    const int64_t need = ds_ceil_div(A.m * 32, kThreads);
+    spmm_rows_kernel<V, TIn, TOut, TQ><<<(unsigned)(need < grid ? need : grid), kThreads, 0, st>>>(
+        A.rowptr, A.colidx, A.val, A.m, A.nnz, X, ldx, Y, ldy, nslot, ep);
     return cudaGetLastError();
   }
-  const int64_t warps = scr.warps;
-  spmm_merge_kernel<V><<<(unsigned)ds_ceil_div(warps * 32, 256), 256, 0, st>>>(
-      A.rowptr, A.colidx, A.val, A.m, A.nnz, X, ldx, Y, ldy, nslot, ep, warps, scr.carry, scr.carry_row);
+  if (part.segments > scr.max_segments || scr.ldc < ((l + 3) / 4) * 4) return cudaErrorInvalidValue;
+  const int64_t need = ds_ceil_div(part.segments * 32, kThreads);
+  spmm_merge_kernel<V, TIn, TOut, TQ><<<(unsigned)(need < grid ? need : grid), kThreads, 0, st>>>(
+      A.rowptr, A.colidx, A.val, A.m, X, ldx, Y, ldy, nslot, ep, part, scr.carry, scr.carry_row, scr.ldc);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  spmm_fixup_kernel<<<(unsigned)ds_ceil_div(2 * warps * 32, 256), 256, 0, st>>>(scr.carry, scr.carry_row, 2 * warps,
-                                                                              Y, ldy, ep);
+  spmm_fixup_kernel<TOut, TQ><<<(unsigned)ds_ceil_div(2 * part.segments * 32, kThreads), kThreads, 0, st>>>(
+      scr.carry, scr.carry_row, 2 * part.segments, scr.ldc, Y, ldy, ep);
   return cudaGetLastError();
+}
+
+template <typename TIn, typename TOut, typename TQ>
+cudaError_t dispatch(const dashsvd_csr& A, const SpmmPart& part, const TIn* X, int64_t ldx, int l, TOut* Y,
+                     int64_t ldy, const double* alpha, const TQ* Q, int64_t ldq, int variant, const SpmmScratch& scr,
+                     int num_sms, cudaStream_t st) {
+  Epilogue<TQ> ep{alpha, Q, ldq, l};
+  const int V = ((l + 3) / 4 + 7) / 8;
+  switch (V) {
+    case 1: return launch_v<1>(A, part, X, ldx, l, Y, ldy, ep, variant, scr, num_sms, st);
+    case 2: return launch_v<2>(A, part, X, ldx, l, Y, ldy, ep, variant, scr, num_sms, st);
+    case 3: return launch_v<3>(A, part, X, ldx, l, Y, ldy, ep, variant, scr, num_sms, st);
+    case 4: return launch_v<4>(A, part, X, ldx, l, Y, ldy, ep, variant, scr, num_sms, st);
+    case 5: return launch_v<5>(A, part, X, ldx, l, Y, ldy, ep, variant, scr, num_sms, st);
+    case 6: return launch_v<6>(A, part, X, ldx, l, Y, ldy, ep, variant, scr, num_sms, st);
+    case 7: return launch_v<7>(A, part, X, ldx, l, Y, ldy, ep, variant, scr, num_sms, st);
+    case 8: return launch_v<8>(A, part, X, ldx, l, Y, ldy, ep, variant, scr, num_sms, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
 
-int spmm_mergepath_warps(int num_sms) { return num_sms * 16; }
+int64_t spmm_segments(const dashsvd_csr& A, int num_sms) {
+  // about four segments per resident warp (at most 24 warps per SM fit), and
+  // at least 256 merge items (rows + nonzeros) per segment
+  const int64_t total = A.m + A.nnz;
+  int64_t segs = (int64_t)num_sms * 24 * 4;
+  const int64_t cap = ds_ceil_div(total, 256);
+  if (segs > cap) segs = cap;
+  return segs < 1 ? 1 : segs;
+}
 
-cudaError_t launch_spmm(const dashsvd_csr& A, const float* X, int64_t ldx, int l, float* Y, int64_t ldy,
-                        const double* alpha, const float* Q, int64_t ldq, int variant, const SpmmScratch& scr,
-                        int num_sms, cudaStream_t st) {
-  Epilogue ep{alpha, Q, ldq, l};
-  const int V = ((l + 3) / 4 + 7) / 8;
-  switch (V) {
-    case 1: return launch_v<1>(A, X, ldx, l, Y, ldy, ep, variant, scr, num_sms, st);
-    case 2: return launch_v<2>(A, X, ldx, l, Y, ldy, ep, variant, scr, num_sms, st);
-    case 3: return launch_v<3>(A, X, ldx, l, Y, ldy, ep, variant, scr, num_sms, st);
-    case 4: return launch_v<4>(A, X, ldx, l, Y, ldy, ep, variant, scr, num_sms, st);
-    case 5: return launch_v<5>(A, X, ldx, l, Y, ldy, ep, variant, scr, num_sms, st);
-    case 6: return launch_v<6>(A, X, ldx, l, Y, ldy, ep, variant, scr, num_sms, st);
-    case 7: return launch_v<7>(A, X, ldx, l, Y, ldy, ep, variant, scr, num_sms, st);
-    case 8: return launch_v<8>(A, X, ldx, l, Y, ldy, ep, variant, scr, num_sms, st);
-    default: return cudaErrorInvalidValue;
-  }
+cudaError_t launch_spmm_partition(const dashsvd_csr& A, SpmmPart& part, cudaStream_t st) {
+  const int64_t total = A.m + A.nnz;
+  part.per = ds_ceil_div(total, part.segments);
+  if (part.per < 1) part.per = 1;
+  merge_partition_kernel<<<(unsigned)ds_ceil_div(part.segments + 1, 256), 256, 0, st>>>(
+      A.rowptr, A.m, A.nnz, part.segments, part.per, part.seg_row, part.seg_nnz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spmm(const dashsvd_csr& A, const SpmmPart& part, const float* X, int64_t ldx, int l, float* Y,
+                        int64_t ldy, const double* alpha, const float* Q, int64_t ldq, int variant,
+                        const SpmmScratch& scr, int num_sms, cudaStream_t st) {
+  return dispatch<float, float, float>(A, part, X, ldx, l, Y, ldy, alpha, Q, ldq, variant, scr, num_sms, st);
+}
+
+cudaError_t launch_spmm_bf16(const dashsvd_csr& A, const SpmmPart& part, const void* X, int64_t ldx, int l, void* Y,
+                             bool y_bf16, int64_t ldy, const double* alpha, const void* Q, int64_t ldq, int variant,
+                             const SpmmScratch& scr, int num_sms, cudaStream_t st) {
+  const __nv_bfloat16* Xb = reinterpret_cast<const __nv_bfloat16*>(X);
+  const __nv_bfloat16* Qb = reinterpret_cast<const __nv_bfloat16*>(Q);
+  if (y_bf16)
+    return dispatch<__nv_bfloat16, __nv_bfloat16, __nv_bfloat16>(A, part, Xb, ldx, l,
+                                                                 reinterpret_cast<__nv_bfloat16*>(Y), ldy, alpha, Qb,
+                                                                 ldq, variant, scr, num_sms, st);
+  return dispatch<__nv_bfloat16, float, __nv_bfloat16>(A, part, Xb, ldx, l, reinterpret_cast<float*>(Y), ldy, alpha,
+                                                       Qb, ldq, variant, scr, num_sms, st);
 }
 
 }  // namespace dsvd

@@ -113,7 +113,7 @@ def _spmm_check(A, X, Y, l):
 
 
 @pytest.mark.parametrize("name", list(MATRICES))
-@pytest.mark.parametrize("l", [1, 7, 30, 150, 160])
+@pytest.mark.parametrize("l", [1, 7, 30, 150, 160, 220])
 @pytest.mark.parametrize("variant", [0, 1])
 def test_spmm_matches_fp64(ds, h, name, l, variant):
     A = MATRICES[name]()
@@ -163,7 +163,8 @@ def test_spmm_merge_path_matches_warp_per_row_closely(ds, h):
     np.testing.assert_allclose(y0, y1, rtol=1e-4, atol=1e-4)
 
 
-@pytest.mark.parametrize("rows,l", [(1, 1), (100, 30), (5000, 7), (20011, 150), (3000, 160), (70000, 64)])
+@pytest.mark.parametrize("rows,l", [(1, 1), (100, 30), (5000, 7), (20011, 150), (3000, 160), (70000, 64),
+                                    (9001, 220), (3000, 256)])
 def test_gram_matches_fp64(ds, h, rows, l):
     rng = np.random.default_rng(rows)
     ld = ds.ld_for(l)
@@ -176,8 +177,27 @@ def test_gram_matches_fp64(ds, h, rows, l):
     np.testing.assert_array_equal(G, G.T)
 
 
+@pytest.mark.parametrize("rows,l", [(1, 1), (64, 16), (1000, 30), (20011, 150), (3000, 160), (70000, 64),
+                                    (9001, 220), (3000, 256), (500000, 150)])
+def test_gram_bf16x3_matches_fp64(ds, h, rows, l):
+    """Tensor-core BF16x3 Gram: each product carries a relative error of about
+    2^-16 (the dropped lo*lo term and the rounding of the split), plus FP32
+    accumulation within a row chunk."""
+    rng = np.random.default_rng(rows + 7)
+    ld = ds.ld_for(l)
+    Cm = _padded((rng.standard_normal((rows, l)) * np.logspace(0, -2, l)).astype(np.float32), ld)
+    G = _np(h.gram_bf16x3(_t(Cm), l))
+    C64 = Cm[:, :l].astype(np.float64)
+    ref = C64.T @ C64
+    bound = np.abs(C64).T @ np.abs(C64)
+    err = np.abs(G - ref)
+    assert np.all(err <= 4e-5 * bound + 1e-30), float(np.max(err / (bound + 1e-300)))
+    np.testing.assert_allclose(G, G.T, rtol=1e-6, atol=1e-6 * np.abs(G).max())
+
+
 @pytest.mark.parametrize("rows,l,cols,ldo", [(10, 4, 4, 4), (1000, 30, 30, 32), (12345, 150, 150, 152),
-                                             (777, 150, 100, 100), (4097, 160, 37, 40)])
+                                             (777, 150, 100, 100), (4097, 160, 37, 40), (5000, 220, 220, 224),
+                                             (3000, 256, 200, 256)])
 def test_project_matches_fp64(ds, h, rows, l, cols, ldo):
     import torch
 
@@ -193,7 +213,8 @@ def test_project_matches_fp64(ds, h, rows, l, cols, ldo):
     assert np.all(Out[:, cols:] == 0.0)
 
 
-@pytest.mark.parametrize("rows,l", [(500, 12), (4000, 30), (20000, 150), (3000, 160), (300, 1)])
+@pytest.mark.parametrize("rows,l", [(500, 12), (4000, 30), (20000, 150), (3000, 160), (300, 1), (8000, 220),
+                                    (2000, 256), (900, 31)])
 def test_eigsvd_matches_oracle(ds, h, rows, l):
     rng = np.random.default_rng(l)
     ld = ds.ld_for(l)
@@ -211,7 +232,7 @@ def test_eigsvd_matches_oracle(ds, h, rows, l):
     ok = gaps / Sr[0] > 1e-3
     np.testing.assert_allclose(V[:, ok], Vr[:, ok], atol=2e-3)
     np.testing.assert_allclose(U[:, :l].T @ U[:, :l], np.eye(l), atol=2e-3)
-    np.testing.assert_allclose((U[:, :l] * S) @ V.T, Cm[:, :l], atol=1e-4 * np.abs(Cm).max())
+    np.testing.assert_allclose((U[:, :l] * S) @ V.T, Cm[:, :l], atol=1e-4 * np.abs(Cm[:, :l]).max())
 
 
 def test_eigsvd_rank_deficient_null_columns(ds, h):
