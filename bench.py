@@ -272,9 +272,9 @@ def ours(args):
     info = infos[-1]
     passes = info.passes
     var_fwd, var_bwd = info.spmm_variant & 0xFF, (info.spmm_variant >> 8) & 0xFF
-    kpv = lambda v: 2 if v == 1 else 1  # noqa: E731  kernels per SpMM launch (merge path adds its fix-up)
-    launches_per_run = 5 + (1 + kpv(var_bwd) + 2 + 1 + 1) + passes * (kpv(var_fwd) + kpv(var_bwd) + 2 + 1 + 1) + \
-        (kpv(var_fwd) + 2 + 1 + 2)
+    kpv = lambda v: 2 if (v & 1) else 1  # noqa: E731  kernels per SpMM launch (merge path adds its fix-up)
+    launches_per_run = 5 + 2 + (1 + kpv(var_bwd) + 2 + 2 + 1) + passes * (kpv(var_fwd) + kpv(var_bwd) + 2 + 2 + 1) + \
+        (kpv(var_fwd) + 2 + 2 + 2)
 
     # ---- one untimed run with the per-pass trace (shift, PVE ratio, Jacobi sweeps)
     with ds.Handle(stream=stream, record_trace=1) as ht:

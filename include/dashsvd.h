@@ -80,7 +80,11 @@ typedef struct {
   int32_t use_graph;       /* 1: the power-iteration loop runs on the device inside a
                               CUDA graph with a conditional WHILE node (no host sync
                               per pass); 0: host-driven loop (one sync per pass) */
-  int32_t spmm_variant;    /* -1: autotuned per matrix; 0: warp per row; 1: merge path */
+  int32_t spmm_variant;    /* -1: autotuned per matrix (each variant timed once on the first
+                              run, the choice cached per matrix); else 0..5 = work split
+                              (0 warp per row, 1 merge path) + 2 * configuration (0: two
+                              nonzeros per team in flight, 1: four, 2: two with registers
+                              capped for four blocks per SM) */
   int32_t record_trace;    /* 1: keep the per-pass Shat / shift history (get_trace) */
   int32_t shift;           /* 1: dynamic shifts (dashSVD); 0: alpha = 0 (Alg. 1 form) */
   int32_t reserved[7];
@@ -158,7 +162,8 @@ int dashsvd_csr_transpose(dashsvd_handle h, const dashsvd_csr* A, int32_t* rowpt
 
 /* Y = A X (Alg. 5 step 4, inner product A Q; also B = A Q, step 9).
  * X: A.n x ldx, Y: A.m x ldy, both with ld % 4 == 0 and ld >= l; Y's columns
- * l .. ldy-1 are set to 0. variant: -1 auto, 0 warp per row, 1 merge path. */
+ * l .. ldy-1 are set to 0. variant: -1 (merge path, configuration 0) or 0..5
+ * as in dashsvd_options.spmm_variant. */
 int dashsvd_spmm(dashsvd_handle h, const dashsvd_csr* A, const float* X, int64_t ldx, int l,
                  float* Y, int64_t ldy, int variant);
 

@@ -95,6 +95,14 @@ struct dashsvd_handle_s {
   int last_l = 0;
   int64_t last_records = 0;
   std::vector<float> mlp;
+  // autotuner cache: SpMM variant per (matrix, l, form)
+  struct Tune {
+    const void *rowptr, *colidx;
+    int64_t m, n, nnz;
+    int l, form, var_fwd, var_bwd;
+    float t_fwd, t_bwd;
+  };
+  std::vector<Tune> tuned;
 };
 
 namespace {
@@ -254,6 +262,58 @@ int build_graph(dashsvd_handle h, const RunPlan& p) {
   return DASHSVD_OK;
 }
 
+constexpr int kSpmmVariants = 6;  // split (warp per row, merge path) x 3 configurations
+
+// Time every SpMM variant once on this matrix (after one warm-up launch each)
+// for both products of a pass, and keep the fastest.
+int autotune_spmm(dashsvd_handle h, RunPlan& p, const dashsvd_csr& A) {
+  for (const auto& t : h->tuned)
+    if (t.rowptr == A.rowptr && t.colidx == A.colidx && t.m == A.m && t.n == A.n && t.nnz == A.nnz && t.l == p.l &&
+        t.form == h->opt.form) {
+      p.var_fwd = t.var_fwd;
+      p.var_bwd = t.var_bwd;
+      return DASHSVD_OK;
+    }
+  cudaStream_t st = h->stream;
+  DS_CUDA(cudaMemsetAsync(h->Q.p, 0, h->Q.bytes, st));
+  DS_CUDA(cudaMemsetAsync(h->Y.p, 0, h->Y.bytes, st));
+  cudaEvent_t e0, e1;
+  DS_CUDA(cudaEventCreate(&e0));
+  DS_CUDA(cudaEventCreate(&e1));
+  const Control* ctl = as<Control>(h->ctl);
+  float best[2] = {3.4e38f, 3.4e38f};
+  int arg[2] = {1, 1};
+  cudaError_t err = cudaSuccess;
+  for (int prod = 0; prod < 2 && err == cudaSuccess; ++prod) {
+    for (int v = 0; v < kSpmmVariants && err == cudaSuccess; ++v) {
+      float ms = 0.f;
+      for (int rep = 0; rep < 2 && err == cudaSuccess; ++rep) {
+        if (rep == 1) err = cudaEventRecord(e0, st);
+        if (err == cudaSuccess) {
+          err = prod == 0 ? launch_spmm(p.Aw, p.part_fwd, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld, nullptr,
+                                        nullptr, 0, v, p.scr, h->num_sms, st)
+                          : launch_spmm(p.AwT, p.part_bwd, as<float>(h->Y), p.ld, p.l, as<float>(h->Z), p.ld,
+                                        &ctl->alpha, as<float>(h->Q), p.ld, v, p.scr, h->num_sms, st);
+        }
+        if (rep == 1 && err == cudaSuccess) err = cudaEventRecord(e1, st);
+      }
+      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+      if (err == cudaSuccess && ms < best[prod]) {
+        best[prod] = ms;
+        arg[prod] = v;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  DS_CUDA(err);
+  p.var_fwd = arg[0];
+  p.var_bwd = arg[1];
+  h->tuned.push_back({A.rowptr, A.colidx, A.m, A.n, A.nnz, p.l, h->opt.form, arg[0], arg[1], best[0], best[1]});
+  return DASHSVD_OK;
+}
+
 int status_from_control(const Control& c) {
   if (c.status & kStatusNonFinite) return DASHSVD_ENONFINITE;
   if (c.status & kStatusNoConv) return DASHSVD_ENOCONV;
@@ -304,7 +364,8 @@ int dashsvd_create(dashsvd_handle* out, const dashsvd_options* opt, void* cuda_s
     h->opt = *opt;
   else
     dashsvd_options_init(&h->opt);
-  if (h->opt.alpha_prev_mode != 0 && h->opt.alpha_prev_mode != 1) {
+  if ((h->opt.alpha_prev_mode != 0 && h->opt.alpha_prev_mode != 1) || h->opt.spmm_variant < -1 ||
+      h->opt.spmm_variant >= kSpmmVariants) {
     delete h;
     return DASHSVD_EINVAL;
   }
@@ -429,7 +490,6 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
   p.part_fwd.seg_nnz = p.part_fwd.seg_row + p.part_fwd.segments + 1;
   p.part_bwd.seg_row = as<int32_t>(h->seg_bwd);
   p.part_bwd.seg_nnz = p.part_bwd.seg_row + p.part_bwd.segments + 1;
-  // work split: merge path where row lengths are very uneven, else warp per row
   const int forced = h->opt.spmm_variant;
   p.var_fwd = forced >= 0 ? forced : 1;
   p.var_bwd = forced >= 0 ? forced : 1;
@@ -439,6 +499,7 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
                                as<int32_t>(h->cursor), as<int32_t>(h->scan_tmp), st));
   DS_CUDA(launch_spmm_partition(p.Aw, p.part_fwd, st));
   DS_CUDA(launch_spmm_partition(p.AwT, p.part_bwd, st));
+  if (forced < 0 && (rc = autotune_spmm(h, p, *A)) != DASHSVD_OK) return rc;
 
   if (h->opt.use_graph) {
     GraphKey key;
@@ -524,7 +585,7 @@ static int spmm_common(dashsvd_handle h, const dashsvd_csr* A, const float* X, i
   if (!h || !csr_ok(A) || !X || !Y || l < 1 || l > DASHSVD_MAX_L) return DASHSVD_EINVAL;
   if (ldx < l || ldy < l || ldx % 4 || ldy % 4 || !aligned16(X) || !aligned16(Y)) return DASHSVD_EINVAL;
   if (alpha && (!Q || ldq < l || ldq % 4 || !aligned16(Q))) return DASHSVD_EINVAL;
-  if (variant < -1 || variant > 1) return DASHSVD_EINVAL;
+  if (variant < -1 || variant >= kSpmmVariants) return DASHSVD_EINVAL;
   SpmmPart part;
   part.segments = spmm_segments(*A, h->num_sms);
   const int64_t ldc = ((l + 3) / 4) * 4;
@@ -543,7 +604,7 @@ static int spmm_common(dashsvd_handle h, const dashsvd_csr* A, const float* X, i
   part.seg_row = as<int32_t>(h->seg_fwd);
   part.seg_nnz = part.seg_row + part.segments + 1;
   const int var = variant < 0 ? 1 : variant;
-  if (var == 1) DS_CUDA(launch_spmm_partition(*A, part, h->stream));
+  if (var & 1) DS_CUDA(launch_spmm_partition(*A, part, h->stream));
   DS_CUDA(launch_spmm(*A, part, X, ldx, l, Y, ldy, alpha, Q, ldq, var, scr, h->num_sms, h->stream));
   return DASHSVD_OK;
 }

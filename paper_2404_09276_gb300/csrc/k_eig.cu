@@ -43,18 +43,21 @@ __device__ __forceinline__ void rr_pair(int i, int step, int N, int& p, int& q) 
   }
 }
 
+// Rotation of pair i in the current step, packed for two 16-byte loads.
+struct __align__(16) PairRec {
+  int p, q, offp, offq;  // indices and packed-row offsets (element (a, b), a <= b, at off[a] + b)
+  float c, s, t;
+  int rot;
+};
+
 struct PairSmem {
-  int p[kMaxN / 2], q[kMaxN / 2];
-  float c[kMaxN / 2], s[kMaxN / 2], t[kMaxN / 2];
-  int rot[kMaxN / 2];
-  int off[kMaxN];  // packed upper triangle: element (a, b), a <= b, at off[a] + b
+  PairRec r[kMaxN / 2];
+  int off[kMaxN];
   int count;
   float gmax;
 };
 
-constexpr int kMaxBlocksPerThread = (kMaxN / 2 * (kMaxN / 2 + 1) / 2 + kJacThreads - 1) / kJacThreads;
-
-__device__ __forceinline__ int pki(const int* off, int a, int b) { return a <= b ? off[a] + b : off[b] + a; }
+__device__ __forceinline__ int pko(int a, int offa, int b, int offb) { return a <= b ? offa + b : offb + a; }
 
 __global__ void __launch_bounds__(kJacThreads) jacobi_f32_kernel(const float* __restrict__ Gin, int64_t ldg, int l,
                                                                  EigWork wk) {
@@ -63,6 +66,7 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_f32_kernel(const float* __
   const int N = l + (l & 1);
   const int P = N / 2;
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
   for (int a = tid; a < N; a += nt) ps.off[a] = a * N - ((a * (a - 1)) >> 1) - a;
   if (tid == 0) ps.gmax = 0.f;
   __syncthreads();
@@ -78,28 +82,9 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_f32_kernel(const float* __
     }
   }
   atomicMax(reinterpret_cast<int*>(&ps.gmax), __float_as_int(gm));  // non-negative floats order as ints
-  // this thread's 2x2 blocks (I, J), I <= J, fixed for the whole kernel
-  int bI[kMaxBlocksPerThread], bJ[kMaxBlocksPerThread];
-  const int T = P * (P + 1) / 2;
-#pragma unroll
-  for (int u = 0; u < kMaxBlocksPerThread; ++u) {
-    const int b = tid + u * nt;
-    bI[u] = -1;
-    bJ[u] = 0;
-    if (b < T) {
-      // row I of the triangle: start(I) = I P - I (I - 1) / 2 <= b < start(I + 1)
-      const float disc = (float)(2 * P + 1) * (float)(2 * P + 1) - 8.f * (float)b;
-      int I = (int)((2.f * P + 1.f - sqrtf(fmaxf(disc, 0.f))) * 0.5f);
-      if (I < 0) I = 0;
-      if (I > P - 1) I = P - 1;
-      while (I > 0 && I * P - ((I * (I - 1)) >> 1) > b) --I;
-      while (I + 1 < P && (I + 1) * P - (((I + 1) * I) >> 1) <= b) ++I;
-      bI[u] = I;
-      bJ[u] = I + (b - (I * P - ((I * (I - 1)) >> 1)));
-    }
-  }
   __syncthreads();
   const float tiny = ps.gmax * 1e-30f + 1e-35f;
+  const int F = (P + 1) / 2;  // folded pair-rows: I and P-1-I share one row of P+1 blocks
   float2* log = wk.log;
   int sweep = 0;
   bool converged = false;
@@ -110,12 +95,15 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_f32_kernel(const float* __
       if (tid < P) {
         int p, q;
         rr_pair(tid, step, N, p, q);
-        ps.p[tid] = p;
-        ps.q[tid] = q;
+        PairRec rec;
+        rec.p = p;
+        rec.q = q;
+        rec.offp = ps.off[p];
+        rec.offq = ps.off[q];
         float c = 1.f, s = 0.f, t = 0.f;
         int rot = 0;
         if (p < l && q < l) {
-          const float app = G[ps.off[p] + p], aqq = G[ps.off[q] + q], apq = G[pki(ps.off, p, q)];
+          const float app = G[rec.offp + p], aqq = G[rec.offq + q], apq = G[pko(p, rec.offp, q, rec.offq)];
           const float thr = kEps32 * sqrtf(fabsf(app) * fabsf(aqq));
           if (fabsf(apq) > thr && fabsf(apq) > tiny) {
             // correctly rounded sqrt and division keep c^2 + s^2 = 1 to an ulp,
@@ -129,42 +117,45 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_f32_kernel(const float* __
             atomicAdd(&ps.count, 1);
           }
         }
-        ps.c[tid] = c;
-        ps.s[tid] = s;
-        ps.t[tid] = t;
-        ps.rot[tid] = rot;
+        rec.c = c;
+        rec.s = s;
+        rec.t = t;
+        rec.rot = rot;
+        ps.r[tid] = rec;
         log[((int64_t)sweep * (N - 1) + step) * P + tid] = make_float2(c, s);
       }
       __syncthreads();
-      // G <- J^T G J on this thread's 2x2 blocks
-#pragma unroll
-      for (int u = 0; u < kMaxBlocksPerThread; ++u) {
-        const int I = bI[u];
-        if (I < 0) continue;
-        const int J = bJ[u];
-        const int rI = ps.rot[I], rJ = ps.rot[J];
-        if (!rI && !rJ) continue;
-        const int p1 = ps.p[I], q1 = ps.q[I];
-        if (I == J) {
-          const float t = ps.t[I];
-          const int ipq = pki(ps.off, p1, q1);
-          const float apq = G[ipq];
-          G[ps.off[p1] + p1] -= t * apq;
-          G[ps.off[q1] + q1] += t * apq;
-          G[ipq] = 0.f;
-          continue;
+      // G <- J^T G J on the 2x2 blocks (I, J), I <= J: warp per folded pair-row
+      for (int f = warp; f < F; f += nwarps) {
+        const int Ia = f, Ib = P - 1 - f;
+        const int na = P - Ia;                  // blocks of row Ia
+        const int nb = (Ib != Ia) ? P - Ib : 0;  // blocks of row Ib
+        const PairRec ra = ps.r[Ia];
+        const PairRec rb = ps.r[Ib];
+        for (int k = lane; k < na + nb; k += 32) {
+          const bool first = k < na;
+          const PairRec& ri = first ? ra : rb;
+          const int J = first ? Ia + k : Ib + (k - na);
+          const PairRec rj = ps.r[J];
+          if (!ri.rot && !rj.rot) continue;
+          if (first ? J == Ia : J == Ib) {  // diagonal block
+            const int ipq = pko(ri.p, ri.offp, ri.q, ri.offq);
+            const float apq = G[ipq];
+            G[ri.offp + ri.p] -= ri.t * apq;
+            G[ri.offq + ri.q] += ri.t * apq;
+            G[ipq] = 0.f;
+            continue;
+          }
+          const int i11 = pko(ri.p, ri.offp, rj.p, rj.offp), i12 = pko(ri.p, ri.offp, rj.q, rj.offq);
+          const int i21 = pko(ri.q, ri.offq, rj.p, rj.offp), i22 = pko(ri.q, ri.offq, rj.q, rj.offq);
+          const float x11 = G[i11], x12 = G[i12], x21 = G[i21], x22 = G[i22];
+          const float y11 = ri.c * x11 - ri.s * x21, y12 = ri.c * x12 - ri.s * x22;
+          const float y21 = ri.s * x11 + ri.c * x21, y22 = ri.s * x12 + ri.c * x22;
+          G[i11] = rj.c * y11 - rj.s * y12;
+          G[i12] = rj.s * y11 + rj.c * y12;
+          G[i21] = rj.c * y21 - rj.s * y22;
+          G[i22] = rj.s * y21 + rj.c * y22;
         }
-        const int p2 = ps.p[J], q2 = ps.q[J];
-        const float c1 = ps.c[I], s1 = ps.s[I], c2 = ps.c[J], s2 = ps.s[J];
-        const int i11 = pki(ps.off, p1, p2), i12 = pki(ps.off, p1, q2);
-        const int i21 = pki(ps.off, q1, p2), i22 = pki(ps.off, q1, q2);
-        const float x11 = G[i11], x12 = G[i12], x21 = G[i21], x22 = G[i22];
-        const float y11 = c1 * x11 - s1 * x21, y12 = c1 * x12 - s1 * x22;
-        const float y21 = s1 * x11 + c1 * x21, y22 = s1 * x12 + c1 * x22;
-        G[i11] = c2 * y11 - s2 * y12;
-        G[i12] = s2 * y11 + c2 * y12;
-        G[i21] = c2 * y21 - s2 * y22;
-        G[i22] = s2 * y21 + c2 * y22;
       }
       __syncthreads();
     }
@@ -185,11 +176,13 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_f32_kernel(const float* __
 // ------------------------------------------------------------- kernel 2
 
 constexpr int kVecWarps = 8;
+constexpr int kBatch = 16;  // log steps staged per batch
 
 struct FinishSmem {
   int rank[kMaxL];
   double S[kMaxL];  // by sorted position
   float x[kVecWarps][kMaxN];
+  float2 logb[2][kBatch * (kMaxN / 2)];
   double red[32];
   int flag;
 };
@@ -222,27 +215,48 @@ __global__ void __launch_bounds__(kVecWarps * 32) eigvec_finish_kernel(EigWork w
   __syncthreads();
   const int nsteps = wk.hdr[0] * (N - 1);
 
-  // eigenvector c = J_1 (J_2 (... (J_T e_c)))
+  // eigenvector c = J_1 (J_2 (... (J_T e_c))): replay the log backwards, in
+  // batches of kBatch steps staged in shared memory by the whole CTA
   const int c = blockIdx.x * kVecWarps + warp;
-  if (c < l) {
-    float* x = fs.x[warp];
-    for (int j = lane; j < N; j += 32) x[j] = j == c ? 1.f : 0.f;
-    __syncwarp();
-    for (int t = nsteps - 1; t >= 0; --t) {
-      const int step = t % (N - 1);
-      const float2* lg = wk.log + (int64_t)t * P;
-      for (int i = lane; i < P; i += 32) {
-        const float2 cs = lg[i];
-        if (cs.y != 0.f) {
-          int p, q;
-          rr_pair(i, step, N, p, q);
-          const float xp = x[p], xq = x[q];
-          x[p] = cs.x * xp + cs.y * xq;
-          x[q] = -cs.y * xp + cs.x * xq;
+  float* x = fs.x[warp];
+  for (int j = lane; j < N; j += 32) x[j] = j == c ? 1.f : 0.f;
+  const int nbatch = (nsteps + kBatch - 1) / kBatch;
+  // batch b covers steps [nsteps - (b+1) kBatch, nsteps - b kBatch)
+  auto stage = [&](int b, int buf) {
+    const int t1 = nsteps - b * kBatch;
+    const int t0 = t1 - kBatch > 0 ? t1 - kBatch : 0;
+    const float2* src = wk.log + (int64_t)t0 * P;
+    float2* dst = fs.logb[buf];
+    const int n = (t1 - t0) * P;
+    for (int i = tid; i < n; i += nt) dst[i] = src[i];
+  };
+  if (nbatch > 0) stage(0, 0);
+  __syncthreads();
+  for (int b = 0; b < nbatch; ++b) {
+    if (b + 1 < nbatch) stage(b + 1, (b + 1) & 1);  // next batch loads while this one is applied
+    const int t1 = nsteps - b * kBatch;
+    const int t0 = t1 - kBatch > 0 ? t1 - kBatch : 0;
+    const float2* lg = fs.logb[b & 1];
+    if (c < l) {
+      for (int t = t1 - 1; t >= t0; --t) {
+        const int step = t % (N - 1);
+        const float2* lgt = lg + (t - t0) * P;
+        for (int i = lane; i < P; i += 32) {
+          const float2 cs = lgt[i];
+          if (cs.y != 0.f) {
+            int p, q;
+            rr_pair(i, step, N, p, q);
+            const float xp = x[p], xq = x[q];
+            x[p] = cs.x * xp + cs.y * xq;
+            x[q] = -cs.y * xp + cs.x * xq;
+          }
         }
+        __syncwarp();
       }
-      __syncwarp();
     }
+    __syncthreads();
+  }
+  if (c < l) {
     // sign: largest |entry| (lowest index on ties) positive
     float best = -1.f;
     int bj = 0;

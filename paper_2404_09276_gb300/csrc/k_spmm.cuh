@@ -1,32 +1,13 @@
-// Sparse x tall-skinny dense products of the power iteration (Alg. 5 step 4):
-//   Y = A X                (A*Q, and B = A*Q at step 9)
-//   Z = A^T Y - alpha Q    (with A^T given in CSR form; the shift is fused)
-//
-// Both products gather rows of the dense operand: for row r of the sparse
-// matrix, y_r = sum_e a_e x_{col(e)}. A warp works on one row at a time; its
-// 32 lanes form 4 teams of 8 lanes, each team takes every 4th nonzero and each
-// lane owns V slots of 4 columns (slot t + 8v for lane t of the team), so a
-// team reads one contiguous run of the row per slot group. The 32 (col, val)
-// pairs of a row chunk are loaded once, coalesced, and broadcast by shuffles;
-// the next chunk's pairs are fetched while the current one is gathered.
-// The dense operand and the output are FP32 or BF16 (the precision form keeps
-// the gathered operands in BF16); accumulation is always FP32.
-//
-// Two work splits (the autotuner picks one per matrix):
-//   variant 0  warp per row: rows strided over persistent warps
-//   variant 1  merge path (Merrill and Garland, SC'16): the merge of row ends
-//              with nonzero indices is cut into equal segments, computed once
-//              per matrix; persistent warps take segments in turn, so very
-//              long rows (hot columns of A^T) are split across warps. Pieces
-//              of split rows go to per-segment carry slots that a fix-up
-//              kernel adds in segment order, so the result does not depend on
-//              scheduling.
+// Sparse x tall-skinny dense product kernels (templates shared by the FP32
+// and BF16 translation units). See k_spmm_f32.cu for the description.
+#pragma once
 #include <cuda_bf16.h>
 
 #include "internal.cuh"
 
 namespace dsvd {
-namespace {
+namespace spmm_detail {
+namespace {  // internal linkage: each including unit gets its own kernels
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kThreads = 256;
@@ -77,27 +58,35 @@ __device__ __forceinline__ void store4(__nv_bfloat16* row, int slot, float4 v) {
 
 // Gather-accumulate one chunk: entries [pos, pos + cnt) of the sparse row,
 // whose (col, val) pairs sit in lanes 0..cnt-1 of (c, a), into acc (this lane's slots).
-template <int V, typename TIn>
+template <int V, int U, typename TIn>
 __device__ __forceinline__ void gather_chunk(int c, float a, int cnt, const TIn* __restrict__ X, int64_t ldx,
                                              int nslot, int lane, float4 (&acc)[V]) {
   const int g = lane >> 3, t = lane & 7;
-  for (int s = 0; 4 * s < cnt; s += 2) {
-    const int src0 = 4 * s + g, src1 = src0 + 4;
-    int c0 = __shfl_sync(kFull, c, src0), c1 = __shfl_sync(kFull, c, src1);
-    const float a0 = __shfl_sync(kFull, a, src0), a1 = __shfl_sync(kFull, a, src1);
-    if (src0 >= cnt) c0 = -1;
-    if (src1 >= cnt) c1 = -1;
-    float4 x0[V], x1[V];
-    const TIn* r0 = X + (int64_t)(c0 < 0 ? 0 : c0) * ldx;
-    const TIn* r1 = X + (int64_t)(c1 < 0 ? 0 : c1) * ldx;
+  // each team takes U entries per round: U x V row slots in flight per lane
+  for (int s = 0; 4 * s < cnt; s += U) {
+    int cu[U];
+    float au[U];
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-      const int slot = t + 8 * v;
-      x0[v] = (c0 >= 0 && slot < nslot) ? load4(r0, slot) : f4_zero();
-      x1[v] = (c1 >= 0 && slot < nslot) ? load4(r1, slot) : f4_zero();
+    for (int u = 0; u < U; ++u) {
+      const int src = 4 * (s + u) + g;
+      cu[u] = __shfl_sync(kFull, c, src & 31);
+      au[u] = __shfl_sync(kFull, a, src & 31);
+      if (src >= cnt) cu[u] = -1;
+    }
+    float4 x[U][V];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const TIn* r = X + (int64_t)(cu[u] < 0 ? 0 : cu[u]) * ldx;
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const int slot = t + 8 * v;
+        x[u][v] = (cu[u] >= 0 && slot < nslot) ? load4(r, slot) : f4_zero();
+      }
     }
 #pragma unroll
-    for (int v = 0; v < V; ++v) acc[v] = f4_fma(a1, x1[v], f4_fma(a0, x0[v], acc[v]));
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[v] = f4_fma(au[u], x[u][v], acc[v]);
   }
 }
 
@@ -165,8 +154,8 @@ __device__ __forceinline__ void store_carry(const float4 (&acc)[V], float* __res
   }
 }
 
-template <int V, typename TIn, typename TOut, typename TQ>
-__global__ void __launch_bounds__(kThreads) spmm_rows_kernel(const int32_t* __restrict__ rowptr,
+template <int V, int U, int MINB, typename TIn, typename TOut, typename TQ>
+__global__ void __launch_bounds__(kThreads, MINB) spmm_rows_kernel(const int32_t* __restrict__ rowptr,
                                                              const int32_t* __restrict__ col,
                                                              const float* __restrict__ val, int64_t m, int64_t nnz,
                                                              const TIn* __restrict__ X, int64_t ldx,
@@ -196,7 +185,7 @@ __global__ void __launch_bounds__(kThreads) spmm_rows_kernel(const int32_t* __re
     float an;
     load_pairs(col, val, next, next_e, lane, cn, an);
     const int cnt = (int)(e - pos < 32 ? e - pos : 32);
-    gather_chunk<V, TIn>(c, a, cnt, X, ldx, nslot, lane, acc);
+    gather_chunk<V, U, TIn>(c, a, cnt, X, ldx, nslot, lane, acc);
     c = cn;
     a = an;
     if (pos + 32 >= e) {  // row done
@@ -243,8 +232,8 @@ __global__ void merge_partition_kernel(const int32_t* __restrict__ rowptr, int64
   seg_nnz[s] = (int32_t)j;
 }
 
-template <int V, typename TIn, typename TOut, typename TQ>
-__global__ void __launch_bounds__(kThreads) spmm_merge_kernel(const int32_t* __restrict__ rowptr,
+template <int V, int U, int MINB, typename TIn, typename TOut, typename TQ>
+__global__ void __launch_bounds__(kThreads, MINB) spmm_merge_kernel(const int32_t* __restrict__ rowptr,
                                                               const int32_t* __restrict__ col,
                                                               const float* __restrict__ val, int64_t m,
                                                               const TIn* __restrict__ X, int64_t ldx,
@@ -287,7 +276,7 @@ __global__ void __launch_bounds__(kThreads) spmm_merge_kernel(const int32_t* __r
       float an;
       load_pairs(col, val, next, k1, lane, cn, an);
       const int cnt = (int)(e - pos < 32 ? e - pos : 32);
-      gather_chunk<V, TIn>(c, a, cnt, X, ldx, nslot, lane, acc);
+      gather_chunk<V, U, TIn>(c, a, cnt, X, ldx, nslot, lane, acc);
       c = cn;
       a = an;
       pos = next;
@@ -350,29 +339,45 @@ __global__ void __launch_bounds__(kThreads) spmm_fixup_kernel(const float* __res
   }
 }
 
-template <int V, typename TIn, typename TOut, typename TQ>
-cudaError_t launch_v(const dashsvd_csr& A, const SpmmPart& part, const TIn* X, int64_t ldx, int l, TOut* Y,
-                     int64_t ldy, const Epilogue<TQ>& ep, int variant, const SpmmScratch& scr, int num_sms,
-                     cudaStream_t st) {
+template <int V, int U, int MINB, typename TIn, typename TOut, typename TQ>
+cudaError_t launch_vc(const dashsvd_csr& A, const SpmmPart& part, const TIn* X, int64_t ldx, int l, TOut* Y,
+                      int64_t ldy, const Epilogue<TQ>& ep, int split, const SpmmScratch& scr, int num_sms,
+                      cudaStream_t st) {
   const int nslot = (l + 3) / 4;
   if (A.m <= 0) return cudaSuccess;
   // persistent warps: more blocks than fit at once are simply queued
   const int64_t grid = (int64_t)num_sms * 8;
-  if (variant == 0) {
+  if (split == 0) {
     const int64_t need = ds_ceil_div(A.m * 32, kThreads);
-    spmm_rows_kernel<V, TIn, TOut, TQ><<<(unsigned)(need < grid ? need : grid), kThreads, 0, st>>>(
+    spmm_rows_kernel<V, U, MINB, TIn, TOut, TQ><<<(unsigned)(need < grid ? need : grid), kThreads, 0, st>>>(
         A.rowptr, A.colidx, A.val, A.m, A.nnz, X, ldx, Y, ldy, nslot, ep);
     return cudaGetLastError();
   }
   if (part.segments > scr.max_segments || scr.ldc < ((l + 3) / 4) * 4) return cudaErrorInvalidValue;
   const int64_t need = ds_ceil_div(part.segments * 32, kThreads);
-  spmm_merge_kernel<V, TIn, TOut, TQ><<<(unsigned)(need < grid ? need : grid), kThreads, 0, st>>>(
+  spmm_merge_kernel<V, U, MINB, TIn, TOut, TQ><<<(unsigned)(need < grid ? need : grid), kThreads, 0, st>>>(
       A.rowptr, A.colidx, A.val, A.m, X, ldx, Y, ldy, nslot, ep, part, scr.carry, scr.carry_row, scr.ldc);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   spmm_fixup_kernel<TOut, TQ><<<(unsigned)ds_ceil_div(2 * part.segments * 32, kThreads), kThreads, 0, st>>>(
       scr.carry, scr.carry_row, 2 * part.segments, scr.ldc, Y, ldy, ep);
   return cudaGetLastError();
+}
+
+// variant = split (0 warp per row, 1 merge path) + 2 * configuration, where
+// configuration 0: two entries per team per round; 1: four entries per round;
+// 2: two entries per round with registers capped for four blocks per SM
+template <int V, typename TIn, typename TOut, typename TQ>
+cudaError_t launch_v(const dashsvd_csr& A, const SpmmPart& part, const TIn* X, int64_t ldx, int l, TOut* Y,
+                     int64_t ldy, const Epilogue<TQ>& ep, int variant, const SpmmScratch& scr, int num_sms,
+                     cudaStream_t st) {
+  const int split = variant & 1;
+  switch (variant >> 1) {
+    case 0: return launch_vc<V, 2, 1, TIn, TOut, TQ>(A, part, X, ldx, l, Y, ldy, ep, split, scr, num_sms, st);
+    case 1: return launch_vc<V, 4, 1, TIn, TOut, TQ>(A, part, X, ldx, l, Y, ldy, ep, split, scr, num_sms, st);
+    case 2: return launch_vc<V, 2, 4, TIn, TOut, TQ>(A, part, X, ldx, l, Y, ldy, ep, split, scr, num_sms, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <typename TIn, typename TOut, typename TQ>
@@ -395,43 +400,5 @@ cudaError_t dispatch(const dashsvd_csr& A, const SpmmPart& part, const TIn* X, i
 }
 
 }  // namespace
-
-int64_t spmm_segments(const dashsvd_csr& A, int num_sms) {
-  // about four segments per resident warp (at most 24 warps per SM fit), and
-  // at least 256 merge items (rows + nonzeros) per segment
-  const int64_t total = A.m + A.nnz;
-  int64_t segs = (int64_t)num_sms * 24 * 4;
-  const int64_t cap = ds_ceil_div(total, 256);
-  if (segs > cap) segs = cap;
-  return segs < 1 ? 1 : segs;
-}
-
-cudaError_t launch_spmm_partition(const dashsvd_csr& A, SpmmPart& part, cudaStream_t st) {
-  const int64_t total = A.m + A.nnz;
-  part.per = ds_ceil_div(total, part.segments);
-  if (part.per < 1) part.per = 1;
-  merge_partition_kernel<<<(unsigned)ds_ceil_div(part.segments + 1, 256), 256, 0, st>>>(
-      A.rowptr, A.m, A.nnz, part.segments, part.per, part.seg_row, part.seg_nnz);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_spmm(const dashsvd_csr& A, const SpmmPart& part, const float* X, int64_t ldx, int l, float* Y,
-                        int64_t ldy, const double* alpha, const float* Q, int64_t ldq, int variant,
-                        const SpmmScratch& scr, int num_sms, cudaStream_t st) {
-  return dispatch<float, float, float>(A, part, X, ldx, l, Y, ldy, alpha, Q, ldq, variant, scr, num_sms, st);
-}
-
-cudaError_t launch_spmm_bf16(const dashsvd_csr& A, const SpmmPart& part, const void* X, int64_t ldx, int l, void* Y,
-                             bool y_bf16, int64_t ldy, const double* alpha, const void* Q, int64_t ldq, int variant,
-                             const SpmmScratch& scr, int num_sms, cudaStream_t st) {
-  const __nv_bfloat16* Xb = reinterpret_cast<const __nv_bfloat16*>(X);
-  const __nv_bfloat16* Qb = reinterpret_cast<const __nv_bfloat16*>(Q);
-  if (y_bf16)
-    return dispatch<__nv_bfloat16, __nv_bfloat16, __nv_bfloat16>(A, part, Xb, ldx, l,
-                                                                 reinterpret_cast<__nv_bfloat16*>(Y), ldy, alpha, Qb,
-                                                                 ldq, variant, scr, num_sms, st);
-  return dispatch<__nv_bfloat16, float, __nv_bfloat16>(A, part, Xb, ldx, l, reinterpret_cast<float*>(Y), ldy, alpha,
-                                                       Qb, ldq, variant, scr, num_sms, st);
-}
-
+}  // namespace spmm_detail
 }  // namespace dsvd
