@@ -190,6 +190,25 @@ int dashsvd_gram(dashsvd_handle h, const float* C, int64_t rows, int l, int64_t 
 int dashsvd_gram_bf16x3(dashsvd_handle h, const float* C, int64_t rows, int l, int64_t ldc, double* G,
                         int64_t ldg);
 
+/* G = C^T C like dashsvd_gram, for callers that cannot allocate device memory
+ * (code running during CUDA graph capture, hosts whose own allocator owns the
+ * GPU's memory, real-time paths that must not enter the driver's allocator).
+ * The paper has no counterpart; this is an interface addition of this library.
+ * It takes no handle and never calls cudaMalloc, cudaFree or an allocating
+ * library routine: the per-chunk partial sums live in one file-scope device
+ * array of 16 MiB, held on every GPU that loads the library until the process
+ * exits. C: rows x ldc FP32 (ldc % 4 == 0, 16-byte aligned), G: l x ldg FP32,
+ * l <= DASHSVD_MAX_L (larger l returns DASHSVD_EINVAL); any number of rows
+ * (fewer, longer row chunks when the array would overflow). Asynchronous on
+ * `cuda_stream` (a cudaStream_t, NULL = legacy default stream).
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. All calls share the one array and each call
+ * overwrites it, so calls whose work overlaps on the GPU (two streams, two
+ * threads) race and must be serialised by the caller. */
+int dashsvd_gram_noalloc(const float* C, int64_t rows, int l, int64_t ldc, float* G, int64_t ldg,
+                         void* cuda_stream);
+
 /* Out = C W (Alg. 3 step 3 with W = V S^-1; Alg. 5 step 11 with W = V(:, 1:k)).
  * C: rows x ldc (first l columns used), W: l x ldw (first `cols` columns used),
  * Out: rows x ldo with ldo >= cols; columns cols .. ldo-1 are set to 0. */

@@ -37,7 +37,7 @@ EXPORTS = (
     "dashsvd_options_init", "dashsvd_create", "dashsvd_destroy", "dashsvd_run", "dashsvd_get_trace",
     "dashsvd_load_mlp", "dashsvd_status_string", "dashsvd_last_error", "dashsvd_gaussian",
     "dashsvd_csr_transpose", "dashsvd_spmm", "dashsvd_spmm_shift", "dashsvd_gram", "dashsvd_gram_bf16x3",
-    "dashsvd_project", "dashsvd_eigsvd",
+    "dashsvd_project", "dashsvd_eigsvd", "dashsvd_gram_noalloc",
 )
 
 
@@ -88,6 +88,7 @@ def _load():
         "dashsvd_gram_bf16x3": (I, [P, P, I64, I, I64, P, I64]),
         "dashsvd_project": (I, [P, P, I64, I, I64, P, I64, I, P, I64]),
         "dashsvd_eigsvd": (I, [P, P, I64, I, I64, P, I64, P, P, I]),
+        "dashsvd_gram_noalloc": (I, [P, I64, I, I64, P, I64, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -121,6 +122,7 @@ dashsvd_gram = _export("dashsvd_gram")
 dashsvd_gram_bf16x3 = _export("dashsvd_gram_bf16x3")
 dashsvd_project = _export("dashsvd_project")
 dashsvd_eigsvd = _export("dashsvd_eigsvd")
+dashsvd_gram_noalloc = _export("dashsvd_gram_noalloc")
 
 
 class DashSvdError(RuntimeError):

@@ -93,6 +93,8 @@ cudaError_t launch_spmm_bf16(const dashsvd_csr& A, const SpmmPart& part, const v
 size_t gram_partial_floats(int64_t rows, int l, int num_sms);
 cudaError_t launch_gram(const float* C, int64_t rows, int l, int64_t ldc, float* G, int64_t ldg,
                         float* partial, int num_sms, cudaStream_t st);
+cudaError_t launch_gram_bounded(const float* C, int64_t rows, int l, int64_t ldc, float* G, int64_t ldg,
+                                float* partial, size_t max_partial, int num_sms, cudaStream_t st);
 
 // Gram on tcgen05 (BF16x3): G64 (and G32 if non-null) from C; `err` is set on a wait timeout.
 size_t gram_tc_partial_floats(int64_t rows, int l, int num_sms);

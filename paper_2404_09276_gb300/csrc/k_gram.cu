@@ -158,6 +158,38 @@ cudaError_t launch_tm(const GramPlan& g, const float* C, int64_t rows, int l, in
 
 }  // namespace
 
+// Same kernels as launch_gram, with the chunk count lowered until the per-chunk
+// partial blocks fit in `max_partial` floats of caller-provided scratch.
+cudaError_t launch_gram_bounded(const float* C, int64_t rows, int l, int64_t ldc, float* G, int64_t ldg,
+                                float* partial, size_t max_partial, int num_sms, cudaStream_t st) {
+  GramPlan g = plan_gram(rows, l, num_sms);
+  const size_t per_chunk = (size_t)g.pairs * g.BS * g.BS;
+  if (per_chunk > max_partial) return cudaErrorInvalidValue;
+  const int64_t max_chunks = (int64_t)(max_partial / per_chunk);
+  if (g.chunks > max_chunks) {
+    g.chunk_rows = ds_ceil_div(ds_ceil_div(rows, max_chunks), kKT) * kKT;
+    g.chunks = (int)ds_ceil_div(rows, g.chunk_rows);
+  }
+  cudaError_t e;
+  switch (g.TM) {
+    case 1: e = launch_tm<1>(g, C, rows, l, ldc, partial, st); break;
+    case 2: e = launch_tm<2>(g, C, rows, l, ldc, partial, st); break;
+    case 3: e = launch_tm<3>(g, C, rows, l, ldc, partial, st); break;
+    case 4: e = launch_tm<4>(g, C, rows, l, ldc, partial, st); break;
+    case 5: e = launch_tm<5>(g, C, rows, l, ldc, partial, st); break;
+    case 6: e = launch_tm<6>(g, C, rows, l, ldc, partial, st); break;
+    case 7: e = launch_tm<7>(g, C, rows, l, ldc, partial, st); break;
+    case 8: e = launch_tm<8>(g, C, rows, l, ldc, partial, st); break;
+    case 9: e = launch_tm<9>(g, C, rows, l, ldc, partial, st); break;
+    case 10: e = launch_tm<10>(g, C, rows, l, ldc, partial, st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
+  gram_reduce_kernel<<<(unsigned)ds_ceil_div((int64_t)l * l, 256), 256, 0, st>>>(partial, g.chunks, g.nb, g.BS, l, G,
+                                                                                 ldg);
+  return cudaGetLastError();
+}
+
 size_t gram_partial_floats(int64_t rows, int l, int num_sms) {
   const GramPlan g = plan_gram(rows, l, num_sms);
   return (size_t)g.chunks * g.pairs * g.BS * g.BS;
