@@ -60,6 +60,8 @@ def _args():
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (testing only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-reps", type=int, default=20)
+    ap.add_argument("--form", default="both", choices=["both", "plain", "precision"],
+                    help="both: time the plain FP32 form and the chosen (precision) form")
     ap.add_argument("--no-graph", action="store_true",
                     help="host-driven loop instead of the CUDA graph (profilers see every launch)")
     return ap.parse_args()
@@ -208,48 +210,32 @@ def _time_kernel(fn, reps, stream):
     return s.elapsed_time(e) / 1e3 / reps
 
 
-def ours(args):
-    import numpy as np
+FORMS = {
+    "plain": "plain FP32 (FP32 SpMM, SIMT Gram/projection, FP32 Jacobi eig)",
+    "precision": "precision (BF16 gathered Q/Y, BF16x3 tcgen05 Gram and projection, FP32 Jacobi refined in FP64, "
+                 "FP64 shift/PVE)",
+}
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    A, prm, name = _workload(args.config, args.scale)
+
+def _launches_per_run(form, passes, var_fwd, var_bwd):
+    kpv = lambda v: 2 if (v & 1) else 1  # noqa: E731  kernels per SpMM launch (merge path adds its fix-up)
+    eig = 3 if form == "plain" else 3 + 1 + 2 * 5  # Jacobi, replay, finish (+ FP64 refinement)
+    setup = 5 + 2  # CSR transpose, merge-path partitions
+    prologue = 1 + kpv(var_bwd) + 2 + eig + 1
+    per_pass = kpv(var_fwd) + kpv(var_bwd) + 2 + eig + 1
+    final = kpv(var_fwd) + 2 + eig + 2
+    return setup + prologue + passes * per_pass + final
+
+
+def _measure_form(form, args, ds, torch, A, Ad, prm, stream, flush, barrier, world, local):
+    """Time `steps` full runs of one form, plus its trace, e2e and per-kernel times."""
     k, s, p_max, tol = prm["k"], prm["s"], prm["p_max"], prm["tol"]
     l = k + s
-
-    # CPU baseline first (separate process, before this process touches CUDA)
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        npz = _save_npz(A)
-        try:
-            cpu = _oracle_leg(npz, k, s, 2)
-        finally:
-            os.unlink(npz)
-
-    import torch
-
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl")
-    import paper_2404_09276_gb300 as ds
-
-    stream = torch.cuda.current_stream()
-    Ad = ds.CsrDevice.from_host(A)
+    fcode = ds.DASHSVD_FORM_PRECISION if form == "precision" else ds.DASHSVD_FORM_PLAIN
     U = torch.empty((A.m, k), dtype=torch.float32, device="cuda")
     S = torch.empty((k,), dtype=torch.float32, device="cuda")
     V = torch.empty((A.n, k), dtype=torch.float32, device="cuda")
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
-    h = ds.Handle(stream=stream, use_graph=0 if args.no_graph else 1)
-
-    def barrier():
-        torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-            torch.cuda.synchronize()
-
+    h = ds.Handle(stream=stream, use_graph=0 if args.no_graph else 1, form=fcode)
     infos = []
     for _ in range(args.warmup):
         infos.append(h.run(Ad, k, s, p_max, tol, U, S, V)[3])
@@ -272,17 +258,14 @@ def ours(args):
     info = infos[-1]
     passes = info.passes
     var_fwd, var_bwd = info.spmm_variant & 0xFF, (info.spmm_variant >> 8) & 0xFF
-    kpv = lambda v: 2 if (v & 1) else 1  # noqa: E731  kernels per SpMM launch (merge path adds its fix-up)
-    launches_per_run = 5 + 2 + (1 + kpv(var_bwd) + 2 + 2 + 1) + passes * (kpv(var_fwd) + kpv(var_bwd) + 2 + 2 + 1) + \
-        (kpv(var_fwd) + 2 + 2 + 2)
 
-    # ---- one untimed run with the per-pass trace (shift, PVE ratio, Jacobi sweeps)
-    with ds.Handle(stream=stream, record_trace=1) as ht:
+    # one untimed run with the per-pass trace (shift, PVE ratio, Jacobi sweeps)
+    with ds.Handle(stream=stream, record_trace=1, form=fcode) as ht:
         ht.run(Ad, k, s, p_max, tol, U, S, V)
         trace = [{"pass": j, "alpha": a_used, "pve_ratio": ratio, "eig_sweeps": sw}
                  for j, a_used, ratio, a_next, sw, _ in ht.trace()]
 
-    # ---- end to end: A from pinned host memory, U, S, V back to pinned host memory
+    # end to end: A from pinned host memory, U, S, V back to pinned host memory
     rp_h = torch.from_numpy(A.rowptr).pin_memory()
     ci_h = torch.from_numpy(A.colidx).pin_memory()
     va_h = torch.from_numpy(A.val).pin_memory()
@@ -310,10 +293,11 @@ def ours(args):
         e2e_step()
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
-    h2d = A.rowptr.nbytes + A.colidx.nbytes + A.val.nbytes
-    d2h = (A.m * k + k + A.n * k) * 4
+    e2e = {"value": statistics.median(e2e_times), "unit": "s",
+           "h2d_bytes_per_step": A.rowptr.nbytes + A.colidx.nbytes + A.val.nbytes,
+           "d2h_bytes_per_step": (A.m * k + k + A.n * k) * 4}
 
-    # ---- per-kernel times through the step-level entry points (same matrix, same shapes)
+    # per-kernel times through the step-level entry points (same matrix, same shapes)
     ld = ds.ld_for(l)
     g = torch.Generator(device="cuda").manual_seed(0)
     Q = torch.randn((A.n, ld), device="cuda", generator=g)
@@ -324,17 +308,30 @@ def ours(args):
     alpha = torch.tensor([0.5], dtype=torch.float64, device="cuda")
     At = h.csr_transpose(Ad)
     reps = args.kernel_reps
-    kt = {
-        "spmm_fwd": _time_kernel(lambda: h.spmm(Ad, Q, l, out=Y, variant=var_fwd), reps, stream),
-        "spmm_bwd": _time_kernel(lambda: h.spmm_shift(At, Y, l, alpha, Q, out=Z, variant=var_bwd), reps, stream),
-        "gram": _time_kernel(lambda: h.gram(Z, l), reps, stream),
-        "project": _time_kernel(lambda: h.project(Z, l, W, l, out=Q, ldo=ld), reps, stream),
-    }
-    t_eigsvd = _time_kernel(lambda: h.eigsvd(Z, l), max(3, reps // 4), stream)
+    if form == "plain":
+        kt = {
+            "spmm_fwd": _time_kernel(lambda: h.spmm(Ad, Q, l, out=Y, variant=var_fwd), reps, stream),
+            "spmm_bwd": _time_kernel(lambda: h.spmm_shift(At, Y, l, alpha, Q, out=Z, variant=var_bwd), reps, stream),
+            "gram": _time_kernel(lambda: h.gram(Z, l), reps, stream),
+            "project": _time_kernel(lambda: h.project(Z, l, W, l, out=Q, ldo=ld), reps, stream),
+        }
+        bq = by = 4
+    else:
+        Qb = Q.to(torch.bfloat16)
+        Yb = torch.empty((A.m, ld), dtype=torch.bfloat16, device="cuda")
+        kt = {
+            "spmm_fwd": _time_kernel(lambda: h.spmm_bf16(Ad, Qb, l, Yb, variant=var_fwd), reps, stream),
+            "spmm_bwd": _time_kernel(lambda: h.spmm_bf16(At, Yb, l, Z, alpha_dev=alpha, Q=Qb, variant=var_bwd),
+                                     reps, stream),
+            "gram": _time_kernel(lambda: h.gram_bf16x3(Z, l), reps, stream),
+            "project": _time_kernel(lambda: h.project_bf16x3(Z, l, W, l, out=Q, ldo=ld), reps, stream),
+        }
+        bq = by = 2
+    t_eigsvd = _time_kernel(lambda: h.eigsvd(Z, l, form=fcode), max(3, reps // 4), stream)
     kt["eig"] = max(0.0, t_eigsvd - kt["gram"] - kt["project"])
     csr_bytes = 4 * (A.m + 1) + 8 * A.nnz
-    bytes_fwd = csr_bytes + 4 * A.n * l + 4 * A.m * ld
-    bytes_bwd = csr_bytes + 4 * A.m * l + 4 * A.n * l + 4 * A.n * ld
+    bytes_fwd = csr_bytes + bq * A.n * l + by * A.m * ld
+    bytes_bwd = csr_bytes + by * A.m * l + bq * A.n * l + 4 * A.n * ld
     per_run = {
         "spmm_fwd": (passes + 1) * kt["spmm_fwd"],
         "spmm_bwd": (passes + 1) * kt["spmm_bwd"],
@@ -342,53 +339,105 @@ def ours(args):
         "project": (passes + 3) * kt["project"],
         "eig": (passes + 2) * kt["eig"],
     }
-    dom = max(per_run, key=per_run.get)
-    pk = _peaks()
-    fp32_peak = NUM_SMS_GB300 * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    spmm = {
-        "fwd_gbs": bytes_fwd / kt["spmm_fwd"] / 1e9,
-        "bwd_gbs": bytes_bwd / kt["spmm_bwd"] / 1e9,
-        "fwd_bytes": bytes_fwd,
-        "bwd_bytes": bytes_bwd,
-    }
-    spmm["fwd_frac_of_measured_hbm"] = spmm["fwd_gbs"] / pk["hbm_gbs"]
-    spmm["bwd_frac_of_measured_hbm"] = spmm["bwd_gbs"] / pk["hbm_gbs"]
-    if dom in ("spmm_fwd", "spmm_bwd"):
-        gbs = spmm["fwd_gbs" if dom == "spmm_fwd" else "bwd_gbs"]
-        roof = {"kernel": dom, "bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": gbs / pk["hbm_gbs"], "traffic": None, "peak_source": pk["source"]}
-    elif dom in ("gram", "project"):
-        flops = (2 * A.n * l * l) if dom == "project" else (2 * A.n * l * l)
-        tf = flops / kt[dom] / 1e12
-        roof = {"kernel": dom, "bound": "alu", "achieved": tf, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": tf / fp32_peak, "traffic": None,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock"}
-    else:
-        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": None, "traffic": None, "peak_source": "latency-bound single-CTA eigensolver"}
+    spmm = {"fwd_gbs": bytes_fwd / kt["spmm_fwd"] / 1e9, "bwd_gbs": bytes_bwd / kt["spmm_bwd"] / 1e9,
+            "fwd_bytes": bytes_fwd, "bwd_bytes": bytes_bwd, "variants": [var_fwd, var_bwd]}
+    h.close()
+    return {"form": form, "value": t_step, "times": times, "passes": passes, "status": info.status,
+            "pve_surrogate": info.pve_ratio, "trace": trace, "e2e": e2e, "kernels_s": kt,
+            "kernel_s_per_run": per_run, "spmm": spmm, "clocks": clk,
+            "gpu_launches": _launches_per_run(form, passes, var_fwd, var_bwd) * args.steps,
+            "bytes": {"spmm_fwd": bytes_fwd, "spmm_bwd": bytes_bwd}}
 
+
+def _roofline(r, A, l, pk):
+    kt, per_run = r["kernels_s"], r["kernel_s_per_run"]
+    dom = max(per_run, key=per_run.get)
+    fp32_peak = NUM_SMS_GB300 * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    if dom in ("spmm_fwd", "spmm_bwd"):
+        gbs = r["bytes"][dom] / kt[dom] / 1e9
+        return {"kernel": dom, "bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": gbs / pk["hbm_gbs"], "traffic": None, "peak_source": pk["source"] + " HBM copy bandwidth"}
+    if dom in ("gram", "project") and r["form"] == "plain":
+        tf = 2 * A.n * l * l / kt[dom] / 1e12
+        return {"kernel": dom, "bound": "alu", "achieved": tf, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": tf / fp32_peak, "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x max SM clock"}
+    if dom in ("gram", "project"):
+        gbs = 4 * A.n * l / kt[dom] / 1e9
+        return {"kernel": dom, "bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": gbs / pk["hbm_gbs"], "traffic": None, "peak_source": pk["source"] + " HBM copy bandwidth"}
+    return {"kernel": dom, "bound": "alu", "achieved": None, "peak": fp32_peak, "unit": "TFLOP/s", "frac": None,
+            "traffic": None, "peak_source": "latency-bound single-CTA Jacobi eigensolver (no throughput roofline)"}
+
+
+def ours(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    A, prm, name = _workload(args.config, args.scale)
+    k, s = prm["k"], prm["s"]
+    l = k + s
+
+    # CPU baseline first (separate process, before this process touches CUDA)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        npz = _save_npz(A)
+        try:
+            cpu = _oracle_leg(npz, k, s, 2)
+        finally:
+            os.unlink(npz)
+
+    import torch
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    import paper_2404_09276_gb300 as ds
+
+    stream = torch.cuda.current_stream()
+    Ad = ds.CsrDevice.from_host(A)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    forms = ["plain", "precision"] if args.form == "both" else [args.form]
+    res = {f: _measure_form(f, args, ds, torch, A, Ad, prm, stream, flush, barrier, world, local) for f in forms}
+    chosen = res["precision"] if "precision" in res else res[forms[0]]
+    pk = _peaks()
     line = {
-        "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": name, "form": "plain FP32", "l2": "flushed (256 MB write) before each step",
+        "metric": METRIC, "value": chosen["value"], "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": chosen["value"] * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16x3+f64" if chosen["form"] == "precision" else "f32", "data": "synthetic",
+        "config": {"workload": name, "form": FORMS[chosen["form"]],
+                   "l2": "flushed (256 MB write) before each step",
                    "loop": "host-driven" if args.no_graph else "CUDA graph, device-side WHILE",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "passes": passes, "status": info.status, "pve_surrogate": info.pve_ratio, "trace": trace,
-        "roofline": roof, "kernels_s": kt, "kernel_s_per_run": per_run, "spmm": spmm,
-        "e2e": {"value": statistics.median(e2e_times), "unit": "s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches_per_run * args.steps, "clocks": clk,
+        "passes": chosen["passes"], "status": chosen["status"], "pve_surrogate": chosen["pve_surrogate"],
+        "trace": chosen["trace"], "roofline": _roofline(chosen, A, l, pk), "kernels_s": chosen["kernels_s"],
+        "kernel_s_per_run": chosen["kernel_s_per_run"], "spmm": chosen["spmm"], "e2e": chosen["e2e"],
+        "gpu_launches": chosen["gpu_launches"], "clocks": chosen["clocks"],
     }
+    if "plain" in res and chosen["form"] != "plain":
+        pl = res["plain"]
+        line["plain"] = {"value": pl["value"], "passes": pl["passes"], "status": pl["status"],
+                         "kernels_s": pl["kernels_s"], "spmm": pl["spmm"], "e2e": pl["e2e"]["value"],
+                         "roofline": _roofline(pl, A, l, pk)}
+        line["speedup_vs_plain"] = pl["value"] / chosen["value"]
+        line["gpu_launches"] += pl["gpu_launches"]
     if cpu is not None:
         t_pass = statistics.median(cpu["t_pass"])
         line["cpu_baseline"] = {
-            "value": t_pass * (passes + 2), "unit": "s", "cores": cpu["threads"], "kind": "oracle",
+            "value": t_pass * (chosen["passes"] + 2), "unit": "s", "cores": cpu["threads"], "kind": "oracle",
             "sample": f"one full-size power-iteration pass of the FP64 oracle ({t_pass:.2f} s, median of "
-                      f"{len(cpu['t_pass'])}), scaled by this run's passes + 2 = {passes + 2}"}
+                      f"{len(cpu['t_pass'])}), scaled by this run's passes + 2 = {chosen['passes'] + 2}"}
     if rank == 0:
         print(json.dumps(line))
-    h.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0

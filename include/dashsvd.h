@@ -175,6 +175,13 @@ int dashsvd_spmm_shift(dashsvd_handle h, const dashsvd_csr* At, const float* Y, 
                        int l, const double* alpha, const float* Q, int64_t ldq, float* Z,
                        int64_t ldz, int variant);
 
+/* Precision-form sparse products with a BF16 dense operand (row-major, ld
+ * in elements, ld % 4 == 0): Y = A X with Y in BF16 (y_bf16 = 1) or FP32, or
+ * Y = A X - alpha Q with a BF16 Q (alpha a DEVICE pointer to a double, or
+ * NULL). FP32 accumulation; shapes and variants as in dashsvd_spmm. */
+int dashsvd_spmm_bf16(dashsvd_handle h, const dashsvd_csr* A, const void* X, int64_t ldx, int l, void* Y,
+                      int y_bf16, int64_t ldy, const double* alpha, const void* Q, int64_t ldq, int variant);
+
 /* G = C^T C for a tall block C (rows x l, leading dimension ldc % 4 == 0)
  * (Alg. 3 step 1). G: l x l, leading dimension ldg >= l, FP32 partial sums
  * per row chunk added in FP64. */
@@ -214,6 +221,15 @@ int dashsvd_gram_noalloc(const float* C, int64_t rows, int l, int64_t ldc, float
  * Out: rows x ldo with ldo >= cols; columns cols .. ldo-1 are set to 0. */
 int dashsvd_project(dashsvd_handle h, const float* C, int64_t rows, int l, int64_t ldc,
                     const float* W, int64_t ldw, int cols, float* Out, int64_t ldo);
+
+/* Out = C W on the tensor cores as a split BF16x3 product (precision form of
+ * Alg. 3 step 3): C = C_hi + C_lo, W = W_hi + W_lo with BF16 parts,
+ * C W ~= C_hi W_hi + C_hi W_lo + C_lo W_hi with FP32 accumulation (relative
+ * error per term about 2^-16). Shapes as in dashsvd_project. This call waits
+ * for its own work and returns DASHSVD_ETIMEOUT if a bounded device wait ran
+ * out. */
+int dashsvd_project_bf16x3(dashsvd_handle h, const float* C, int64_t rows, int l, int64_t ldc, const float* W,
+                           int64_t ldw, int cols, float* Out, int64_t ldo);
 
 /* eigSVD of a tall block C (rows x l, ldc % 4 == 0, rows >= l) (Alg. 3):
  * U: rows x ldu (first l columns), S: l values descending, V: l x l

@@ -36,8 +36,9 @@ DASHSVD_MAX_L = 256
 EXPORTS = (
     "dashsvd_options_init", "dashsvd_create", "dashsvd_destroy", "dashsvd_run", "dashsvd_get_trace",
     "dashsvd_load_mlp", "dashsvd_status_string", "dashsvd_last_error", "dashsvd_gaussian",
-    "dashsvd_csr_transpose", "dashsvd_spmm", "dashsvd_spmm_shift", "dashsvd_gram", "dashsvd_gram_bf16x3",
-    "dashsvd_project", "dashsvd_eigsvd", "dashsvd_gram_noalloc",
+    "dashsvd_csr_transpose", "dashsvd_spmm", "dashsvd_spmm_shift", "dashsvd_spmm_bf16", "dashsvd_gram",
+    "dashsvd_gram_bf16x3",
+    "dashsvd_project", "dashsvd_project_bf16x3", "dashsvd_eigsvd", "dashsvd_gram_noalloc",
 )
 
 
@@ -84,9 +85,11 @@ def _load():
         "dashsvd_csr_transpose": (I, [P, P, P, P, P]),
         "dashsvd_spmm": (I, [P, P, P, I64, I, P, I64, I]),
         "dashsvd_spmm_shift": (I, [P, P, P, I64, I, P, P, I64, P, I64, I]),
+        "dashsvd_spmm_bf16": (I, [P, P, P, I64, I, P, I, I64, P, P, I64, I]),
         "dashsvd_gram": (I, [P, P, I64, I, I64, P, I64]),
         "dashsvd_gram_bf16x3": (I, [P, P, I64, I, I64, P, I64]),
         "dashsvd_project": (I, [P, P, I64, I, I64, P, I64, I, P, I64]),
+        "dashsvd_project_bf16x3": (I, [P, P, I64, I, I64, P, I64, I, P, I64]),
         "dashsvd_eigsvd": (I, [P, P, I64, I, I64, P, I64, P, P, I]),
         "dashsvd_gram_noalloc": (I, [P, I64, I, I64, P, I64, P]),
     }
@@ -118,9 +121,11 @@ dashsvd_gaussian = _export("dashsvd_gaussian")
 dashsvd_csr_transpose = _export("dashsvd_csr_transpose")
 dashsvd_spmm = _export("dashsvd_spmm")
 dashsvd_spmm_shift = _export("dashsvd_spmm_shift")
+dashsvd_spmm_bf16 = _export("dashsvd_spmm_bf16")
 dashsvd_gram = _export("dashsvd_gram")
 dashsvd_gram_bf16x3 = _export("dashsvd_gram_bf16x3")
 dashsvd_project = _export("dashsvd_project")
+dashsvd_project_bf16x3 = _export("dashsvd_project_bf16x3")
 dashsvd_eigsvd = _export("dashsvd_eigsvd")
 dashsvd_gram_noalloc = _export("dashsvd_gram_noalloc")
 
@@ -278,6 +283,17 @@ class Handle:
                                  out.data_ptr(), out.stride(0), variant), "dashsvd_spmm_shift")
         return out
 
+    def spmm_bf16(self, A: CsrDevice, X, l: int, out, alpha_dev=None, Q=None, variant: int = -1):
+        """BF16 X (and Q); out is BF16 or FP32 (torch tensors)."""
+        import torch
+
+        check(dashsvd_spmm_bf16(self.h, C.byref(A.struct()), X.data_ptr(), X.stride(0), l, out.data_ptr(),
+                                1 if out.dtype == torch.bfloat16 else 0, out.stride(0),
+                                alpha_dev.data_ptr() if alpha_dev is not None else None,
+                                Q.data_ptr() if Q is not None else None, Q.stride(0) if Q is not None else 0,
+                                variant), "dashsvd_spmm_bf16")
+        return out
+
     def gram(self, Cm, l: int, out=None):
         import torch
 
@@ -301,6 +317,15 @@ class Handle:
         out = torch.empty((Cm.shape[0], ldo), dtype=torch.float32, device=Cm.device) if out is None else out
         check(dashsvd_project(self.h, Cm.data_ptr(), Cm.shape[0], l, Cm.stride(0), W.data_ptr(), W.stride(0),
                               cols, out.data_ptr(), out.stride(0)), "dashsvd_project")
+        return out
+
+    def project_bf16x3(self, Cm, l: int, W, cols: int, out=None, ldo: int | None = None):
+        import torch
+
+        ldo = cols if ldo is None else ldo
+        out = torch.empty((Cm.shape[0], ldo), dtype=torch.float32, device=Cm.device) if out is None else out
+        check(dashsvd_project_bf16x3(self.h, Cm.data_ptr(), Cm.shape[0], l, Cm.stride(0), W.data_ptr(), W.stride(0),
+                                     cols, out.data_ptr(), out.stride(0)), "dashsvd_project_bf16x3")
         return out
 
     def eigsvd(self, Cm, l: int, form: int = DASHSVD_FORM_PLAIN):

@@ -65,7 +65,7 @@ struct GraphKey {
   double tol;
   float *U, *S, *V;
   uint64_t seed;
-  int alpha_prev_mode, shift, record_trace, var_fwd, var_bwd;
+  int alpha_prev_mode, shift, record_trace, var_fwd, var_bwd, form;
   bool operator==(const GraphKey& o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
 };
 
@@ -86,6 +86,7 @@ struct dashsvd_handle_s {
   DevBuf Y, Z, Q, G, W, W2, partial, carry, carry_row, ctl, trace, eigw;
   DevBuf seg_fwd, seg_bwd;  // merge-path partitions of A and A^T (rows, nonzeros)
   DevBuf errw;              // device error word of the bounded-wait kernels
+  DevBuf Qb, G64;           // precision form: BF16 basis, FP64 Gram
   // cached graph
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -99,8 +100,7 @@ struct dashsvd_handle_s {
   struct Tune {
     const void *rowptr, *colidx;
     int64_t m, n, nnz;
-    int l, form, var_fwd, var_bwd;
-    float t_fwd, t_bwd;
+    int l, form, var_fwd32, var_bwd32, var_fwd, var_bwd;
   };
   std::vector<Tune> tuned;
 };
@@ -133,7 +133,8 @@ struct RunPlan {
   int k, l, ld, pmax;
   double tol;
   float *Uw, *Vw, *S;  // outputs on the working side
-  int var_fwd, var_bwd;
+  int var_fwd, var_bwd;      // SpMM variants of the pass (BF16 operands in the precision form)
+  int var_fwd32, var_bwd32;  // FP32 variants (prologue, final, plain form)
   SpmmPart part_fwd, part_bwd;
   SpmmScratch scr;
 };
@@ -159,11 +160,42 @@ EigArgs eig_args(dashsvd_handle h, const RunPlan& p, int mode, unsigned long lon
   return a;
 }
 
+bool precision(dashsvd_handle h) { return h->opt.form == DASHSVD_FORM_PRECISION; }
+
+// Refinement iterations of the precision form's FP64 eigensolve, and the
+// rounding level of its BF16x3 Gram used by the null-column test (R6).
+constexpr int kRefineIters = 2;
+constexpr double kEpsBf16x3 = 1.52587890625e-05;  // 2^-16
+
+// eigSVD of C (rows x l): Gram, eigensolve with the control tail (the
+// projection C W follows separately)
 cudaError_t eigsvd_step(dashsvd_handle h, const RunPlan& p, const float* C, int64_t rows, int mode,
                         unsigned long long cond, cudaStream_t st) {
-  cudaError_t e = launch_gram(C, rows, p.l, p.ld, as<float>(h->G), p.ld, as<float>(h->partial), h->num_sms, st);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
+  if (precision(h)) {
+    if ((e = launch_gram_tc(C, rows, p.l, p.ld, as<double>(h->G64), p.ld, as<float>(h->G), p.ld,
+                            as<float>(h->partial), as<int>(h->errw), h->num_sms, st)) != cudaSuccess)
+      return e;
+    return launch_eig_refined(as<float>(h->G), p.ld, as<double>(h->G64), p.ld, kEpsBf16x3, kRefineIters,
+                              eig_args(h, p, mode, cond), eig_work_view(h->eigw.p), st);
+  }
+  if ((e = launch_gram(C, rows, p.l, p.ld, as<float>(h->G), p.ld, as<float>(h->partial), h->num_sms, st)) !=
+      cudaSuccess)
+    return e;
   return launch_eig_f32(as<float>(h->G), p.ld, eig_args(h, p, mode, cond), eig_work_view(h->eigw.p), st);
+}
+
+// Q <- Z W (the new basis): FP32 in the plain form; in the precision form BF16
+// for the next gathers plus FP32 once the loop is about to end (the final
+// B = A Q uses the FP32 copy)
+cudaError_t project_basis(dashsvd_handle h, const RunPlan& p, cudaStream_t st) {
+  if (precision(h)) {
+    const Control* ctl = as<Control>(h->ctl);
+    return launch_project_tc(as<float>(h->Z), p.nw, p.l, p.ld, as<float>(h->W), p.ld, p.l, as<float>(h->Q), p.ld,
+                             h->Qb.p, p.ld, &ctl->cont, as<int>(h->errw), h->num_sms, st);
+  }
+  return launch_project(as<float>(h->Z), p.nw, p.l, p.ld, as<float>(h->W), p.ld, p.l, as<float>(h->Q), p.ld,
+                        h->num_sms, st);
 }
 
 cudaError_t launch_prologue(dashsvd_handle h, const RunPlan& p, unsigned long long cond, cudaStream_t st) {
@@ -171,38 +203,52 @@ cudaError_t launch_prologue(dashsvd_handle h, const RunPlan& p, unsigned long lo
   // Alg. 5 step 1: Omega (mw x l) into Y
   if ((e = launch_gaussian(h->opt.seed, p.mw, p.l, 0, as<float>(h->Y), p.ld, st)) != cudaSuccess) return e;
   // step 2: Z = A^T Omega, Q = eigSVD(Z)
-  if ((e = launch_spmm(p.AwT, p.part_bwd, as<float>(h->Y), p.ld, p.l, as<float>(h->Z), p.ld, nullptr, nullptr, 0, p.var_bwd, p.scr,
-                       h->num_sms, st)) != cudaSuccess)
+  if ((e = launch_spmm(p.AwT, p.part_bwd, as<float>(h->Y), p.ld, p.l, as<float>(h->Z), p.ld, nullptr, nullptr, 0,
+                       p.var_bwd32, p.scr, h->num_sms, st)) != cudaSuccess)
     return e;
   if ((e = eigsvd_step(h, p, as<float>(h->Z), p.nw, kModeInit, cond, st)) != cudaSuccess) return e;
-  return launch_project(as<float>(h->Z), p.nw, p.l, p.ld, as<float>(h->W), p.ld, p.l, as<float>(h->Q), p.ld,
-                        h->num_sms, st);
+  return project_basis(h, p, st);
 }
 
 cudaError_t launch_pass(dashsvd_handle h, const RunPlan& p, unsigned long long cond, cudaStream_t st) {
   cudaError_t e;
   const Control* ctl = as<Control>(h->ctl);
   // step 4: Y = A Q; Z = A^T Y - alpha Q; [Q, Shat] = eigSVD(Z)
-  if ((e = launch_spmm(p.Aw, p.part_fwd, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld, nullptr, nullptr, 0, p.var_fwd, p.scr,
-                       h->num_sms, st)) != cudaSuccess)
-    return e;
-  if ((e = launch_spmm(p.AwT, p.part_bwd, as<float>(h->Y), p.ld, p.l, as<float>(h->Z), p.ld, &ctl->alpha, as<float>(h->Q), p.ld,
-                       p.var_bwd, p.scr, h->num_sms, st)) != cudaSuccess)
-    return e;
-  // steps 5-7 run inside the eig kernel's control tail
+  if (precision(h)) {
+    if ((e = launch_spmm_bf16(p.Aw, p.part_fwd, h->Qb.p, p.ld, p.l, h->Y.p, true, p.ld, nullptr, nullptr, 0,
+                              p.var_fwd, p.scr, h->num_sms, st)) != cudaSuccess)
+      return e;
+    if ((e = launch_spmm_bf16(p.AwT, p.part_bwd, h->Y.p, p.ld, p.l, h->Z.p, false, p.ld, &ctl->alpha, h->Qb.p, p.ld,
+                              p.var_bwd, p.scr, h->num_sms, st)) != cudaSuccess)
+      return e;
+  } else {
+    if ((e = launch_spmm(p.Aw, p.part_fwd, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld, nullptr, nullptr, 0,
+                         p.var_fwd, p.scr, h->num_sms, st)) != cudaSuccess)
+      return e;
+    if ((e = launch_spmm(p.AwT, p.part_bwd, as<float>(h->Y), p.ld, p.l, as<float>(h->Z), p.ld, &ctl->alpha,
+                         as<float>(h->Q), p.ld, p.var_bwd, p.scr, h->num_sms, st)) != cudaSuccess)
+      return e;
+  }
+  // steps 5-7 run inside the eig kernels' control tail
   if ((e = eigsvd_step(h, p, as<float>(h->Z), p.nw, kModePass, cond, st)) != cudaSuccess) return e;
-  return launch_project(as<float>(h->Z), p.nw, p.l, p.ld, as<float>(h->W), p.ld, p.l, as<float>(h->Q), p.ld,
-                        h->num_sms, st);
+  return project_basis(h, p, st);
 }
 
 cudaError_t launch_final(dashsvd_handle h, const RunPlan& p, cudaStream_t st) {
   cudaError_t e;
-  // step 9: B = A Q (into Y)
-  if ((e = launch_spmm(p.Aw, p.part_fwd, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld, nullptr, nullptr, 0, p.var_fwd, p.scr,
-                       h->num_sms, st)) != cudaSuccess)
+  // step 9: B = A Q (into Y), from the FP32 basis in both forms
+  if ((e = launch_spmm(p.Aw, p.part_fwd, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld, nullptr, nullptr, 0,
+                       p.var_fwd32, p.scr, h->num_sms, st)) != cudaSuccess)
     return e;
   // steps 10-11: eigSVD(B); U = B V_k S_k^-1; V = Q V_k
   if ((e = eigsvd_step(h, p, as<float>(h->Y), p.mw, kModeFinal, 0, st)) != cudaSuccess) return e;
+  if (precision(h)) {
+    if ((e = launch_project_tc(as<float>(h->Y), p.mw, p.l, p.ld, as<float>(h->W), p.ld, p.k, p.Uw, p.k, nullptr, 0,
+                               nullptr, as<int>(h->errw), h->num_sms, st)) != cudaSuccess)
+      return e;
+    return launch_project_tc(as<float>(h->Q), p.nw, p.l, p.ld, as<float>(h->W2), p.ld, p.k, p.Vw, p.k, nullptr, 0,
+                             nullptr, as<int>(h->errw), h->num_sms, st);
+  }
   if ((e = launch_project(as<float>(h->Y), p.mw, p.l, p.ld, as<float>(h->W), p.ld, p.k, p.Uw, p.k, h->num_sms, st)) !=
       cudaSuccess)
     return e;
@@ -265,11 +311,14 @@ int build_graph(dashsvd_handle h, const RunPlan& p) {
 constexpr int kSpmmVariants = 6;  // split (warp per row, merge path) x 3 configurations
 
 // Time every SpMM variant once on this matrix (after one warm-up launch each)
-// for both products of a pass, and keep the fastest.
+// for both products of a pass, with FP32 operands and, in the precision form,
+// with BF16 operands too, and keep the fastest of each.
 int autotune_spmm(dashsvd_handle h, RunPlan& p, const dashsvd_csr& A) {
   for (const auto& t : h->tuned)
     if (t.rowptr == A.rowptr && t.colidx == A.colidx && t.m == A.m && t.n == A.n && t.nnz == A.nnz && t.l == p.l &&
         t.form == h->opt.form) {
+      p.var_fwd32 = t.var_fwd32;
+      p.var_bwd32 = t.var_bwd32;
       p.var_fwd = t.var_fwd;
       p.var_bwd = t.var_bwd;
       return DASHSVD_OK;
@@ -277,23 +326,37 @@ int autotune_spmm(dashsvd_handle h, RunPlan& p, const dashsvd_csr& A) {
   cudaStream_t st = h->stream;
   DS_CUDA(cudaMemsetAsync(h->Q.p, 0, h->Q.bytes, st));
   DS_CUDA(cudaMemsetAsync(h->Y.p, 0, h->Y.bytes, st));
+  if (h->Qb.p) DS_CUDA(cudaMemsetAsync(h->Qb.p, 0, h->Qb.bytes, st));
   cudaEvent_t e0, e1;
   DS_CUDA(cudaEventCreate(&e0));
   DS_CUDA(cudaEventCreate(&e1));
   const Control* ctl = as<Control>(h->ctl);
-  float best[2] = {3.4e38f, 3.4e38f};
-  int arg[2] = {1, 1};
+  const int nprod = precision(h) ? 4 : 2;
+  float best[4] = {3.4e38f, 3.4e38f, 3.4e38f, 3.4e38f};
+  int arg[4] = {1, 1, 1, 1};
   cudaError_t err = cudaSuccess;
-  for (int prod = 0; prod < 2 && err == cudaSuccess; ++prod) {
+  for (int prod = 0; prod < nprod && err == cudaSuccess; ++prod) {
     for (int v = 0; v < kSpmmVariants && err == cudaSuccess; ++v) {
       float ms = 0.f;
       for (int rep = 0; rep < 2 && err == cudaSuccess; ++rep) {
         if (rep == 1) err = cudaEventRecord(e0, st);
-        if (err == cudaSuccess) {
-          err = prod == 0 ? launch_spmm(p.Aw, p.part_fwd, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld, nullptr,
-                                        nullptr, 0, v, p.scr, h->num_sms, st)
-                          : launch_spmm(p.AwT, p.part_bwd, as<float>(h->Y), p.ld, p.l, as<float>(h->Z), p.ld,
-                                        &ctl->alpha, as<float>(h->Q), p.ld, v, p.scr, h->num_sms, st);
+        if (err != cudaSuccess) break;
+        switch (prod) {
+          case 0:  // FP32 A Q
+            err = launch_spmm(p.Aw, p.part_fwd, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld, nullptr, nullptr,
+                              0, v, p.scr, h->num_sms, st);
+            break;
+          case 1:  // FP32 A^T Y - alpha Q
+            err = launch_spmm(p.AwT, p.part_bwd, as<float>(h->Y), p.ld, p.l, as<float>(h->Z), p.ld, &ctl->alpha,
+                              as<float>(h->Q), p.ld, v, p.scr, h->num_sms, st);
+            break;
+          case 2:  // BF16 A Q -> BF16
+            err = launch_spmm_bf16(p.Aw, p.part_fwd, h->Qb.p, p.ld, p.l, h->Y.p, true, p.ld, nullptr, nullptr, 0, v,
+                                   p.scr, h->num_sms, st);
+            break;
+          default:  // BF16 A^T Y - alpha Q -> FP32
+            err = launch_spmm_bf16(p.AwT, p.part_bwd, h->Y.p, p.ld, p.l, h->Z.p, false, p.ld, &ctl->alpha, h->Qb.p,
+                                   p.ld, v, p.scr, h->num_sms, st);
         }
         if (rep == 1 && err == cudaSuccess) err = cudaEventRecord(e1, st);
       }
@@ -308,9 +371,12 @@ int autotune_spmm(dashsvd_handle h, RunPlan& p, const dashsvd_csr& A) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   DS_CUDA(err);
-  p.var_fwd = arg[0];
-  p.var_bwd = arg[1];
-  h->tuned.push_back({A.rowptr, A.colidx, A.m, A.n, A.nnz, p.l, h->opt.form, arg[0], arg[1], best[0], best[1]});
+  p.var_fwd32 = arg[0];
+  p.var_bwd32 = arg[1];
+  p.var_fwd = precision(h) ? arg[2] : arg[0];
+  p.var_bwd = precision(h) ? arg[3] : arg[1];
+  h->tuned.push_back({A.rowptr, A.colidx, A.m, A.n, A.nnz, p.l, h->opt.form, p.var_fwd32, p.var_bwd32, p.var_fwd,
+                      p.var_bwd});
   return DASHSVD_OK;
 }
 
@@ -377,6 +443,7 @@ int dashsvd_create(dashsvd_handle* out, const dashsvd_options* opt, void* cuda_s
   if (e == cudaSuccess) e = prepare_project();
   if (e == cudaSuccess) e = prepare_eig();
   if (e == cudaSuccess) e = prepare_gram_tc();
+  if (e == cudaSuccess) e = prepare_project_tc();
   if (e != cudaSuccess) {
     set_last_error("dashsvd_create", e, __FILE__, __LINE__);
     if (h->side) cudaStreamDestroy(h->side);
@@ -394,7 +461,7 @@ int dashsvd_destroy(dashsvd_handle h) {
   drop_graph(h);
   DevBuf* bufs[] = {&h->rowptr_b, &h->col_b, &h->val_b, &h->cursor, &h->scan_tmp, &h->Y,       &h->Z,
                     &h->Q,        &h->G,     &h->W,     &h->W2,     &h->partial,  &h->carry, &h->carry_row,
-                    &h->ctl,      &h->trace, &h->eigw,   &h->seg_fwd, &h->seg_bwd, &h->errw};
+                    &h->ctl,      &h->trace, &h->eigw,   &h->seg_fwd, &h->seg_bwd, &h->errw, &h->Qb, &h->G64};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (h->side) cudaStreamDestroy(h->side);
@@ -429,7 +496,8 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
   const int64_t l = (int64_t)k + s;
   const int64_t mn = A->m < A->n ? A->m : A->n;
   if (l > mn || l > DASHSVD_MAX_L) return DASHSVD_EINVAL;
-  if (h->opt.form != DASHSVD_FORM_PLAIN || h->opt.learned) return DASHSVD_ENOTIMPL;
+  if ((h->opt.form != DASHSVD_FORM_PLAIN && h->opt.form != DASHSVD_FORM_PRECISION) || h->opt.learned)
+    return DASHSVD_ENOTIMPL;
 
   RunPlan p;
   const bool tr = A->m < A->n;
@@ -480,7 +548,13 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
       (rc = ensure(h->seg_bwd, sizeof(int32_t) * (size_t)(2 * (p.part_bwd.segments + 1)), &moved)) ||
       (rc = ensure(h->ctl, sizeof(Control), &moved)) ||
       (rc = ensure(h->trace, sizeof(double) * (size_t)((max_passes + 1) * (5 + l)), &moved)) ||
-      (rc = ensure(h->eigw, eig_work_bytes(), &moved)))
+      (rc = ensure(h->eigw, eig_work_bytes(), &moved)) || (rc = ensure(h->errw, 16, &moved)) ||
+      (rc = ensure(h->G64, sizeof(double) * (size_t)(p.ld * p.ld), &moved)) ||
+      (precision(h) && (rc = ensure(h->Qb, 2 * (size_t)(p.nw * p.ld), &moved))) ||
+      (precision(h) &&
+       (rc = ensure(h->partial, sizeof(float) * std::max(gram_tc_partial_floats(p.mw, p.l, h->num_sms),
+                                                         gram_tc_partial_floats(p.nw, p.l, h->num_sms)),
+                    &moved))))
     return rc;
   p.scr.carry = as<float>(h->carry);
   p.scr.carry_row = as<int32_t>(h->carry_row);
@@ -491,8 +565,8 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
   p.part_bwd.seg_row = as<int32_t>(h->seg_bwd);
   p.part_bwd.seg_nnz = p.part_bwd.seg_row + p.part_bwd.segments + 1;
   const int forced = h->opt.spmm_variant;
-  p.var_fwd = forced >= 0 ? forced : 1;
-  p.var_bwd = forced >= 0 ? forced : 1;
+  p.var_fwd = p.var_fwd32 = forced >= 0 ? forced : 1;
+  p.var_bwd = p.var_bwd32 = forced >= 0 ? forced : 1;
 
   cudaStream_t st = h->stream;
   DS_CUDA(launch_csr_transpose(*A, as<int32_t>(h->rowptr_b), as<int32_t>(h->col_b), as<float>(h->val_b),
@@ -500,6 +574,7 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
   DS_CUDA(launch_spmm_partition(p.Aw, p.part_fwd, st));
   DS_CUDA(launch_spmm_partition(p.AwT, p.part_bwd, st));
   if (forced < 0 && (rc = autotune_spmm(h, p, *A)) != DASHSVD_OK) return rc;
+  DS_CUDA(cudaMemsetAsync(h->errw.p, 0, sizeof(int), st));
 
   if (h->opt.use_graph) {
     GraphKey key;
@@ -516,8 +591,9 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
     key.alpha_prev_mode = h->opt.alpha_prev_mode;
     key.shift = h->opt.shift;
     key.record_trace = h->opt.record_trace;
-    key.var_fwd = p.var_fwd;
-    key.var_bwd = p.var_bwd;
+    key.var_fwd = p.var_fwd | (p.var_fwd32 << 8);
+    key.var_bwd = p.var_bwd | (p.var_bwd32 << 8);
+    key.form = h->opt.form;
     if (moved || !h->have_graph || !(key == h->key)) {
       if ((rc = build_graph(h, p)) != DASHSVD_OK) return rc;
       h->key = key;
@@ -535,11 +611,13 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
     DS_CUDA(launch_final(h, p, st));
   }
   Control hc;
+  int werr = 0;
   DS_CUDA(cudaMemcpyAsync(&hc, h->ctl.p, sizeof(Control), cudaMemcpyDeviceToHost, st));
+  DS_CUDA(cudaMemcpyAsync(&werr, h->errw.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   DS_CUDA(cudaStreamSynchronize(st));
   h->last_l = p.l;
   h->last_records = h->opt.record_trace ? hc.pass : 0;
-  const int status = status_from_control(hc);
+  const int status = werr ? DASHSVD_ETIMEOUT : status_from_control(hc);
   if (info) {
     info->passes = hc.pass;
     info->status = status;
@@ -550,7 +628,7 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
     int64_t ws = 0;
     DevBuf* bufs[] = {&h->rowptr_b, &h->col_b, &h->val_b, &h->cursor, &h->scan_tmp, &h->Y,       &h->Z,
                       &h->Q,        &h->G,     &h->W,     &h->W2,     &h->partial,  &h->carry, &h->carry_row,
-                      &h->ctl,      &h->trace, &h->eigw,   &h->seg_fwd, &h->seg_bwd};
+                      &h->ctl,      &h->trace, &h->eigw,   &h->seg_fwd, &h->seg_bwd, &h->errw, &h->Qb, &h->G64};
     for (DevBuf* b : bufs) ws += (int64_t)b->bytes;
     info->workspace_bytes = ws;
     info->eig_sweeps = hc.sweeps;
@@ -619,6 +697,36 @@ int dashsvd_spmm_shift(dashsvd_handle h, const dashsvd_csr* At, const float* Y, 
   return spmm_common(h, At, Y, ldy, l, Z, ldz, alpha, Q, ldq, variant);
 }
 
+int dashsvd_spmm_bf16(dashsvd_handle h, const dashsvd_csr* A, const void* X, int64_t ldx, int l, void* Y, int y_bf16,
+                      int64_t ldy, const double* alpha, const void* Q, int64_t ldq, int variant) {
+  if (!h || !csr_ok(A) || !X || !Y || l < 1 || l > DASHSVD_MAX_L) return DASHSVD_EINVAL;
+  if (ldx < l || ldy < l || ldx % 4 || ldy % 4 || ((uintptr_t)X & 7u) || ((uintptr_t)Y & (y_bf16 ? 7u : 15u)))
+    return DASHSVD_EINVAL;
+  if (alpha && (!Q || ldq < l || ldq % 4 || ((uintptr_t)Q & 7u))) return DASHSVD_EINVAL;
+  if (variant < -1 || variant >= kSpmmVariants) return DASHSVD_EINVAL;
+  SpmmPart part;
+  part.segments = spmm_segments(*A, h->num_sms);
+  const int64_t ldc = ((l + 3) / 4) * 4;
+  int rc;
+  bool moved = false;
+  if ((rc = ensure(h->carry, sizeof(float) * (size_t)(2 * part.segments * ldc), &moved)) ||
+      (rc = ensure(h->carry_row, sizeof(int32_t) * (size_t)(2 * part.segments), &moved)) ||
+      (rc = ensure(h->seg_fwd, sizeof(int32_t) * (size_t)(2 * (part.segments + 1)), &moved)))
+    return rc;
+  if (moved) h->have_graph = false;
+  SpmmScratch scr;
+  scr.carry = as<float>(h->carry);
+  scr.carry_row = as<int32_t>(h->carry_row);
+  scr.max_segments = part.segments;
+  scr.ldc = (int)ldc;
+  part.seg_row = as<int32_t>(h->seg_fwd);
+  part.seg_nnz = part.seg_row + part.segments + 1;
+  const int var = variant < 0 ? 1 : variant;
+  if (var & 1) DS_CUDA(launch_spmm_partition(*A, part, h->stream));
+  DS_CUDA(launch_spmm_bf16(*A, part, X, ldx, l, Y, y_bf16 != 0, ldy, alpha, Q, ldq, var, scr, h->num_sms, h->stream));
+  return DASHSVD_OK;
+}
+
 int dashsvd_gram(dashsvd_handle h, const float* C, int64_t rows, int l, int64_t ldc, float* G, int64_t ldg) {
   if (!h || !C || !G || rows < 0 || l < 1 || l > DASHSVD_MAX_L || ldc < l || ldc % 4 || ldg < l || !aligned16(C))
     return DASHSVD_EINVAL;
@@ -648,6 +756,25 @@ int dashsvd_gram_bf16x3(dashsvd_handle h, const float* C, int64_t rows, int l, i
   return err ? DASHSVD_ETIMEOUT : DASHSVD_OK;
 }
 
+int dashsvd_project_bf16x3(dashsvd_handle h, const float* C, int64_t rows, int l, int64_t ldc, const float* W,
+                           int64_t ldw, int cols, float* Out, int64_t ldo) {
+  if (!h || !C || !W || !Out || rows < 0 || l < 1 || l > DASHSVD_MAX_L || cols < 1 || cols > DASHSVD_MAX_L)
+    return DASHSVD_EINVAL;
+  if (ldc < l || ldc % 4 || ldw < cols || ldo < cols || ldo > ((cols + 15) / 16) * 16 || !aligned16(C))
+    return DASHSVD_EINVAL;
+  int rc;
+  bool moved = false;
+  if ((rc = ensure(h->errw, 16, &moved))) return rc;
+  if (moved) h->have_graph = false;
+  DS_CUDA(cudaMemsetAsync(h->errw.p, 0, sizeof(int), h->stream));
+  DS_CUDA(launch_project_tc(C, rows, l, ldc, W, ldw, cols, Out, ldo, nullptr, 0, nullptr, as<int>(h->errw),
+                            h->num_sms, h->stream));
+  int err = 0;
+  DS_CUDA(cudaMemcpyAsync(&err, h->errw.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  DS_CUDA(cudaStreamSynchronize(h->stream));
+  return err ? DASHSVD_ETIMEOUT : DASHSVD_OK;
+}
+
 int dashsvd_project(dashsvd_handle h, const float* C, int64_t rows, int l, int64_t ldc, const float* W, int64_t ldw,
                     int cols, float* Out, int64_t ldo) {
   if (!h || !C || !W || !Out || rows < 0 || l < 1 || l > DASHSVD_MAX_L || cols < 1 || cols > DASHSVD_MAX_L)
@@ -662,19 +789,29 @@ int dashsvd_eigsvd(dashsvd_handle h, const float* C, int64_t rows, int l, int64_
   if (!h || !C || !U || !S || !V || l < 1 || rows < l || ldc < l || ldc % 4 || ldu < l || ldu > DASHSVD_MAX_L ||
       !aligned16(C))
     return DASHSVD_EINVAL;
-  if (form != DASHSVD_FORM_PLAIN) return DASHSVD_ENOTIMPL;
+  if (form != DASHSVD_FORM_PLAIN && form != DASHSVD_FORM_PRECISION) return DASHSVD_EINVAL;
   if (l > eig_max_l_f32()) return DASHSVD_EINVAL;
   const int64_t ld = round_up(l, 8);
   int rc;
   bool moved = false;
   if ((rc = ensure(h->G, sizeof(float) * (size_t)(ld * ld), &moved)) ||
       (rc = ensure(h->W, sizeof(float) * (size_t)(ld * ld), &moved)) ||
-      (rc = ensure(h->eigw, eig_work_bytes(), &moved)) ||
-      (rc = ensure(h->partial, sizeof(float) * gram_partial_floats(rows, l, h->num_sms), &moved)))
+      (rc = ensure(h->eigw, eig_work_bytes(), &moved)) || (rc = ensure(h->errw, 16, &moved)) ||
+      (rc = ensure(h->G64, sizeof(double) * (size_t)(ld * ld), &moved)) ||
+      (rc = ensure(h->partial, sizeof(float) * std::max(gram_partial_floats(rows, l, h->num_sms),
+                                                        gram_tc_partial_floats(rows, l, h->num_sms)),
+                   &moved)))
     return rc;
   if (moved) h->have_graph = false;
   cudaStream_t st = h->stream;
-  DS_CUDA(launch_gram(C, rows, l, ldc, as<float>(h->G), ld, as<float>(h->partial), h->num_sms, st));
+  const bool prec = form == DASHSVD_FORM_PRECISION;
+  if (prec) {
+    DS_CUDA(cudaMemsetAsync(h->errw.p, 0, sizeof(int), st));
+    DS_CUDA(launch_gram_tc(C, rows, l, ldc, as<double>(h->G64), ld, as<float>(h->G), ld, as<float>(h->partial),
+                           as<int>(h->errw), h->num_sms, st));
+  } else {
+    DS_CUDA(launch_gram(C, rows, l, ldc, as<float>(h->G), ld, as<float>(h->partial), h->num_sms, st));
+  }
   EigArgs a;
   std::memset(&a, 0, sizeof(a));
   a.l = l;
@@ -684,6 +821,16 @@ int dashsvd_eigsvd(dashsvd_handle h, const float* C, int64_t rows, int l, int64_
   a.W = as<float>(h->W);
   a.W2 = V;
   a.S_out = S;
+  if (prec) {
+    DS_CUDA(launch_eig_refined(as<float>(h->G), ld, as<double>(h->G64), ld, kEpsBf16x3, kRefineIters, a,
+                               eig_work_view(h->eigw.p), st));
+    DS_CUDA(launch_project_tc(C, rows, l, ldc, as<float>(h->W), ld, l, U, ldu, nullptr, 0, nullptr, as<int>(h->errw),
+                              h->num_sms, st));
+    int err = 0;
+    DS_CUDA(cudaMemcpyAsync(&err, h->errw.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DS_CUDA(cudaStreamSynchronize(st));
+    return err ? DASHSVD_ETIMEOUT : DASHSVD_OK;
+  }
   DS_CUDA(launch_eig_f32(as<float>(h->G), ld, a, eig_work_view(h->eigw.p), st));
   DS_CUDA(launch_project(C, rows, l, ldc, as<float>(h->W), ld, l, U, ldu, h->num_sms, st));
   return DASHSVD_OK;

@@ -102,19 +102,36 @@ cudaError_t prepare_gram_tc();
 cudaError_t launch_gram_tc(const float* C, int64_t rows, int l, int64_t ldc, double* G64, int64_t ldg64, float* G32,
                            int64_t ldg32, float* partial, int* err, int num_sms, cudaStream_t st);
 
+// Projection on tcgen05 (BF16x3): Out = C W into FP32 (outF, skipped while
+// *f32_only_when_zero != 0 when that pointer is given) and/or BF16 (outB).
+cudaError_t prepare_project_tc();
+cudaError_t launch_project_tc(const float* C, int64_t rows, int l, int64_t ldc, const float* W, int64_t ldw, int cols,
+                              float* outF, int64_t ldf, void* outB, int64_t ldb, const int* f32_only_when_zero,
+                              int* err, int num_sms, cudaStream_t st);
+
 // Jacobi eigensolver (rotation log) + eigenvector replay with the eigSVD
 // conventions and the loop control. Work buffer: header, eigenvalues, log.
 constexpr int kMaxSweeps = 30;
 struct EigWork {
-  int* hdr;     // [0] sweeps to replay, [1] status bits, [2] sweeps run
-  float* d;     // kMaxL eigenvalues (unsorted)
-  float* d0;    // kMaxL diagonal entries of G before the iteration
-  float2* log;  // (c, s) per sweep x step x pair
+  int* hdr;       // [0] sweeps to replay, [1] status bits, [2] sweeps run
+  float* d;       // kMaxL eigenvalues (unsorted, FP32 Jacobi)
+  float* d0;      // kMaxL diagonal entries of G before the iteration
+  float* V32;     // l x l eigenvectors (column c = eigenvector c), row-major
+  double* X64;    // 6 l x l FP64 matrices for the refinement
+  double* lam64;  // kMaxL refined eigenvalues
+  double* d0_64;  // kMaxL diagonal of the FP64 Gram
+  float2* log;    // (c, s) per sweep x step x pair
 };
 int eig_max_l_f32();
 size_t eig_work_bytes();
 EigWork eig_work_view(void* base);
 cudaError_t launch_eig_f32(const float* G, int64_t ldg, const EigArgs& a, const EigWork& wk, cudaStream_t st);
+cudaError_t launch_eig_refined(const float* G32, int64_t ldg32, const double* G64, int64_t ldg64, double eps_null,
+                               int iters, const EigArgs& a, const EigWork& wk, cudaStream_t st);
+// FP64 iterative refinement of an approximate eigenbasis V32 of G64 (Ogita and
+// Aishima); *X receives the refined basis (inside wk), wk.lam64 the eigenvalues.
+cudaError_t launch_refine_fp64(const double* G64, int64_t ldg, const float* V32, int l, int iters, const EigWork& wk,
+                               const double** X, cudaStream_t st);
 
 // Out = C W.
 cudaError_t launch_project(const float* C, int64_t rows, int l, int64_t ldc, const float* W,

@@ -178,47 +178,23 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_f32_kernel(const float* __
 constexpr int kVecWarps = 8;
 constexpr int kBatch = 16;  // log steps staged per batch
 
-struct FinishSmem {
-  int rank[kMaxL];
-  double S[kMaxL];  // by sorted position
+struct ReplaySmem {
   float x[kVecWarps][kMaxN];
   float2 logb[2][kBatch * (kMaxN / 2)];
-  double red[32];
-  int flag;
 };
 
-__global__ void __launch_bounds__(kVecWarps * 32) eigvec_finish_kernel(EigWork wk, EigArgs a) {
-  __shared__ FinishSmem fs;
-  const int l = a.l;
+// Column c of V = J_1 (J_2 (... (J_T e_c))): each warp replays the log
+// backwards on e_c, in batches of kBatch steps staged in shared memory by the
+// whole CTA. Writes V row-major (V[j * l + c]).
+__global__ void __launch_bounds__(kVecWarps * 32) eigvec_replay_kernel(EigWork wk, int l) {
+  __shared__ ReplaySmem rs;
   const int N = l + (l & 1);
   const int P = N / 2;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5;
-  const float* d = wk.d;
-
-  // ranks: descending, ties by lower index; non-finite check
-  if (tid == 0) fs.flag = 0;
-  __syncthreads();
-  for (int i = tid; i < l; i += nt) {
-    const float di = d[i];
-    if (!isfinite(di)) fs.flag = 1;
-    int r = 0;
-    for (int j = 0; j < l; ++j) {
-      const float dj = d[j];
-      r += (dj > di) || (dj == di && j < i);
-    }
-    fs.rank[i] = r < l ? r : l - 1;
-  }
-  __syncthreads();
-  const bool nonfinite = fs.flag != 0;
-  for (int i = tid; i < l; i += nt) fs.S[fs.rank[i]] = sqrt(fmax((double)d[i], 0.0));
-  __syncthreads();
   const int nsteps = wk.hdr[0] * (N - 1);
-
-  // eigenvector c = J_1 (J_2 (... (J_T e_c))): replay the log backwards, in
-  // batches of kBatch steps staged in shared memory by the whole CTA
   const int c = blockIdx.x * kVecWarps + warp;
-  float* x = fs.x[warp];
+  float* x = rs.x[warp];
   for (int j = lane; j < N; j += 32) x[j] = j == c ? 1.f : 0.f;
   const int nbatch = (nsteps + kBatch - 1) / kBatch;
   // batch b covers steps [nsteps - (b+1) kBatch, nsteps - b kBatch)
@@ -226,7 +202,7 @@ __global__ void __launch_bounds__(kVecWarps * 32) eigvec_finish_kernel(EigWork w
     const int t1 = nsteps - b * kBatch;
     const int t0 = t1 - kBatch > 0 ? t1 - kBatch : 0;
     const float2* src = wk.log + (int64_t)t0 * P;
-    float2* dst = fs.logb[buf];
+    float2* dst = rs.logb[buf];
     const int n = (t1 - t0) * P;
     for (int i = tid; i < n; i += nt) dst[i] = src[i];
   };
@@ -236,7 +212,7 @@ __global__ void __launch_bounds__(kVecWarps * 32) eigvec_finish_kernel(EigWork w
     if (b + 1 < nbatch) stage(b + 1, (b + 1) & 1);  // next batch loads while this one is applied
     const int t1 = nsteps - b * kBatch;
     const int t0 = t1 - kBatch > 0 ? t1 - kBatch : 0;
-    const float2* lg = fs.logb[b & 1];
+    const float2* lg = rs.logb[b & 1];
     if (c < l) {
       for (int t = t1 - 1; t >= t0; --t) {
         const int step = t % (N - 1);
@@ -256,32 +232,81 @@ __global__ void __launch_bounds__(kVecWarps * 32) eigvec_finish_kernel(EigWork w
     }
     __syncthreads();
   }
+  if (c < l)
+    for (int j = lane; j < l; j += 32) wk.V32[(int64_t)j * l + c] = x[j];
+}
+
+// ------------------------------------------------------------- kernel 3
+
+struct FinishSmem {
+  int rank[kMaxL];
+  double S[kMaxL];  // by sorted position
+  double red[32];
+  int flag;
+};
+
+// The eigSVD conventions (Alg. 3 steps 2-4) and the dashSVD control (Alg. 5
+// steps 5-7) on eigenpairs (d, V) of precision T: d[c] and column c of the
+// row-major V (V[j * l + c]); d0 holds the diagonal of G for the null test,
+// eps_null its rounding level. One warp per eigenvector; CTA 0 also runs the
+// control.
+template <typename T>
+__global__ void __launch_bounds__(kVecWarps * 32) finish_kernel(const T* __restrict__ d, const T* __restrict__ V,
+                                                                const T* __restrict__ d0, double eps_null,
+                                                                const int* __restrict__ hdr, EigArgs a) {
+  __shared__ FinishSmem fs;
+  const int l = a.l;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5;
+
+  // ranks: descending, ties by lower index; non-finite check
+  if (tid == 0) fs.flag = 0;
+  __syncthreads();
+  for (int i = tid; i < l; i += nt) {
+    const T di = d[i];
+    if (!isfinite((double)di)) fs.flag = 1;
+    int r = 0;
+    for (int j = 0; j < l; ++j) {
+      const T dj = d[j];
+      r += (dj > di) || (dj == di && j < i);
+    }
+    fs.rank[i] = r < l ? r : l - 1;
+  }
+  __syncthreads();
+  const bool nonfinite = fs.flag != 0;
+  for (int i = tid; i < l; i += nt) fs.S[fs.rank[i]] = sqrt(fmax((double)d[i], 0.0));
+  __syncthreads();
+
+  const int c = blockIdx.x * kVecWarps + warp;
   if (c < l) {
     // sign: largest |entry| (lowest index on ties) positive
-    float best = -1.f;
+    double best = -1.0;
     int bj = 0;
     for (int j = lane; j < l; j += 32) {
-      const float av = fabsf(x[j]);
+      const double av = fabs((double)V[(int64_t)j * l + c]);
       if (av > best) { best = av; bj = j; }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
       const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
       if (ob > best || (ob == best && oj < bj)) { best = ob; bj = oj; }
     }
-    const double sg = x[bj] < 0.f ? -1.0 : 1.0;
+    const double sg = (double)V[(int64_t)bj * l + c] < 0.0 ? -1.0 : 1.0;
     const int r = fs.rank[c];
     // null when the eigenvalue is at the rounding level of the diagonal entries it is made of
     double wsum = 0.0;
-    for (int j = lane; j < l; j += 32) wsum += (double)x[j] * (double)x[j] * (double)wk.d0[j];
+    for (int j = lane; j < l; j += 32) {
+      const double v = (double)V[(int64_t)j * l + c];
+      wsum += v * v * (double)d0[j];
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
-    const bool null = nonfinite || (double)d[c] <= 16.0 * (double)kEps32 * wsum;
+    const bool null = nonfinite || (double)d[c] <= 16.0 * eps_null * wsum;
     const double inv = null ? 0.0 : 1.0 / fs.S[r];
     const bool keep = a.mode != kModeFinal || r < a.k;
     for (int j = lane; j < l; j += 32) {
-      const double v = sg * (double)x[j];
+      const double v = sg * (double)V[(int64_t)j * l + c];
       a.W[(int64_t)j * a.ldw + r] = keep ? (float)(v * inv) : 0.f;
       if (a.mode == kModeFinal) a.W2[(int64_t)j * a.ldw + r] = keep ? (float)v : 0.f;
       if (a.mode == kModeEigsvd) a.W2[(int64_t)j * l + r] = (float)v;
@@ -304,8 +329,8 @@ __global__ void __launch_bounds__(kVecWarps * 32) eigvec_finish_kernel(EigWork w
   }
   Control* ctl = a.ctl;
   if (tid == 0) {
-    ctl->sweeps = wk.hdr[2];
-    ctl->status |= wk.hdr[1];
+    ctl->sweeps = hdr[2];
+    ctl->status |= hdr[1];
   }
   if (a.mode == kModeFinal) {
     for (int r = tid; r < a.k; r += nt) a.S_out[r] = (float)fs.S[r];
@@ -323,7 +348,7 @@ __global__ void __launch_bounds__(kVecWarps * 32) eigvec_finish_kernel(EigWork w
       ctl->ratio = 0.0;
       ctl->pass = 0;
       ctl->stop = 0;
-      ctl->status = (nonfinite ? kStatusNonFinite : 0) | wk.hdr[1];
+      ctl->status = (nonfinite ? kStatusNonFinite : 0) | hdr[1];
       ctl->cont = (!nonfinite && a.pmax > 0) ? 1 : 0;
       if (a.use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond, (unsigned)ctl->cont);
     }
@@ -366,7 +391,7 @@ __global__ void __launch_bounds__(kVecWarps * 32) eigvec_finish_kernel(EigWork w
       rec[1] = alpha;
       rec[2] = ratio;
       rec[3] = stop ? alpha : alpha_next;
-      rec[4] = wk.hdr[2];
+      rec[4] = hdr[2];
     }
     fs.flag = stop;
     if (a.use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond, (unsigned)ctl->cont);
@@ -391,16 +416,30 @@ size_t jacobi_smem(int l) {
 int eig_max_l_f32() { return kMaxL; }
 
 size_t eig_work_bytes() {
-  return 16 + 2 * sizeof(float) * kMaxL + sizeof(float2) * (size_t)kMaxSweeps * (kMaxN - 1) * (kMaxN / 2) + 16;
+  const size_t L = kMaxL;
+  return 256 + 2 * sizeof(float) * L + sizeof(float) * L * L + 6 * sizeof(double) * L * L + 2 * sizeof(double) * L +
+         sizeof(float2) * (size_t)kMaxSweeps * (kMaxN - 1) * (kMaxN / 2);
 }
 
 EigWork eig_work_view(void* base) {
+  const size_t L = kMaxL;
   EigWork w;
   char* p = reinterpret_cast<char*>(base);
   w.hdr = reinterpret_cast<int*>(p);
-  w.d = reinterpret_cast<float*>(p + 16);
-  w.d0 = w.d + kMaxL;
-  w.log = reinterpret_cast<float2*>(p + 16 + 2 * sizeof(float) * kMaxL);
+  p += 256;
+  w.X64 = reinterpret_cast<double*>(p);  // 6 l x l FP64 matrices: X, X', P, S, T, E
+  p += 6 * sizeof(double) * L * L;
+  w.lam64 = reinterpret_cast<double*>(p);
+  p += sizeof(double) * L;
+  w.d0_64 = reinterpret_cast<double*>(p);
+  p += sizeof(double) * L;
+  w.d = reinterpret_cast<float*>(p);
+  p += sizeof(float) * L;
+  w.d0 = reinterpret_cast<float*>(p);
+  p += sizeof(float) * L;
+  w.V32 = reinterpret_cast<float*>(p);
+  p += sizeof(float) * L * L;
+  w.log = reinterpret_cast<float2*>(p);
   return w;
 }
 
@@ -414,7 +453,27 @@ cudaError_t launch_eig_f32(const float* G, int64_t ldg, const EigArgs& a, const 
   jacobi_f32_kernel<<<1, kJacThreads, jacobi_smem(a.l), st>>>(G, ldg, a.l, wk);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  eigvec_finish_kernel<<<(unsigned)ds_ceil_div(a.l, kVecWarps), kVecWarps * 32, 0, st>>>(wk, a);
+  const unsigned blocks = (unsigned)ds_ceil_div(a.l, kVecWarps);
+  eigvec_replay_kernel<<<blocks, kVecWarps * 32, 0, st>>>(wk, a.l);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  finish_kernel<float><<<blocks, kVecWarps * 32, 0, st>>>(wk.d, wk.V32, wk.d0, (double)kEps32, wk.hdr, a);
+  return cudaGetLastError();
+}
+
+// FP32 Jacobi on G32 for a starting basis, FP64 refinement against G64, then
+// the conventions and control on the refined FP64 eigenpairs.
+cudaError_t launch_eig_refined(const float* G32, int64_t ldg32, const double* G64, int64_t ldg64, double eps_null,
+                               int iters, const EigArgs& a, const EigWork& wk, cudaStream_t st) {
+  if (a.l < 1 || a.l > kMaxL) return cudaErrorInvalidValue;
+  jacobi_f32_kernel<<<1, kJacThreads, jacobi_smem(a.l), st>>>(G32, ldg32, a.l, wk);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const unsigned blocks = (unsigned)ds_ceil_div(a.l, kVecWarps);
+  eigvec_replay_kernel<<<blocks, kVecWarps * 32, 0, st>>>(wk, a.l);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const double* X = nullptr;
+  if ((e = launch_refine_fp64(G64, ldg64, wk.V32, a.l, iters, wk, &X, st)) != cudaSuccess) return e;
+  finish_kernel<double><<<blocks, kVecWarps * 32, 0, st>>>(wk.lam64, X, wk.d0_64, eps_null, wk.hdr, a);
   return cudaGetLastError();
 }
 

@@ -149,6 +149,38 @@ def test_spmm_shift_matches_fp64(ds, h, name, variant):
     assert np.all(Z[:, l:] == 0.0)
 
 
+@pytest.mark.parametrize("name", ["social", "mixed"])
+@pytest.mark.parametrize("variant", [0, 1, 3, 5])
+def test_spmm_bf16_matches_fp64(ds, h, name, variant):
+    """BF16 dense operands (precision form): the products are exact in FP32 and
+    accumulated in FP32; a BF16 output adds one rounding of 2^-9."""
+    import torch
+
+    A = MATRICES[name]()
+    l = 150
+    ld = ds.ld_for(l)
+    rng = np.random.default_rng(2)
+    X = torch.as_tensor(rng.standard_normal((A.n, ld)).astype(np.float32)).cuda()
+    X[:, l:] = 0
+    Xb = X.to(torch.bfloat16)
+    Ad = ds.CsrDevice.from_host(A)
+    Yb = torch.empty((A.m, ld), dtype=torch.bfloat16, device="cuda")
+    Yf = torch.empty((A.m, ld), dtype=torch.float32, device="cuda")
+    h.spmm_bf16(Ad, Xb, l, Yb, variant=variant)
+    h.spmm_bf16(Ad, Xb, l, Yf, variant=variant)
+    torch.cuda.synchronize()
+    X64 = Xb.float().cpu().numpy().astype(np.float64)[:, :l]
+    As = A.to_scipy(np.float64)
+    ref = As @ X64
+    bound = abs(As) @ np.abs(X64)
+    K = int(np.diff(A.rowptr).max()) + 2
+    yf = Yf.cpu().numpy().astype(np.float64)
+    yb = Yb.float().cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(yf[:, :l] - ref) <= K * EPS32 * bound + 1e-30)
+    assert np.all(np.abs(yb[:, :l] - ref) <= (K * EPS32 + 2.0**-8) * bound + 1e-30)
+    assert np.all(yf[:, l:] == 0) and np.all(yb[:, l:] == 0)
+
+
 def test_spmm_merge_path_matches_warp_per_row_closely(ds, h):
     """The two work splits add the same products in different groupings; both
     are within the FP32 bound of the exact result and close to each other."""
@@ -211,6 +243,43 @@ def test_project_matches_fp64(ds, h, rows, l, cols, ldo):
     bound = np.abs(Cm[:, :l]).astype(np.float64) @ np.abs(W).astype(np.float64)
     assert np.all(np.abs(Out[:, :cols] - ref) <= (l + 2) * EPS32 * bound)
     assert np.all(Out[:, cols:] == 0.0)
+
+
+@pytest.mark.parametrize("rows,l,cols,ldo", [(10, 4, 4, 4), (1000, 30, 30, 32), (12345, 150, 150, 152),
+                                             (777, 150, 100, 100), (4097, 160, 37, 40), (5000, 220, 220, 224),
+                                             (3000, 256, 200, 208), (300000, 150, 150, 152)])
+def test_project_bf16x3_matches_fp64(ds, h, rows, l, cols, ldo):
+    """Tensor-core BF16x3 projection: relative error about 2^-16 per product term
+    plus FP32 accumulation over l terms."""
+    import torch
+
+    rng = np.random.default_rng(rows + l + 1)
+    ld = ds.ld_for(l)
+    Cm = _padded(rng.standard_normal((rows, l)).astype(np.float32), ld)
+    W = rng.standard_normal((l, cols)).astype(np.float32)
+    out = torch.full((rows, ldo), float("nan"), dtype=torch.float32, device="cuda")
+    Out = _np(h.project_bf16x3(_t(Cm), l, _t(W), cols, out=out))
+    ref = Cm[:, :l].astype(np.float64) @ W.astype(np.float64)
+    bound = np.abs(Cm[:, :l]).astype(np.float64) @ np.abs(W).astype(np.float64)
+    err = np.abs(Out[:, :cols] - ref)
+    assert np.all(err <= (4e-5 + (l + 2) * EPS32) * bound), float(np.max(err / bound))
+    assert np.all(Out[:, cols:] == 0.0)
+
+
+@pytest.mark.parametrize("rows,l", [(500, 12), (4000, 30), (20000, 150), (3000, 160), (8000, 220)])
+def test_eigsvd_precision_form_matches_oracle(ds, h, rows, l):
+    """eigSVD in the precision form (BF16x3 Gram and projection, FP64-refined
+    eig): the Gram's relative error about 2^-16 bounds the accuracy; S_i moves by
+    about e / (2 S_i) for an absolute Gram error e ~ 2^-16 * S_1^2."""
+    ld = ds.ld_for(l)
+    spec = np.logspace(0, -1.5, l)
+    Cm64 = datagen.dense_with_spectrum(rows, l, spec, seed=l + 3)
+    Cm = _padded(Cm64.astype(np.float32), ld)
+    U, S, V = (_np(x) for x in h.eigsvd(_t(Cm), l, form=ds.DASHSVD_FORM_PRECISION))
+    Ur, Sr, Vr, _ = oracle.eigsvd(Cm[:, :l].astype(np.float64))
+    assert np.all(np.abs(S - Sr) <= 4e-5 * Sr[0] ** 2 / Sr + 1e-6 * Sr)
+    np.testing.assert_allclose(U[:, :l].T @ U[:, :l], np.eye(l), atol=5e-3)
+    np.testing.assert_allclose((U[:, :l] * S) @ V.T, Cm[:, :l], atol=2e-4 * np.abs(Cm[:, :l]).max())
 
 
 @pytest.mark.parametrize("rows,l", [(500, 12), (4000, 30), (20000, 150), (3000, 160), (300, 1), (8000, 220),

@@ -124,6 +124,35 @@ def test_large_l_recommender_shape(ds):
     assert rel[0] <= 1e-5
 
 
+@pytest.mark.parametrize("p", [0, 2, 4])
+def test_precision_form_fixed_passes(ds, p):
+    """Precision form (BF16 gathered operands, BF16x3 Gram and projection, FP64
+    eig/shift/PVE) at fixed p against the FP64 oracle: errors are reported per
+    sigma and bounded by the BF16x3 rounding level amplified by eigSVD."""
+    A, prm = datagen.make_config(1, scale=0.1)
+    k, s = prm["k"], prm["s"]
+    U, S, V, info, _ = _run(ds, A, k, s, p, 0.0, form=ds.DASHSVD_FORM_PRECISION)
+    ref = oracle.dashsvd(A.to_scipy(), k, s, p_max=p, tol=0.0, seed=0x5EED)
+    assert info.passes == p
+    rel = np.abs(S - ref.S) / ref.S
+    kappa2 = (ref.S[0] / ref.S) ** 2
+    assert np.all(rel <= 2e-3 + 1e-4 * kappa2), rel
+    assert np.max(metrics.principal_angles(V[:, :5], ref.V[:, :5])) < 5e-2
+
+
+def test_precision_form_pve_control(ds):
+    """Precision form with the PVE test on the 20000 x 10000 workload: stops
+    within one pass of the oracle and the true PVE error is within the tolerance
+    scale."""
+    A, prm = datagen.make_config(1)
+    k, s = prm["k"], prm["s"]
+    U, S, V, info, _ = _run(ds, A, k, s, prm["p_max"], prm["tol"], form=ds.DASHSVD_FORM_PRECISION)
+    ref = oracle.dashsvd(A.to_scipy(), k, s, p_max=prm["p_max"], tol=prm["tol"], seed=0x5EED)
+    assert abs(info.passes - ref.passes) <= 1
+    rel = np.abs(S - ref.S) / ref.S
+    assert np.max(rel) < 1e-2
+
+
 def test_modes_match_oracle(ds):
     A, prm = datagen.make_config(1, scale=0.05)
     k, s = 8, 4
