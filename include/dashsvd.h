@@ -87,7 +87,13 @@ typedef struct {
                               capped for four blocks per SM) */
   int32_t record_trace;    /* 1: keep the per-pass Shat / shift history (get_trace) */
   int32_t shift;           /* 1: dynamic shifts (dashSVD); 0: alpha = 0 (Alg. 1 form) */
-  int32_t reserved[7];
+  int32_t gather_bf16;     /* precision form only: 1 stores the gathered operands Q and Y
+                              of the power-iteration products (Alg. 5 step 4) in BF16 (half
+                              the gather bytes; the PVE surrogate then settles near the
+                              BF16 rounding level of hub-localized singular vectors, so it
+                              suits pve_tol of a few 1e-2 and up); 0 keeps them in FP32.
+                              EINVAL in the plain form. */
+  int32_t reserved[6];
 } dashsvd_options;
 
 typedef struct {

@@ -53,7 +53,8 @@ class dashsvd_options(C.Structure):
     _fields_ = [
         ("form", C.c_int32), ("learned", C.c_int32), ("seed", C.c_uint64),
         ("alpha_prev_mode", C.c_int32), ("use_graph", C.c_int32), ("spmm_variant", C.c_int32),
-        ("record_trace", C.c_int32), ("shift", C.c_int32), ("reserved", C.c_int32 * 7),
+        ("record_trace", C.c_int32), ("shift", C.c_int32), ("gather_bf16", C.c_int32),
+        ("reserved", C.c_int32 * 6),
     ]
 
 

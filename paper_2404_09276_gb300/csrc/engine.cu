@@ -65,7 +65,7 @@ struct GraphKey {
   double tol;
   float *U, *S, *V;
   uint64_t seed;
-  int alpha_prev_mode, shift, record_trace, var_fwd, var_bwd, form;
+  int alpha_prev_mode, shift, record_trace, var_fwd, var_bwd, form, gather;
   bool operator==(const GraphKey& o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
 };
 
@@ -100,7 +100,7 @@ struct dashsvd_handle_s {
   struct Tune {
     const void *rowptr, *colidx;
     int64_t m, n, nnz;
-    int l, form, var_fwd32, var_bwd32, var_fwd, var_bwd;
+    int l, form, gather, var_fwd32, var_bwd32, var_fwd, var_bwd;
   };
   std::vector<Tune> tuned;
 };
@@ -161,6 +161,8 @@ EigArgs eig_args(dashsvd_handle h, const RunPlan& p, int mode, unsigned long lon
 }
 
 bool precision(dashsvd_handle h) { return h->opt.form == DASHSVD_FORM_PRECISION; }
+// BF16 storage of the gathered operands Q and Y (an option of the precision form)
+bool bf16_gathers(dashsvd_handle h) { return precision(h) && h->opt.gather_bf16; }
 
 // Refinement iterations of the precision form's FP64 eigensolve, and the
 // rounding level of its BF16x3 Gram used by the null-column test (R6).
@@ -185,15 +187,18 @@ cudaError_t eigsvd_step(dashsvd_handle h, const RunPlan& p, const float* C, int6
   return launch_eig_f32(as<float>(h->G), p.ld, eig_args(h, p, mode, cond), eig_work_view(h->eigw.p), st);
 }
 
-// Q <- Z W (the new basis): FP32 in the plain form; in the precision form BF16
-// for the next gathers plus FP32 once the loop is about to end (the final
-// B = A Q uses the FP32 copy)
+// Q <- Z W (the new basis): FP32 (SIMT in the plain form, BF16x3 tensor cores
+// in the precision form); with BF16 gathers, BF16 for the next gathers plus
+// FP32 once the loop is about to end (the final B = A Q uses the FP32 copy)
 cudaError_t project_basis(dashsvd_handle h, const RunPlan& p, cudaStream_t st) {
-  if (precision(h)) {
+  if (bf16_gathers(h)) {
     const Control* ctl = as<Control>(h->ctl);
     return launch_project_tc(as<float>(h->Z), p.nw, p.l, p.ld, as<float>(h->W), p.ld, p.l, as<float>(h->Q), p.ld,
                              h->Qb.p, p.ld, &ctl->cont, as<int>(h->errw), h->num_sms, st);
   }
+  if (precision(h))
+    return launch_project_tc(as<float>(h->Z), p.nw, p.l, p.ld, as<float>(h->W), p.ld, p.l, as<float>(h->Q), p.ld,
+                             nullptr, 0, nullptr, as<int>(h->errw), h->num_sms, st);
   return launch_project(as<float>(h->Z), p.nw, p.l, p.ld, as<float>(h->W), p.ld, p.l, as<float>(h->Q), p.ld,
                         h->num_sms, st);
 }
@@ -214,7 +219,7 @@ cudaError_t launch_pass(dashsvd_handle h, const RunPlan& p, unsigned long long c
   cudaError_t e;
   const Control* ctl = as<Control>(h->ctl);
   // step 4: Y = A Q; Z = A^T Y - alpha Q; [Q, Shat] = eigSVD(Z)
-  if (precision(h)) {
+  if (bf16_gathers(h)) {
     if ((e = launch_spmm_bf16(p.Aw, p.part_fwd, h->Qb.p, p.ld, p.l, h->Y.p, true, p.ld, nullptr, nullptr, 0,
                               p.var_fwd, p.scr, h->num_sms, st)) != cudaSuccess)
       return e;
@@ -316,7 +321,7 @@ constexpr int kSpmmVariants = 6;  // split (warp per row, merge path) x 3 config
 int autotune_spmm(dashsvd_handle h, RunPlan& p, const dashsvd_csr& A) {
   for (const auto& t : h->tuned)
     if (t.rowptr == A.rowptr && t.colidx == A.colidx && t.m == A.m && t.n == A.n && t.nnz == A.nnz && t.l == p.l &&
-        t.form == h->opt.form) {
+        t.form == h->opt.form && t.gather == h->opt.gather_bf16) {
       p.var_fwd32 = t.var_fwd32;
       p.var_bwd32 = t.var_bwd32;
       p.var_fwd = t.var_fwd;
@@ -331,7 +336,7 @@ int autotune_spmm(dashsvd_handle h, RunPlan& p, const dashsvd_csr& A) {
   DS_CUDA(cudaEventCreate(&e0));
   DS_CUDA(cudaEventCreate(&e1));
   const Control* ctl = as<Control>(h->ctl);
-  const int nprod = precision(h) ? 4 : 2;
+  const int nprod = bf16_gathers(h) ? 4 : 2;
   float best[4] = {3.4e38f, 3.4e38f, 3.4e38f, 3.4e38f};
   int arg[4] = {1, 1, 1, 1};
   cudaError_t err = cudaSuccess;
@@ -373,9 +378,10 @@ int autotune_spmm(dashsvd_handle h, RunPlan& p, const dashsvd_csr& A) {
   DS_CUDA(err);
   p.var_fwd32 = arg[0];
   p.var_bwd32 = arg[1];
-  p.var_fwd = precision(h) ? arg[2] : arg[0];
-  p.var_bwd = precision(h) ? arg[3] : arg[1];
-  h->tuned.push_back({A.rowptr, A.colidx, A.m, A.n, A.nnz, p.l, h->opt.form, p.var_fwd32, p.var_bwd32, p.var_fwd,
+  p.var_fwd = bf16_gathers(h) ? arg[2] : arg[0];
+  p.var_bwd = bf16_gathers(h) ? arg[3] : arg[1];
+  h->tuned.push_back({A.rowptr, A.colidx, A.m, A.n, A.nnz, p.l, h->opt.form, h->opt.gather_bf16, p.var_fwd32,
+                      p.var_bwd32, p.var_fwd,
                       p.var_bwd});
   return DASHSVD_OK;
 }
@@ -496,6 +502,7 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
   const int64_t l = (int64_t)k + s;
   const int64_t mn = A->m < A->n ? A->m : A->n;
   if (l > mn || l > DASHSVD_MAX_L) return DASHSVD_EINVAL;
+  if (h->opt.gather_bf16 && !precision(h)) return DASHSVD_EINVAL;
   if ((h->opt.form != DASHSVD_FORM_PLAIN && h->opt.form != DASHSVD_FORM_PRECISION) || h->opt.learned)
     return DASHSVD_ENOTIMPL;
 
@@ -550,7 +557,7 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
       (rc = ensure(h->trace, sizeof(double) * (size_t)((max_passes + 1) * (5 + l)), &moved)) ||
       (rc = ensure(h->eigw, eig_work_bytes(), &moved)) || (rc = ensure(h->errw, 16, &moved)) ||
       (rc = ensure(h->G64, sizeof(double) * (size_t)(p.ld * p.ld), &moved)) ||
-      (precision(h) && (rc = ensure(h->Qb, 2 * (size_t)(p.nw * p.ld), &moved))) ||
+      (bf16_gathers(h) && (rc = ensure(h->Qb, 2 * (size_t)(p.nw * p.ld), &moved))) ||
       (precision(h) &&
        (rc = ensure(h->partial, sizeof(float) * std::max(gram_tc_partial_floats(p.mw, p.l, h->num_sms),
                                                          gram_tc_partial_floats(p.nw, p.l, h->num_sms)),
@@ -594,6 +601,7 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
     key.var_fwd = p.var_fwd | (p.var_fwd32 << 8);
     key.var_bwd = p.var_bwd | (p.var_bwd32 << 8);
     key.form = h->opt.form;
+    key.gather = h->opt.gather_bf16;
     if (moved || !h->have_graph || !(key == h->key)) {
       if ((rc = build_graph(h, p)) != DASHSVD_OK) return rc;
       h->key = key;

@@ -11,18 +11,21 @@
 // tau = (G_qq - G_pp) / (2 G_pq), t = sign(tau) / (|tau| + sqrt(1 + tau^2)),
 // c = 1 / sqrt(1 + t^2), s = t c; it is skipped when |G_pq| <= eps sqrt(G_pp G_qq)
 // (the relative criterion of Demmel and Veselic, which keeps small eigenvalues
-// of a positive semidefinite G accurate), and a sweep without rotations ends
-// the iteration. Each step updates the 2x2 blocks (I, J), I <= J, of G as
-// J_I^T B J_J (one thread per block) and appends its (c, s) to a rotation log.
+// of a positive semidefinite G accurate). The iteration ends when no pair is
+// above that threshold, which is checked before each sweep. Each step updates
+// the 2x2 blocks (I, J), I <= J, of G as J_I^T B J_J and appends its (c, s)
+// to a rotation log.
 //
 // Kernel 2 (one warp per eigenvector): V = J_1 J_2 ... J_T, so column c of V
 // is J_1 (J_2 (... (J_T e_c))): each warp replays the log backwards on e_c.
-// The warp then applies the eigSVD conventions (descending order with ties by
-// lower index, sign so the largest-|.| entry is positive, zero column where
-// D_i <= 16 eps D_1) and writes its column of W = V S^-1 (Alg. 3 steps 2-4).
-// CTA 0 also runs the dashSVD control: the PVE test of Alg. 5 step 5 with the
-// surrogate Shat_i + alpha of Prop. 3, the shift update of step 6, step 7's
-// bookkeeping, and the loop flag (a CUDA graph conditional).
+//
+// Kernel 3 (one warp per eigenvector) applies the eigSVD conventions
+// (descending order with ties by lower index, sign so the largest-|.| entry is
+// positive, zero column where the eigenvalue is at the rounding level of the
+// diagonal entries it is made of) and writes its column of W = V S^-1 (Alg. 3
+// steps 2-4). CTA 0 also runs the dashSVD control: the PVE test of Alg. 5
+// step 5 with the surrogate Shat_i + alpha of Prop. 3, the shift update of
+// step 6, step 7's bookkeeping, and the loop flag (a CUDA graph conditional).
 #include "internal.cuh"
 
 namespace dsvd {
@@ -32,168 +35,185 @@ constexpr int kJacThreads = 1024;
 constexpr int kMaxN = kMaxL;  // N <= 256
 constexpr float kEps32 = 1.1920929e-07f;
 
-__device__ __forceinline__ void rr_pair(int i, int step, int N, int& p, int& q) {
-  const int M = N - 1;
+
+// Packed upper triangle: element (a, b), a <= b, of an N x N matrix at
+// off(a) + b with off(a) = a N - a (a + 1) / 2.
+__host__ __device__ __forceinline__ int pk_off(int a, int N) { return (a * (2 * N - a - 1)) >> 1; }
+__host__ __device__ __forceinline__ int tri_floats(int N) { return ((N * (N + 1) / 2) + 3) & ~3; }
+
+// Pair i of step `step` without integer division (i < M, step < M).
+__device__ __forceinline__ void rr_pair_fast(int i, int step, int M, int& p, int& q) {
   if (i == 0) {
     p = M;
     q = step;
   } else {
-    p = (step + i) % M;
-    q = (step - i + M) % M;
+    p = step + i;
+    p -= p >= M ? M : 0;
+    q = step - i;
+    q += q < 0 ? M : 0;
   }
 }
 
-// Rotation of pair i in the current step, packed for two 16-byte loads.
+// Rotation of one pair in the current step (16 bytes: one shared-memory load).
 struct __align__(16) PairRec {
-  int p, q, offp, offq;  // indices and packed-row offsets (element (a, b), a <= b, at off[a] + b)
-  float c, s, t;
-  int rot;
+  float c, s;
+  int pq;   // p | q << 16
+  int off;  // off(p) | off(q) << 16 (packed-row offsets, < 2^15 for N <= 256)
 };
 
-struct PairSmem {
+struct JacSmem {
   PairRec r[kMaxN / 2];
-  int off[kMaxN];
-  int count;
+  float d[kMaxN];  // diagonal of the iterate (eigenvalue estimates)
   float gmax;
 };
 
-__device__ __forceinline__ int pko(int a, int offa, int b, int offb) { return a <= b ? offa + b : offb + a; }
+// Dynamic shared memory: the packed triangle (off-diagonal entries) and the
+// table of the P (P + 1) / 2 blocks (I, J), I <= J, that the threads stride over.
+size_t jacobi_smem(int l) {
+  const int N = l + (l & 1), P = N / 2;
+  return (size_t)tri_floats(N) * sizeof(float) + (size_t)(P * (P + 1) / 2) * sizeof(int);
+}
 
+// Step structure: the first P threads compute the step's rotations from the
+// diagonal d and the pivots G_pq (updating d), a barrier, then all threads
+// apply G <- J^T G J to the off-diagonal 2x2 blocks, spread evenly over the
+// block table, and a barrier. A sweep starts only if some pair is above the
+// skip threshold, so no sweep is spent just to see that none rotates.
 __global__ void __launch_bounds__(kJacThreads) jacobi_f32_kernel(const float* __restrict__ Gin, int64_t ldg, int l,
                                                                  EigWork wk) {
-  extern __shared__ __align__(16) float G[];
-  __shared__ PairSmem ps;
-  const int N = l + (l & 1);
-  const int P = N / 2;
+  extern __shared__ __align__(16) float dyn[];
+  __shared__ JacSmem js;
+  const int N = l + (l & 1), P = N / 2, M = N - 1;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
-  for (int a = tid; a < N; a += nt) ps.off[a] = a * N - ((a * (a - 1)) >> 1) - a;
-  if (tid == 0) ps.gmax = 0.f;
+  const int nblk = P * (P + 1) / 2;
+  float* G = dyn;
+  int* blk = reinterpret_cast<int*>(G + tri_floats(N));
+  float* d = js.d;
+
+  if (tid == 0) js.gmax = 0.f;
+  for (int I = 0; I < P; ++I) {  // block table, row-major over I <= J
+    const int base = I * P - ((I * (I - 1)) >> 1);
+    for (int J = I + tid; J < P; J += nt) blk[base + (J - I)] = I | (J << 16);
+  }
   __syncthreads();
   float gm = 0.f;
   for (int idx = tid; idx < N * N; idx += nt) {
     const int a = idx / N, b = idx - a * N;
     if (b < a) continue;
     const float g = (a < l && b < l) ? Gin[(int64_t)a * ldg + b] : 0.f;
-    G[ps.off[a] + b] = g;
     if (a == b) {
       gm = fmaxf(gm, fabsf(g));
+      d[a] = g;
       if (a < l) wk.d0[a] = g;
+    } else {
+      G[pk_off(a, N) + b] = g;
     }
   }
-  atomicMax(reinterpret_cast<int*>(&ps.gmax), __float_as_int(gm));  // non-negative floats order as ints
+  atomicMax(reinterpret_cast<int*>(&js.gmax), __float_as_int(gm));  // non-negative floats order as ints
   __syncthreads();
-  const float tiny = ps.gmax * 1e-30f + 1e-35f;
-  const int F = (P + 1) / 2;  // folded pair-rows: I and P-1-I share one row of P+1 blocks
+  const float tiny = js.gmax * 1e-30f + 1e-35f;
   float2* log = wk.log;
   int sweep = 0;
   bool converged = false;
-  for (; sweep < kMaxSweeps; ++sweep) {
-    if (tid == 0) ps.count = 0;
-    __syncthreads();
-    for (int step = 0; step < N - 1; ++step) {
+  for (; sweep <= kMaxSweeps; ++sweep) {
+    // convergence: no off-diagonal pair above the skip threshold
+    int found = 0;
+    for (int idx = tid; idx < N * N && !found; idx += nt) {
+      const int a = idx / N, b = idx - a * N;
+      if (b <= a || b >= l) continue;
+      const float g = fabsf(G[pk_off(a, N) + b]);
+      found = g > kEps32 * sqrtf(fabsf(d[a]) * fabsf(d[b])) && g > tiny;
+    }
+    if (!__syncthreads_or(found)) {
+      converged = true;
+      break;
+    }
+    if (sweep == kMaxSweeps) break;
+    for (int step = 0; step < M; ++step) {
       if (tid < P) {
         int p, q;
-        rr_pair(tid, step, N, p, q);
-        PairRec rec;
-        rec.p = p;
-        rec.q = q;
-        rec.offp = ps.off[p];
-        rec.offq = ps.off[q];
-        float c = 1.f, s = 0.f, t = 0.f;
-        int rot = 0;
+        rr_pair_fast(tid, step, M, p, q);
+        const int op = pk_off(p, N), oq = pk_off(q, N);
+        float c = 1.f, sn = 0.f;
         if (p < l && q < l) {
-          const float app = G[rec.offp + p], aqq = G[rec.offq + q], apq = G[pko(p, rec.offp, q, rec.offq)];
+          const float app = d[p], aqq = d[q], apq = G[p < q ? op + q : oq + p];
           const float thr = kEps32 * sqrtf(fabsf(app) * fabsf(aqq));
           if (fabsf(apq) > thr && fabsf(apq) > tiny) {
             // correctly rounded sqrt and division keep c^2 + s^2 = 1 to an ulp,
             // so that rotations do not rescale G and V over many sweeps
             const float tau = __fdiv_rn(aqq - app, 2.f * apq);
-            t = __fdiv_rn(tau >= 0.f ? 1.f : -1.f, fabsf(tau) + __fsqrt_rn(fmaf(tau, tau, 1.f)));
+            const float t = __fdiv_rn(tau >= 0.f ? 1.f : -1.f, fabsf(tau) + __fsqrt_rn(fmaf(tau, tau, 1.f)));
             const float r = __fsqrt_rn(fmaf(t, t, 1.f));
             c = __fdiv_rn(1.f, r);
-            s = __fdiv_rn(t, r);
-            rot = 1;
-            atomicAdd(&ps.count, 1);
+            sn = __fdiv_rn(t, r);
+            d[p] = app - t * apq;
+            d[q] = aqq + t * apq;
           }
         }
+        PairRec rec;
         rec.c = c;
-        rec.s = s;
-        rec.t = t;
-        rec.rot = rot;
-        ps.r[tid] = rec;
-        log[((int64_t)sweep * (N - 1) + step) * P + tid] = make_float2(c, s);
+        rec.s = sn;
+        rec.pq = p | (q << 16);
+        rec.off = op | (oq << 16);
+        js.r[tid] = rec;
+        log[((int64_t)sweep * M + step) * P + tid] = make_float2(c, sn);
       }
       __syncthreads();
-      // G <- J^T G J on the 2x2 blocks (I, J), I <= J: warp per folded pair-row
-      for (int f = warp; f < F; f += nwarps) {
-        const int Ia = f, Ib = P - 1 - f;
-        const int na = P - Ia;                  // blocks of row Ia
-        const int nb = (Ib != Ia) ? P - Ib : 0;  // blocks of row Ib
-        const PairRec ra = ps.r[Ia];
-        const PairRec rb = ps.r[Ib];
-        for (int k = lane; k < na + nb; k += 32) {
-          const bool first = k < na;
-          const PairRec& ri = first ? ra : rb;
-          const int J = first ? Ia + k : Ib + (k - na);
-          const PairRec rj = ps.r[J];
-          if (!ri.rot && !rj.rot) continue;
-          if (first ? J == Ia : J == Ib) {  // diagonal block
-            const int ipq = pko(ri.p, ri.offp, ri.q, ri.offq);
-            const float apq = G[ipq];
-            G[ri.offp + ri.p] -= ri.t * apq;
-            G[ri.offq + ri.q] += ri.t * apq;
-            G[ipq] = 0.f;
-            continue;
-          }
-          const int i11 = pko(ri.p, ri.offp, rj.p, rj.offp), i12 = pko(ri.p, ri.offp, rj.q, rj.offq);
-          const int i21 = pko(ri.q, ri.offq, rj.p, rj.offp), i22 = pko(ri.q, ri.offq, rj.q, rj.offq);
-          const float x11 = G[i11], x12 = G[i12], x21 = G[i21], x22 = G[i22];
-          const float y11 = ri.c * x11 - ri.s * x21, y12 = ri.c * x12 - ri.s * x22;
-          const float y21 = ri.s * x11 + ri.c * x21, y22 = ri.s * x12 + ri.c * x22;
-          G[i11] = rj.c * y11 - rj.s * y12;
-          G[i12] = rj.s * y11 + rj.c * y12;
-          G[i21] = rj.c * y21 - rj.s * y22;
-          G[i22] = rj.s * y21 + rj.c * y22;
+      // G <- J^T G J on the 2x2 blocks (I, J), I <= J
+      for (int b = tid; b < nblk; b += nt) {
+        const int ij = blk[b];
+        const int I = ij & 0xffff, J = ij >> 16;
+        const PairRec ri = js.r[I], rj = js.r[J];
+        if (ri.s == 0.f && rj.s == 0.f) continue;
+        const int pI = ri.pq & 0xffff, qI = ri.pq >> 16, pJ = rj.pq & 0xffff, qJ = rj.pq >> 16;
+        const int opI = ri.off & 0xffff, oqI = ri.off >> 16, opJ = rj.off & 0xffff, oqJ = rj.off >> 16;
+        if (I == J) {  // diagonal block: the rotation annihilates G_pq
+          G[pI < qI ? opI + qI : oqI + pI] = 0.f;
+          continue;
         }
+        const int i11 = pI <= pJ ? opI + pJ : opJ + pI, i12 = pI <= qJ ? opI + qJ : oqJ + pI;
+        const int i21 = qI <= pJ ? oqI + pJ : opJ + qI, i22 = qI <= qJ ? oqI + qJ : oqJ + qI;
+        const float x11 = G[i11], x12 = G[i12], x21 = G[i21], x22 = G[i22];
+        const float y11 = ri.c * x11 - ri.s * x21, y12 = ri.c * x12 - ri.s * x22;
+        const float y21 = ri.s * x11 + ri.c * x21, y22 = ri.s * x12 + ri.c * x22;
+        G[i11] = rj.c * y11 - rj.s * y12;
+        G[i12] = rj.s * y11 + rj.c * y12;
+        G[i21] = rj.c * y21 - rj.s * y22;
+        G[i22] = rj.s * y21 + rj.c * y22;
       }
       __syncthreads();
     }
-    if (ps.count == 0) {
-      converged = true;
-      break;
-    }
-    __syncthreads();
   }
-  for (int i = tid; i < l; i += nt) wk.d[i] = G[ps.off[i] + i];
+  for (int i = tid; i < l; i += nt) wk.d[i] = d[i];
   if (tid == 0) {
-    wk.hdr[0] = sweep;  // sweeps whose rotations the replay applies (a final empty sweep adds none)
+    wk.hdr[0] = sweep;  // sweeps whose rotations the replay applies
     wk.hdr[1] = converged ? 0 : kStatusNoConv;
-    wk.hdr[2] = converged ? sweep + 1 : sweep;
+    wk.hdr[2] = sweep;
   }
 }
 
 // ------------------------------------------------------------- kernel 2
 
-constexpr int kVecWarps = 8;
-constexpr int kBatch = 16;  // log steps staged per batch
+constexpr int kVecWarps = 8;     // finish kernel: one warp per eigenvector
+constexpr int kReplayWarps = 2;  // replay: few columns per CTA, so that about l / 2 SMs take part
+constexpr int kBatch = 16;       // log steps staged per batch
 
 struct ReplaySmem {
-  float x[kVecWarps][kMaxN];
+  float x[kReplayWarps][kMaxN];
   float2 logb[2][kBatch * (kMaxN / 2)];
 };
 
 // Column c of V = J_1 (J_2 (... (J_T e_c))): each warp replays the log
 // backwards on e_c, in batches of kBatch steps staged in shared memory by the
 // whole CTA. Writes V row-major (V[j * l + c]).
-__global__ void __launch_bounds__(kVecWarps * 32) eigvec_replay_kernel(EigWork wk, int l) {
+__global__ void __launch_bounds__(kReplayWarps * 32) eigvec_replay_kernel(EigWork wk, int l) {
   __shared__ ReplaySmem rs;
   const int N = l + (l & 1);
   const int P = N / 2;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int nsteps = wk.hdr[0] * (N - 1);
-  const int c = blockIdx.x * kVecWarps + warp;
+  const int c = blockIdx.x * kReplayWarps + warp;
   float* x = rs.x[warp];
   for (int j = lane; j < N; j += 32) x[j] = j == c ? 1.f : 0.f;
   const int nbatch = (nsteps + kBatch - 1) / kBatch;
@@ -221,7 +241,7 @@ __global__ void __launch_bounds__(kVecWarps * 32) eigvec_replay_kernel(EigWork w
           const float2 cs = lgt[i];
           if (cs.y != 0.f) {
             int p, q;
-            rr_pair(i, step, N, p, q);
+            rr_pair_fast(i, step, N - 1, p, q);
             const float xp = x[p], xq = x[q];
             x[p] = cs.x * xp + cs.y * xq;
             x[q] = -cs.y * xp + cs.x * xq;
@@ -406,11 +426,6 @@ __global__ void __launch_bounds__(kVecWarps * 32) finish_kernel(const T* __restr
   }
 }
 
-size_t jacobi_smem(int l) {
-  const int N = l + (l & 1);
-  return (size_t)(N * (N + 1) / 2) * sizeof(float);
-}
-
 }  // namespace
 
 int eig_max_l_f32() { return kMaxL; }
@@ -453,8 +468,8 @@ cudaError_t launch_eig_f32(const float* G, int64_t ldg, const EigArgs& a, const 
   jacobi_f32_kernel<<<1, kJacThreads, jacobi_smem(a.l), st>>>(G, ldg, a.l, wk);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  eigvec_replay_kernel<<<(unsigned)ds_ceil_div(a.l, kReplayWarps), kReplayWarps * 32, 0, st>>>(wk, a.l);
   const unsigned blocks = (unsigned)ds_ceil_div(a.l, kVecWarps);
-  eigvec_replay_kernel<<<blocks, kVecWarps * 32, 0, st>>>(wk, a.l);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   finish_kernel<float><<<blocks, kVecWarps * 32, 0, st>>>(wk.d, wk.V32, wk.d0, (double)kEps32, wk.hdr, a);
   return cudaGetLastError();
@@ -468,8 +483,8 @@ cudaError_t launch_eig_refined(const float* G32, int64_t ldg32, const double* G6
   jacobi_f32_kernel<<<1, kJacThreads, jacobi_smem(a.l), st>>>(G32, ldg32, a.l, wk);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  eigvec_replay_kernel<<<(unsigned)ds_ceil_div(a.l, kReplayWarps), kReplayWarps * 32, 0, st>>>(wk, a.l);
   const unsigned blocks = (unsigned)ds_ceil_div(a.l, kVecWarps);
-  eigvec_replay_kernel<<<blocks, kVecWarps * 32, 0, st>>>(wk, a.l);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const double* X = nullptr;
   if ((e = launch_refine_fp64(G64, ldg64, wk.V32, a.l, iters, wk, &X, st)) != cudaSuccess) return e;

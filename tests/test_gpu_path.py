@@ -124,33 +124,48 @@ def test_large_l_recommender_shape(ds):
     assert rel[0] <= 1e-5
 
 
+@pytest.mark.parametrize("gather_bf16", [0, 1])
 @pytest.mark.parametrize("p", [0, 2, 4])
-def test_precision_form_fixed_passes(ds, p):
-    """Precision form (BF16 gathered operands, BF16x3 Gram and projection, FP64
-    eig/shift/PVE) at fixed p against the FP64 oracle: errors are reported per
-    sigma and bounded by the BF16x3 rounding level amplified by eigSVD."""
+def test_precision_form_fixed_passes(ds, p, gather_bf16):
+    """Precision form (BF16x3 Gram and projection, FP64-refined eig/shift/PVE;
+    FP32 or BF16 gathered operands) at fixed p against the FP64 oracle: errors
+    are bounded by the rounding level of the stored operands amplified by
+    eigSVD's squared conditioning."""
     A, prm = datagen.make_config(1, scale=0.1)
     k, s = prm["k"], prm["s"]
-    U, S, V, info, _ = _run(ds, A, k, s, p, 0.0, form=ds.DASHSVD_FORM_PRECISION)
+    U, S, V, info, _ = _run(ds, A, k, s, p, 0.0, form=ds.DASHSVD_FORM_PRECISION, gather_bf16=gather_bf16)
     ref = oracle.dashsvd(A.to_scipy(), k, s, p_max=p, tol=0.0, seed=0x5EED)
     assert info.passes == p
     rel = np.abs(S - ref.S) / ref.S
     kappa2 = (ref.S[0] / ref.S) ** 2
-    assert np.all(rel <= 2e-3 + 1e-4 * kappa2), rel
-    assert np.max(metrics.principal_angles(V[:, :5], ref.V[:, :5])) < 5e-2
+    if gather_bf16:  # BF16 Q and Y: unit roundoff 2^-9
+        assert np.all(rel <= 2e-3 + 1e-4 * kappa2), rel
+        assert np.max(metrics.principal_angles(V[:, :5], ref.V[:, :5])) < 5e-2
+    else:  # FP32 gathers; BF16x3 Gram and projection keep 16 bits of Z
+        assert np.all(rel <= 1e-4 + 3e-5 * kappa2), rel
+        assert np.max(metrics.principal_angles(V[:, :5], ref.V[:, :5])) < 1e-2
 
 
-def test_precision_form_pve_control(ds):
+@pytest.mark.parametrize("gather_bf16", [0, 1])
+def test_precision_form_pve_control(ds, gather_bf16):
     """Precision form with the PVE test on the 20000 x 10000 workload: stops
     within one pass of the oracle and the true PVE error is within the tolerance
     scale."""
     A, prm = datagen.make_config(1)
     k, s = prm["k"], prm["s"]
-    U, S, V, info, _ = _run(ds, A, k, s, prm["p_max"], prm["tol"], form=ds.DASHSVD_FORM_PRECISION)
+    U, S, V, info, _ = _run(ds, A, k, s, prm["p_max"], prm["tol"], form=ds.DASHSVD_FORM_PRECISION,
+                            gather_bf16=gather_bf16)
     ref = oracle.dashsvd(A.to_scipy(), k, s, p_max=prm["p_max"], tol=prm["tol"], seed=0x5EED)
     assert abs(info.passes - ref.passes) <= 1
     rel = np.abs(S - ref.S) / ref.S
     assert np.max(rel) < 1e-2
+
+
+def test_gather_bf16_needs_precision_form(ds):
+    A, _ = datagen.make_config(1, scale=0.05)
+    with pytest.raises(ds.DashSvdError) as ei:
+        _run(ds, A, 8, 4, 1, 0.0, gather_bf16=1)
+    assert ei.value.status == ds.DASHSVD_EINVAL
 
 
 def test_modes_match_oracle(ds):
