@@ -45,6 +45,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
+from .mlp_ref import features as mlp_features
 from .philox import gaussian_block
 
 EPS64 = np.finfo(np.float64).eps
@@ -128,6 +129,7 @@ def dashsvd(
     shift: bool = True,
     keep_q: bool = False,
     Omega: np.ndarray | None = None,
+    policy=None,
 ) -> Result:
     """dashSVD with PVE accuracy control (Alg. 5) in FP64.
 
@@ -135,6 +137,10 @@ def dashsvd(
     stop test, which gives the fixed-p dashSVD of Alg. 4. ``shift=False`` keeps
     alpha = 0, which is the basic randomized SVD with eigSVD orthonormalization
     (Alg. 1 in the m >= n form). ``Omega`` overrides the Philox block.
+    ``policy`` (learned form) maps the features of a pass (``mlp_ref.features``)
+    to (f, o_1): the next shift is f times the plain rule's value, clamped to
+    [0, that value], and o_1 > 0 stops the run from pass 2 on while the
+    surrogate ratio is at most 3 tol.
     """
     import scipy.sparse as sp
 
@@ -153,6 +159,7 @@ def dashsvd(
     Q, _, _, _ = eigsvd(At @ Om)  # step 2
     alpha = 0.0
     alpha_prev = 0.0
+    ratio_prev = 0.0
     S_prev = np.zeros(l)
     trace = []
     passes = 0
@@ -163,13 +170,21 @@ def dashsvd(
         Q, S, _, _ = eigsvd(C)
         passes = j
         ratio = pve_ratio(S_prev, alpha_prev, S, alpha, k)
-        if tol > 0 and ratio <= tol:  # step 5
+        stop = tol > 0 and ratio <= tol  # step 5
+        f = 1.0
+        if policy is not None:
+            x = mlp_features(S, alpha, ratio, ratio_prev if j > 1 else ratio, j, p_max, tol, k)
+            f, o1 = policy(x)
+            stop = stop or (tol > 0 and j >= 2 and ratio <= 3.0 * tol and o1 > 0.0)
+        if stop:
             trace.append(PassRecord(j, alpha, S, ratio, True, alpha, Q_in))
             converged = True
             break
         alpha_used = alpha
-        if shift and S[l - 1] > alpha:  # step 6
-            alpha = 0.5 * (S[l - 1] + alpha)
+        ratio_prev = ratio
+        if shift:  # step 6 (learned form: a fraction of the same bound)
+            bound = 0.5 * (S[l - 1] + alpha) if S[l - 1] > alpha else alpha
+            alpha = min(max(f * bound, 0.0), bound) if np.isfinite(f) else bound
         S_prev = S  # step 7
         alpha_prev = alpha_used if alpha_prev_mode == 0 else alpha
         trace.append(PassRecord(j, alpha_used, S, ratio, False, alpha, Q_in))
