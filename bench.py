@@ -62,8 +62,9 @@ def _args():
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (testing only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-reps", type=int, default=20)
-    ap.add_argument("--form", default="both", choices=["both", "plain", "precision"],
-                    help="both: time the plain FP32 form and the chosen (precision) form")
+    ap.add_argument("--form", default="both", choices=["both", "plain", "precision", "precision_learned"],
+                    help="both: time the plain FP32 form, the precision form and (when its validation let "
+                         "it ship) the precision form with the learned network; the last is the chosen form")
     ap.add_argument("--with-bf16-gathers", action="store_true",
                     help="also time the precision form with BF16 gathered operands")
     ap.add_argument("--no-graph", action="store_true",
@@ -219,6 +220,8 @@ FORMS = {
     "precision": "precision (FP32 gathers, BF16x3 tcgen05 Gram and projection, FP32 Jacobi refined in FP64, "
                  "FP64 shift/PVE)",
     "precision_bf16": "precision with BF16 gathered Q/Y (BF16x3 tcgen05 Gram and projection, FP64-refined eig)",
+    "precision_learned": "precision + learned shift/stop network (FP32 gathers, BF16x3 tcgen05 Gram and projection, "
+                         "FP64-refined eig, MLP 16-64-2 proposing the shift fraction and an early stop)",
 }
 
 
@@ -256,10 +259,17 @@ def _measure_form(form, args, ds, torch, A, Ad, prm, stream, flush, barrier, wor
     l = k + s
     fcode = ds.DASHSVD_FORM_PLAIN if form == "plain" else ds.DASHSVD_FORM_PRECISION
     gb = 1 if form == "precision_bf16" else 0
+    learned = 1 if form == "precision_learned" else 0
+    if learned:
+        from paper_2404_09276_gb300 import learn
+
+        mlp, _ = learn.load_weights()
     U = torch.empty((A.m, k), dtype=torch.float32, device="cuda")
     S = torch.empty((k,), dtype=torch.float32, device="cuda")
     V = torch.empty((A.n, k), dtype=torch.float32, device="cuda")
-    h = ds.Handle(stream=stream, use_graph=0 if args.no_graph else 1, form=fcode, gather_bf16=gb)
+    h = ds.Handle(stream=stream, use_graph=0 if args.no_graph else 1, form=fcode, gather_bf16=gb, learned=learned)
+    if learned:
+        h.load_mlp(mlp)
     At = h.csr_transpose(Ad)
 
     def timed(tol_run):
@@ -300,7 +310,9 @@ def _measure_form(form, args, ds, torch, A, Ad, prm, stream, flush, barrier, wor
     var_fwd, var_bwd = info.spmm_variant & 0xFF, (info.spmm_variant >> 8) & 0xFF
 
     # one untimed run with the per-pass trace (shift, PVE ratio, Jacobi sweeps)
-    with ds.Handle(stream=stream, record_trace=1, form=fcode, gather_bf16=gb) as ht:
+    with ds.Handle(stream=stream, record_trace=1, form=fcode, gather_bf16=gb, learned=learned) as ht:
+        if learned:
+            ht.load_mlp(mlp)
         ht.run(Ad, k, s, p_max, tol_run, U, S, V)
         trace = [{"pass": j, "alpha": a_used, "pve_ratio": ratio, "eig_sweeps": sw}
                  for j, a_used, ratio, a_next, sw, _ in ht.trace()]
@@ -348,7 +360,7 @@ def _measure_form(form, args, ds, torch, A, Ad, prm, stream, flush, barrier, wor
     alpha = torch.tensor([0.5], dtype=torch.float64, device="cuda")
     reps = args.kernel_reps
     if form != "precision_bf16":
-        simt = form == "plain"
+        simt = form == "plain"  # the learned form uses the precision form's kernels
         kt = {
             "spmm_fwd": _time_kernel(lambda: h.spmm(Ad, Q, l, out=Y, variant=var_fwd), reps, stream),
             "spmm_bwd": _time_kernel(lambda: h.spmm_shift(At, Y, l, alpha, Q, out=Z, variant=var_bwd), reps, stream),
@@ -450,18 +462,22 @@ def ours(args):
             torch.distributed.barrier()
             torch.cuda.synchronize()
 
-    forms = ["plain", "precision"] if args.form == "both" else [args.form]
+    from paper_2404_09276_gb300 import learn
+
+    _, ship = learn.load_weights()
+    forms = ["plain", "precision"] + (["precision_learned"] if ship else []) if args.form == "both" else [args.form]
     if args.with_bf16_gathers:
         forms.append("precision_bf16")
     sigma_ref = _sigma_ref(args.config, args.scale)
     res = {f: _measure_form(f, args, ds, torch, A, Ad, prm, stream, flush, barrier, world, local, sigma_ref)
            for f in forms}
-    chosen = res["precision"] if "precision" in res else res[forms[0]]
+    # the chosen form: precision + the learned network when validation let it ship
+    chosen = next(res[f] for f in ("precision_learned", "precision", forms[0]) if f in res)
     pk = _peaks()
     line = {
         "metric": METRIC, "value": chosen["value"], "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": chosen["value"] * 1e3, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16x3+f64" if chosen["form"] == "precision" else "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32" if chosen["form"] == "plain" else "bf16x3+f64", "data": "synthetic",
         "config": {"workload": name, "form": FORMS[chosen["form"]],
                    "l2": "flushed (256 MB write) before each step",
                    "loop": "host-driven" if args.no_graph else "CUDA graph, device-side WHILE",
@@ -479,6 +495,11 @@ def ours(args):
                                           "pve_surrogate": pb["pve_surrogate"], "kernels_s": pb["kernels_s"],
                                           "spmm": pb["spmm"], "trace_ratio": [t["pve_ratio"] for t in pb["trace"]]}
         line["gpu_launches"] += pb["gpu_launches"]
+    if "precision" in res and chosen["form"] == "precision_learned":
+        pr = res["precision"]
+        line["precision_plain_rule"] = {"value": pr["value"], "passes": pr["passes"], "status": pr["status"],
+                                        "accuracy": pr["accuracy"], "e2e": pr["e2e"]["value"]}
+        line["gpu_launches"] += pr["gpu_launches"]
     if "plain" in res and chosen["form"] != "plain":
         pl = res["plain"]
         line["plain"] = {"value": pl["value"], "passes": pl["passes"], "status": pl["status"],

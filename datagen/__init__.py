@@ -28,6 +28,7 @@ __all__ = [
     "scaled_gaussian",
     "social_graph",
     "term_document",
+    "training_matrix",
     "recommender",
     "dense_as_csr",
     "dense_with_spectrum",
@@ -201,12 +202,12 @@ def term_document(
 
 def recommender(
     m: int, n: int, seed: int, mean_degree: float = 50.0, degree_tail: float = 1.2,
-    popularity: float = 1.2, name: str = "recommender",
+    popularity: float = 1.2, name: str = "recommender", max_degree: int | None = None,
 ) -> Csr:
-    """User-item ratings: power-law user degrees (capped at n), distinct Zipf
-    items through a permutation, ratings uniform in {1, ..., 5}."""
+    """User-item ratings: power-law user degrees (capped at ``max_degree``, default
+    n), distinct Zipf items through a permutation, ratings uniform in {1, ..., 5}."""
     rng = np.random.default_rng(seed)
-    deg = _powerlaw_degrees(m, degree_tail, mean_degree, n, rng)
+    deg = _powerlaw_degrees(m, degree_tail, mean_degree, n if max_degree is None else min(max_degree, n), rng)
     perm = rng.permutation(n)
     zipf = _ZipfSampler(n, popularity)
     keys = _distinct_targets(deg, n, lambda k, g: perm[zipf(k, g)], rng)
@@ -246,6 +247,34 @@ CONFIGS = {
     4: dict(kind="term_document", m=500_000, n=100_000, k=100, s=50, p_max=20, tol=1e-2),
     5: dict(kind="recommender", m=2_000_000, n=200_000, k=200, s=20, p_max=20, tol=1e-2),
 }
+
+
+# Training and validation family of the learned form: seeds 10,000.. are the
+# training matrices and 20,000.. the held-out ones (disjoint by construction).
+TRAIN_SEED0, VAL_SEED0 = 10_000, 20_000
+
+
+def training_matrix(seed: int, m_range=(10_000, 60_000)) -> tuple[Csr, dict]:
+    """One member of the learned form's matrix family: a power-law social graph,
+    a recommender or a term-document matrix (chosen by the seed), with m drawn
+    uniformly from ``m_range``, n = m * U[1/4, 1], the degree mean, tails and
+    popularity drawn per matrix, and k in {20, 50, 100} with s = k / 2."""
+    rng = np.random.default_rng(seed)
+    m = int(rng.integers(m_range[0], m_range[1] + 1))
+    n = max(400, int(m * rng.uniform(0.25, 1.0)))
+    kind = ("social_graph", "recommender", "term_document")[int(rng.integers(0, 3))]
+    k = int((20, 50, 100)[int(rng.integers(0, 3))])
+    sub = int(rng.integers(0, 2**31))
+    if kind == "social_graph":
+        A = social_graph(m, n, sub, mean_degree=float(rng.uniform(8, 25)), degree_tail=float(rng.uniform(1.05, 1.5)),
+                         max_degree=n // 8, popularity=float(rng.uniform(0.9, 1.3)), name="train_social")
+    elif kind == "recommender":
+        A = recommender(m, n, sub, mean_degree=float(rng.uniform(15, 50)), degree_tail=float(rng.uniform(1.1, 1.6)),
+                        popularity=float(rng.uniform(0.9, 1.4)), name="train_recommender", max_degree=n // 8)
+    else:
+        A = term_document(m, n, sub, mean_len=float(rng.uniform(20, 60)), sigma=float(rng.uniform(0.6, 1.2)),
+                          popularity=float(rng.uniform(0.9, 1.3)), name="train_term_document")
+    return A, dict(kind=kind, k=k, s=k // 2, p_max=20, tol=1e-2)
 
 
 def make_config(cfg: int, scale: float = 1.0) -> tuple[Csr, dict]:

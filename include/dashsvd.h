@@ -72,7 +72,8 @@ typedef struct {
 
 typedef struct {
   int32_t form;            /* dashsvd_form */
-  int32_t learned;         /* 1: the loaded MLP proposes the shift and the stop pass */
+  int32_t learned;         /* 1: the loaded network proposes each shift and may stop
+                              early (see "learned form" below); 0: plain rule */
   uint64_t seed;           /* Philox key of the Gaussian block Omega (Alg. 5 step 1) */
   int32_t alpha_prev_mode; /* 0: alpha' = the shift used in the pass that produced
                               Shat' (pairs each Shat with its own shift, as in Prop. 3);
@@ -138,8 +139,54 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
  * Writes at most `cap` doubles; *count receives the number of records. */
 int dashsvd_get_trace(dashsvd_handle h, double* out, int64_t cap, int64_t* count, int* l);
 
-/* Load the weights of the learned shift/stop network (HOST pointer). */
+/* ---- learned form --------------------------------------------------------
+ * The paper has no learned component; this is an addition. A network
+ * 16 -> 64 (tanh) -> 2 reads features of each power-iteration pass (Shat_i +
+ * alpha relative to Shat_1 + alpha, the PVE surrogate ratios, the pass index;
+ * Prop. 3 makes Shat_i + alpha the estimate of sigma_i^2) and proposes
+ *   - the next shift: sigmoid(o_0) times the plain rule's value of Alg. 5
+ *     step 6 ((Shat_l + alpha) / 2 if Shat_l > alpha, else alpha), so it stays
+ *     in the safe range of Prop. 1; a non-finite output falls back to the
+ *     plain rule;
+ *   - an early stop (o_1 > 0), honoured from pass 2 on and only while the
+ *     surrogate ratio of step 5 is at most 3 pve_tol; the surrogate test
+ *     itself still stops the run at pve_tol.
+ * Parameters (1218 floats): W1 (64 x 16, row-major), b1 (64), W2 (2 x 64), b2 (2).
+ * Features are computed on the device, in FP64, from the same quantities the
+ * trace records (dashsvd_get_trace), and rounded to FP32; the network runs in
+ * FP32. */
+#define DASHSVD_MLP_PARAMS 1218
+#define DASHSVD_MLP_IN 16
+
+/* Copy the network's parameters from HOST memory into the handle (count must
+ * be DASHSVD_MLP_PARAMS, all finite; else DASHSVD_EINVAL). Waits for the
+ * handle's stream first. Runs with options.learned = 1 need a loaded network. */
 int dashsvd_load_mlp(dashsvd_handle h, const float* weights, int64_t count);
+
+/* Training-side entry points (all pointers DEVICE, asynchronous on the
+ * handle's stream). */
+
+/* Features (count x 16, FP32) of trace records (count x (5 + l) doubles laid
+ * out as dashsvd_get_trace writes them, back on the device). A record whose
+ * predecessor has pass index j - 1 takes that record's ratio as the previous
+ * ratio; otherwise (a run's first pass) the previous ratio is its own. */
+int dashsvd_mlp_features(dashsvd_handle h, const double* records, int64_t count, int l, int k, int max_passes,
+                         double pve_tol, float* X);
+
+/* out (batch x 2) = network outputs (o_0, o_1) for features X (batch x 16). */
+int dashsvd_mlp_forward(dashsvd_handle h, const float* W, const float* X, int64_t batch, float* out);
+
+/* Loss and its gradient (DASHSVD_MLP_PARAMS floats) over a batch with targets
+ * T and weights M (batch x 2 each):
+ *   L = (1/batch) sum_b [ M_b0 (sigmoid(o_b0) - T_b0)^2 + M_b1 (softplus(o_b1) - T_b1 o_b1) ].
+ * Deterministic (fixed summation order). `loss` is one float. */
+int dashsvd_mlp_loss_grad(dashsvd_handle h, const float* W, const float* X, const float* targets,
+                          const float* weights, int64_t batch, float* grad, float* loss);
+
+/* One Adam step (Kingma and Ba, with bias correction; `step` counts from 1)
+ * on W with gradient `grad` and moment buffers m, v (DASHSVD_MLP_PARAMS each). */
+int dashsvd_mlp_adam(dashsvd_handle h, float* W, const float* grad, float* m, float* v, int step, float lr,
+                     float beta1, float beta2, float eps);
 
 /* Text for a status code. */
 const char* dashsvd_status_string(int status);

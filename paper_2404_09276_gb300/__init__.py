@@ -39,7 +39,10 @@ EXPORTS = (
     "dashsvd_csr_transpose", "dashsvd_spmm", "dashsvd_spmm_shift", "dashsvd_spmm_bf16", "dashsvd_gram",
     "dashsvd_gram_bf16x3",
     "dashsvd_project", "dashsvd_project_bf16x3", "dashsvd_eigsvd", "dashsvd_gram_noalloc",
+    "dashsvd_mlp_features", "dashsvd_mlp_forward", "dashsvd_mlp_loss_grad", "dashsvd_mlp_adam",
 )
+MLP_PARAMS = 1218
+MLP_IN = 16
 
 
 class dashsvd_csr(C.Structure):
@@ -93,6 +96,10 @@ def _load():
         "dashsvd_project_bf16x3": (I, [P, P, I64, I, I64, P, I64, I, P, I64]),
         "dashsvd_eigsvd": (I, [P, P, I64, I, I64, P, I64, P, P, I]),
         "dashsvd_gram_noalloc": (I, [P, I64, I, I64, P, I64, P]),
+        "dashsvd_mlp_features": (I, [P, P, I64, I, I, I, D, P]),
+        "dashsvd_mlp_forward": (I, [P, P, P, I64, P]),
+        "dashsvd_mlp_loss_grad": (I, [P, P, P, P, P, I64, P, P]),
+        "dashsvd_mlp_adam": (I, [P, P, P, P, P, I, C.c_float, C.c_float, C.c_float, C.c_float]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -129,6 +136,10 @@ dashsvd_project = _export("dashsvd_project")
 dashsvd_project_bf16x3 = _export("dashsvd_project_bf16x3")
 dashsvd_eigsvd = _export("dashsvd_eigsvd")
 dashsvd_gram_noalloc = _export("dashsvd_gram_noalloc")
+dashsvd_mlp_features = _export("dashsvd_mlp_features")
+dashsvd_mlp_forward = _export("dashsvd_mlp_forward")
+dashsvd_mlp_loss_grad = _export("dashsvd_mlp_loss_grad")
+dashsvd_mlp_adam = _export("dashsvd_mlp_adam")
 
 
 class DashSvdError(RuntimeError):
@@ -328,6 +339,44 @@ class Handle:
         check(dashsvd_project_bf16x3(self.h, Cm.data_ptr(), Cm.shape[0], l, Cm.stride(0), W.data_ptr(), W.stride(0),
                                      cols, out.data_ptr(), out.stride(0)), "dashsvd_project_bf16x3")
         return out
+
+    # -- learned form ------------------------------------------------------------
+    def load_mlp(self, weights):
+        """Load the shift/stop network (1218 values, any array-like) into the handle."""
+        import numpy as np
+
+        w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32).ravel())
+        check(dashsvd_load_mlp(self.h, w.ctypes.data, w.size), "dashsvd_load_mlp")
+
+    def mlp_features(self, records, l: int, k: int, max_passes: int, pve_tol: float):
+        """records: torch float64 tensor (count x (5 + l)) on the GPU -> features (count x 16)."""
+        import torch
+
+        X = torch.empty((records.shape[0], MLP_IN), dtype=torch.float32, device=records.device)
+        check(dashsvd_mlp_features(self.h, records.data_ptr(), records.shape[0], l, k, max_passes, pve_tol,
+                                   X.data_ptr()), "dashsvd_mlp_features")
+        return X
+
+    def mlp_forward(self, W, X):
+        import torch
+
+        out = torch.empty((X.shape[0], 2), dtype=torch.float32, device=X.device)
+        check(dashsvd_mlp_forward(self.h, W.data_ptr(), X.data_ptr(), X.shape[0], out.data_ptr()),
+              "dashsvd_mlp_forward")
+        return out
+
+    def mlp_loss_grad(self, W, X, T, M, grad=None, loss=None):
+        import torch
+
+        grad = torch.empty((MLP_PARAMS,), dtype=torch.float32, device=X.device) if grad is None else grad
+        loss = torch.empty((1,), dtype=torch.float32, device=X.device) if loss is None else loss
+        check(dashsvd_mlp_loss_grad(self.h, W.data_ptr(), X.data_ptr(), T.data_ptr(), M.data_ptr(), X.shape[0],
+                                    grad.data_ptr(), loss.data_ptr()), "dashsvd_mlp_loss_grad")
+        return grad, loss
+
+    def mlp_adam(self, W, grad, m, v, step: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8):
+        check(dashsvd_mlp_adam(self.h, W.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(), step, lr, beta1,
+                               beta2, eps), "dashsvd_mlp_adam")
 
     def eigsvd(self, Cm, l: int, form: int = DASHSVD_FORM_PLAIN):
         import torch

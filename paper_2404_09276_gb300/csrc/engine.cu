@@ -13,12 +13,14 @@
 // on any pass. The graph is cached per handle and rebuilt when an argument
 // that is baked into it changes.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
 
 #include "internal.cuh"
+#include "mlp_common.cuh"
 
 namespace dsvd {
 
@@ -65,7 +67,7 @@ struct GraphKey {
   double tol;
   float *U, *S, *V;
   uint64_t seed;
-  int alpha_prev_mode, shift, record_trace, var_fwd, var_bwd, form, gather;
+  int alpha_prev_mode, shift, record_trace, var_fwd, var_bwd, form, gather, learned;
   bool operator==(const GraphKey& o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
 };
 
@@ -87,6 +89,8 @@ struct dashsvd_handle_s {
   DevBuf seg_fwd, seg_bwd;  // merge-path partitions of A and A^T (rows, nonzeros)
   DevBuf errw;              // device error word of the bounded-wait kernels
   DevBuf Qb, G64;           // precision form: BF16 basis, FP64 Gram
+  DevBuf mlpw, mlp_part;    // learned form: network parameters, gradient partials
+  bool mlp_loaded = false;
   // cached graph
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -95,7 +99,6 @@ struct dashsvd_handle_s {
   // last run
   int last_l = 0;
   int64_t last_records = 0;
-  std::vector<float> mlp;
   // autotuner cache: SpMM variant per (matrix, l, form)
   struct Tune {
     const void *rowptr, *colidx;
@@ -157,6 +160,7 @@ EigArgs eig_args(dashsvd_handle h, const RunPlan& p, int mode, unsigned long lon
   a.trace = (mode == kModePass && h->opt.record_trace) ? as<double>(h->trace) : nullptr;
   a.cond = cond;
   a.use_cond = cond != 0;
+  a.mlp = (mode == kModePass && h->opt.learned) ? as<float>(h->mlpw) : nullptr;
   return a;
 }
 
@@ -467,7 +471,8 @@ int dashsvd_destroy(dashsvd_handle h) {
   drop_graph(h);
   DevBuf* bufs[] = {&h->rowptr_b, &h->col_b, &h->val_b, &h->cursor, &h->scan_tmp, &h->Y,       &h->Z,
                     &h->Q,        &h->G,     &h->W,     &h->W2,     &h->partial,  &h->carry, &h->carry_row,
-                    &h->ctl,      &h->trace, &h->eigw,   &h->seg_fwd, &h->seg_bwd, &h->errw, &h->Qb, &h->G64};
+                    &h->ctl,      &h->trace, &h->eigw,   &h->seg_fwd, &h->seg_bwd, &h->errw, &h->Qb, &h->G64,
+                    &h->mlpw, &h->mlp_part};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (h->side) cudaStreamDestroy(h->side);
@@ -477,9 +482,50 @@ int dashsvd_destroy(dashsvd_handle h) {
 }
 
 int dashsvd_load_mlp(dashsvd_handle h, const float* weights, int64_t count) {
-  if (!h || (!weights && count > 0) || count < 0) return DASHSVD_EINVAL;
-  h->mlp.assign(weights, weights + count);
-  return DASHSVD_ENOTIMPL;
+  if (!h || !weights || count != kMlpParams) return DASHSVD_EINVAL;
+  for (int64_t i = 0; i < count; ++i)
+    if (!std::isfinite(weights[i])) return DASHSVD_EINVAL;
+  int rc;
+  bool moved = false;
+  if ((rc = ensure(h->mlpw, sizeof(float) * kMlpParams, &moved))) return rc;
+  DS_CUDA(cudaStreamSynchronize(h->stream));  // no run of this handle reads the old weights any more
+  DS_CUDA(cudaMemcpy(h->mlpw.p, weights, sizeof(float) * kMlpParams, cudaMemcpyHostToDevice));
+  h->mlp_loaded = true;
+  return DASHSVD_OK;
+}
+
+int dashsvd_mlp_features(dashsvd_handle h, const double* records, int64_t count, int l, int k, int max_passes,
+                         double pve_tol, float* X) {
+  if (!h || count < 0 || (count > 0 && (!records || !X)) || l < 2 || l > DASHSVD_MAX_L || k < 1 || k >= l)
+    return DASHSVD_EINVAL;
+  DS_CUDA(launch_mlp_features(records, count, l, k, max_passes, pve_tol, X, h->stream));
+  return DASHSVD_OK;
+}
+
+int dashsvd_mlp_forward(dashsvd_handle h, const float* W, const float* X, int64_t batch, float* out) {
+  if (!h || !W || batch < 0 || (batch > 0 && (!X || !out))) return DASHSVD_EINVAL;
+  DS_CUDA(launch_mlp_forward(W, X, batch, out, h->stream));
+  return DASHSVD_OK;
+}
+
+int dashsvd_mlp_loss_grad(dashsvd_handle h, const float* W, const float* X, const float* targets,
+                          const float* weights, int64_t batch, float* grad, float* loss) {
+  if (!h || !W || !X || !targets || !weights || !grad || !loss || batch < 1) return DASHSVD_EINVAL;
+  const int parts = mlp_grad_parts(batch, h->num_sms);
+  int rc;
+  bool moved = false;
+  if ((rc = ensure(h->mlp_part, sizeof(float) * (size_t)parts * (kMlpParams + 1), &moved))) return rc;
+  DS_CUDA(launch_mlp_loss_grad(W, X, targets, weights, batch, as<float>(h->mlp_part), parts, grad, loss, h->stream));
+  return DASHSVD_OK;
+}
+
+int dashsvd_mlp_adam(dashsvd_handle h, float* W, const float* grad, float* m, float* v, int step, float lr,
+                     float beta1, float beta2, float eps) {
+  if (!h || !W || !grad || !m || !v || step < 1 || !(lr > 0.f) || !(beta1 >= 0.f && beta1 < 1.f) ||
+      !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+    return DASHSVD_EINVAL;
+  DS_CUDA(launch_mlp_adam(W, grad, m, v, step, lr, beta1, beta2, eps, h->stream));
+  return DASHSVD_OK;
 }
 
 int dashsvd_get_trace(dashsvd_handle h, double* out, int64_t cap, int64_t* count, int* l) {
@@ -503,7 +549,9 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
   const int64_t mn = A->m < A->n ? A->m : A->n;
   if (l > mn || l > DASHSVD_MAX_L) return DASHSVD_EINVAL;
   if (h->opt.gather_bf16 && !precision(h)) return DASHSVD_EINVAL;
-  if ((h->opt.form != DASHSVD_FORM_PLAIN && h->opt.form != DASHSVD_FORM_PRECISION) || h->opt.learned)
+  if (h->opt.learned && !h->mlp_loaded) return DASHSVD_EINVAL;
+  if ((h->opt.form != DASHSVD_FORM_PLAIN && h->opt.form != DASHSVD_FORM_PRECISION) || h->opt.learned < 0 ||
+      h->opt.learned > 1)
     return DASHSVD_ENOTIMPL;
 
   RunPlan p;
@@ -602,6 +650,7 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
     key.var_bwd = p.var_bwd | (p.var_bwd32 << 8);
     key.form = h->opt.form;
     key.gather = h->opt.gather_bf16;
+    key.learned = h->opt.learned;
     if (moved || !h->have_graph || !(key == h->key)) {
       if ((rc = build_graph(h, p)) != DASHSVD_OK) return rc;
       h->key = key;
@@ -636,7 +685,8 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
     int64_t ws = 0;
     DevBuf* bufs[] = {&h->rowptr_b, &h->col_b, &h->val_b, &h->cursor, &h->scan_tmp, &h->Y,       &h->Z,
                       &h->Q,        &h->G,     &h->W,     &h->W2,     &h->partial,  &h->carry, &h->carry_row,
-                      &h->ctl,      &h->trace, &h->eigw,   &h->seg_fwd, &h->seg_bwd, &h->errw, &h->Qb, &h->G64};
+                      &h->ctl,      &h->trace, &h->eigw,   &h->seg_fwd, &h->seg_bwd, &h->errw, &h->Qb, &h->G64,
+                    &h->mlpw, &h->mlp_part};
     for (DevBuf* b : bufs) ws += (int64_t)b->bytes;
     info->workspace_bytes = ws;
     info->eig_sweeps = hc.sweeps;

@@ -16,6 +16,7 @@ struct Control {
   double alpha;       // shift applied in the next product A^T A Q - alpha Q
   double alpha_prev;  // alpha' paired with S_prev in the stop test
   double ratio;       // last surrogate PVE ratio
+  double ratio_prev;  // the ratio of the pass before (learned-form feature)
   int32_t pass;       // power iterations done
   int32_t stop;       // 1 once the PVE test has passed
   int32_t status;     // kStatus* bit flags
@@ -54,6 +55,7 @@ struct EigArgs {
   double* trace;     // pass mode: trace buffer or nullptr
   unsigned long long cond;  // cudaGraphConditionalHandle (0: none)
   int use_cond;
+  const float* mlp;  // learned form: the shift/stop network's parameters (nullptr: plain rule)
 };
 
 // ---- launchers (all asynchronous on `st`) --------------------------------
@@ -132,6 +134,17 @@ cudaError_t launch_eig_refined(const float* G32, int64_t ldg32, const double* G6
 // Aishima); *X receives the refined basis (inside wk), wk.lam64 the eigenvalues.
 cudaError_t launch_refine_fp64(const double* G64, int64_t ldg, const float* V32, int l, int iters, const EigWork& wk,
                                const double** X, cudaStream_t st);
+
+// Learned form (mlp_common.cuh): batch features of trace records, forward
+// pass, loss gradient (CTA partials, `nparts` of kMlpParams + 1 floats), Adam.
+int mlp_grad_parts(int64_t B, int num_sms);
+cudaError_t launch_mlp_features(const double* rec, int64_t count, int l, int k, int pmax, double tol, float* X,
+                                cudaStream_t st);
+cudaError_t launch_mlp_forward(const float* W, const float* X, int64_t B, float* O, cudaStream_t st);
+cudaError_t launch_mlp_loss_grad(const float* W, const float* X, const float* T, const float* Mw, int64_t B,
+                                 float* part, int nparts, float* grad, float* loss, cudaStream_t st);
+cudaError_t launch_mlp_adam(float* W, const float* g, float* m, float* v, int step, float lr, float beta1,
+                            float beta2, float eps, cudaStream_t st);
 
 // Out = C W.
 cudaError_t launch_project(const float* C, int64_t rows, int l, int64_t ldc, const float* W,

@@ -27,6 +27,7 @@
 // step 5 with the surrogate Shat_i + alpha of Prop. 3, the shift update of
 // step 6, step 7's bookkeeping, and the loop flag (a CUDA graph conditional).
 #include "internal.cuh"
+#include "mlp_common.cuh"
 
 namespace dsvd {
 namespace {
@@ -263,6 +264,10 @@ struct FinishSmem {
   double S[kMaxL];  // by sorted position
   double red[32];
   int flag;
+  double ratio;          // this pass's surrogate ratio
+  float x[kMlpIn];       // learned form: features, hidden layer, outputs
+  float hid[kMlpHid];
+  float out[kMlpOut];
 };
 
 // The eigSVD conventions (Alg. 3 steps 2-4) and the dashSVD control (Alg. 5
@@ -366,6 +371,7 @@ __global__ void __launch_bounds__(kVecWarps * 32) finish_kernel(const T* __restr
       ctl->alpha = 0.0;
       ctl->alpha_prev = 0.0;
       ctl->ratio = 0.0;
+      ctl->ratio_prev = 0.0;
       ctl->pass = 0;
       ctl->stop = 0;
       ctl->status = (nonfinite ? kStatusNonFinite : 0) | hdr[1];
@@ -391,11 +397,43 @@ __global__ void __launch_bounds__(kVecWarps * 32) finish_kernel(const T* __restr
     const double floor_ = 64.0 * 2.220446049250313e-16 * (fs.S[0] + alpha);
     double denom = fs.S[k] + alpha;
     if (denom < floor_) denom = floor_;
-    const double ratio = denom > 0.0 ? m2 / denom : INFINITY;
+    fs.ratio = denom > 0.0 ? m2 / denom : INFINITY;
+    if (a.mlp) {
+      const int j = ctl->pass + 1;
+      mlp_features(fs.S, l, k, alpha, fs.ratio, j > 1 ? ctl->ratio_prev : fs.ratio, j, a.pmax, a.tol, fs.x);
+    }
+  }
+  __syncthreads();
+  if (a.mlp) {  // learned form: hidden layer by threads 0..63, outputs by thread 0
+    if (tid < kMlpHid) {
+      float z = a.mlp[kMlpB1 + tid];
+#pragma unroll
+      for (int i = 0; i < kMlpIn; ++i) z = fmaf(a.mlp[kMlpW1 + tid * kMlpIn + i], fs.x[i], z);
+      fs.hid[tid] = tanhf(z);
+    }
+    __syncthreads();
+    if (tid < kMlpOut) {
+      float o = a.mlp[kMlpB2 + tid];
+      for (int h = 0; h < kMlpHid; ++h) o = fmaf(a.mlp[kMlpW2 + tid * kMlpHid + h], fs.hid[h], o);
+      fs.out[tid] = o;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const double ratio = fs.ratio;
     const int j = ctl->pass + 1;
-    const int stop = (a.tol > 0.0 && ratio <= a.tol && !nonfinite) ? 1 : 0;
+    int stop = (a.tol > 0.0 && ratio <= a.tol && !nonfinite) ? 1 : 0;
+    double f = 1.0;  // fraction of the safe bound taken as the next shift
+    if (a.mlp) {
+      const float o0 = fs.out[0], o1 = fs.out[1];
+      if (isfinite(o0)) f = 1.0 / (1.0 + exp(-(double)o0));
+      if (!stop && a.tol > 0.0 && j >= 2 && ratio <= kMlpSoftTol * a.tol && o1 > 0.f && !nonfinite) stop = 1;
+    }
     double alpha_next = alpha;
-    if (!stop && a.shift && fs.S[l - 1] > alpha) alpha_next = 0.5 * (fs.S[l - 1] + alpha);
+    if (!stop && a.shift) {
+      const double bound = mlp_safe_bound(fs.S[l - 1], alpha);
+      alpha_next = fmin(fmax(f * bound, 0.0), bound);
+    }
     ctl->pass = j;
     ctl->ratio = ratio;
     ctl->stop = stop;
@@ -403,6 +441,7 @@ __global__ void __launch_bounds__(kVecWarps * 32) finish_kernel(const T* __restr
     if (!stop) {
       ctl->alpha = alpha_next;
       ctl->alpha_prev = a.alpha_prev_mode == 0 ? alpha : alpha_next;
+      ctl->ratio_prev = ratio;
     }
     ctl->cont = (!stop && !nonfinite && j < a.pmax) ? 1 : 0;
     if (a.trace) {

@@ -1,0 +1,214 @@
+"""Learned form on the GPU against the FP64 oracle (oracle/mlp_ref.py):
+features, forward pass, loss gradient and Adam through the C ABI, and learned
+dashSVD runs whose policy has a known effect (the plain rule, a fixed shift
+fraction, always-stop) against the oracle's runs with the same policy."""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+from oracle import mlp_ref as M
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ds():
+    import torch
+
+    assert torch.cuda.is_available()
+    import paper_2404_09276_gb300 as mod
+
+    return mod
+
+
+def _t(x, dtype=None):
+    import torch
+
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype or torch.float32, device="cuda")
+
+
+def _np(x):
+    return x.detach().cpu().numpy().astype(np.float64)
+
+
+def _const_net(o0, o1):
+    """Zero weights, output biases (o0, o1): a constant policy."""
+    return M.pack(np.zeros((64, 16)), np.zeros(64), np.zeros((2, 64)), np.array([o0, o1]))
+
+
+def _run(ds, A, k, s, p, tol, weights=None, **opts):
+    import torch
+
+    with ds.Handle(record_trace=1, learned=1 if weights is not None else 0, **opts) as h:
+        if weights is not None:
+            h.load_mlp(weights)
+        U, S, V, info = h.run(ds.CsrDevice.from_host(A), k, s, p, tol)
+        torch.cuda.synchronize()
+        tr = h.trace()
+    return _np(U), _np(S), _np(V), info, tr
+
+
+def test_features_match_oracle(ds):
+    import torch
+
+    A, prm = datagen.make_config(1, scale=0.1)
+    k, s = prm["k"], prm["s"]
+    l = k + s
+    _, _, _, info, tr = _run(ds, A, k, s, 8, 0.0)
+    rec = np.array([[j, a, r, an, sw, *Sh] for j, a, r, an, sw, Sh in tr])
+    with ds.Handle() as h:
+        X = _np(h.mlp_features(_t(rec, torch.float64), l, k, 8, 1e-2))
+    for i, r in enumerate(rec):
+        prev = rec[i - 1][2] if i > 0 else r[2]
+        x = M.features(r[5:], r[1], r[2], prev, int(r[0]), 8, 1e-2, k)
+        assert np.allclose(X[i], x.astype(np.float32), rtol=2e-7, atol=2e-7), (i, X[i] - x)
+
+
+def test_forward_matches_oracle(ds):
+    rng = np.random.default_rng(10)
+    w = rng.standard_normal(M.N_PARAMS) * 0.5
+    X = rng.uniform(-4, 4, size=(1000, 16))
+    with ds.Handle() as h:
+        O = _np(h.mlp_forward(_t(w), _t(X)))
+    _, Oref = M.forward(w.astype(np.float32).astype(np.float64), X.astype(np.float32).astype(np.float64))
+    # FP32: 16 + 64 term dot products of O(1) values, tanh to a few ulps
+    assert np.max(np.abs(O - Oref)) < 2e-5 * (1 + np.max(np.abs(Oref)))
+
+
+@pytest.mark.parametrize("B", [1, 37, 5000])
+def test_loss_grad_matches_oracle(ds, B):
+    rng = np.random.default_rng(11 + B)
+    w = (rng.standard_normal(M.N_PARAMS) * 0.5).astype(np.float32).astype(np.float64)
+    X = rng.uniform(-3, 3, size=(B, 16)).astype(np.float32).astype(np.float64)
+    T = np.c_[rng.uniform(0, 1, B), rng.integers(0, 2, B)].astype(np.float32).astype(np.float64)
+    Mw = np.c_[rng.uniform(0, 2, B), rng.uniform(0, 2, B)].astype(np.float32).astype(np.float64)
+    with ds.Handle() as h:
+        g, L = h.mlp_loss_grad(_t(w), _t(X), _t(T), _t(Mw))
+        g2, _ = h.mlp_loss_grad(_t(w), _t(X), _t(T), _t(Mw))
+    g, g2, L = _np(g), _np(g2), float(_np(L)[0])
+    Lref, gref = M.loss_and_grad(w, X, T, Mw)
+    assert np.array_equal(g, g2)  # deterministic
+    assert abs(L - Lref) <= 1e-5 * abs(Lref)
+    assert np.linalg.norm(g - gref) <= 1e-4 * np.linalg.norm(gref)
+
+
+def test_adam_matches_oracle(ds):
+    import torch
+
+    rng = np.random.default_rng(12)
+    w = rng.standard_normal(M.N_PARAMS).astype(np.float32)
+    m = np.zeros(M.N_PARAMS)
+    v = np.zeros(M.N_PARAMS)
+    W, Md, Vd = _t(w), torch.zeros(M.N_PARAMS, device="cuda"), torch.zeros(M.N_PARAMS, device="cuda")
+    wr = w.astype(np.float64)
+    with ds.Handle() as h:
+        for step in range(1, 6):
+            g = rng.standard_normal(M.N_PARAMS).astype(np.float32)
+            h.mlp_adam(W, _t(g), Md, Vd, step, 1e-2)
+            wr, m, v = M.adam(wr, g.astype(np.float64), m, v, step, 1e-2)
+    assert np.max(np.abs(_np(W) - wr)) < 1e-5
+
+
+def test_gpu_training_fits_a_teacher(ds):
+    """Full-batch training on the GPU (loss gradient + Adam kernels) lowers the
+    loss the way the FP64 oracle's own training does."""
+    import torch
+
+    rng = np.random.default_rng(13)
+    teacher = rng.standard_normal(M.N_PARAMS) * 0.8
+    X = rng.uniform(-2, 2, size=(512, 16))
+    _, O = M.forward(teacher, X)
+    T = np.c_[1 / (1 + np.exp(-O[:, 0])), (O[:, 1] > 0).astype(float)]
+    w0 = (rng.standard_normal(M.N_PARAMS) * 0.1).astype(np.float32)
+    W = _t(w0)
+    Md, Vd = torch.zeros_like(W), torch.zeros_like(W)
+    Xd, Td, Mk = _t(X), _t(T), _t(np.ones_like(T))
+    with ds.Handle() as h:
+        L0 = float(_np(h.mlp_loss_grad(W, Xd, Td, Mk)[1])[0])
+        for step in range(1, 801):
+            g, L = h.mlp_loss_grad(W, Xd, Td, Mk)
+            h.mlp_adam(W, g, Md, Vd, step, 3e-3)
+        L1 = float(_np(h.mlp_loss_grad(W, Xd, Td, Mk)[1])[0])
+    wr, m, v = w0.astype(np.float64), np.zeros(M.N_PARAMS), np.zeros(M.N_PARAMS)
+    for step in range(1, 801):
+        _, gr = M.loss_and_grad(wr, X, T, np.ones_like(T))
+        wr, m, v = M.adam(wr, gr, m, v, step, 3e-3)
+    Lr = M.loss_and_grad(wr, X, T, np.ones_like(T))[0]
+    assert L1 < 0.5 * L0
+    assert abs(L1 - Lr) <= 0.05 * Lr
+
+
+def test_load_mlp_validation(ds):
+    A, _ = datagen.make_config(1, scale=0.05)
+    with ds.Handle(learned=1) as h:
+        with pytest.raises(ds.DashSvdError) as e:
+            h.run(ds.CsrDevice.from_host(A), 8, 4, 2, 0.0)  # learned without a network
+        assert e.value.status == ds.DASHSVD_EINVAL
+        with pytest.raises(ds.DashSvdError):
+            h.load_mlp(np.zeros(100))
+        bad = np.zeros(M.N_PARAMS)
+        bad[5] = np.nan
+        with pytest.raises(ds.DashSvdError):
+            h.load_mlp(bad)
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_learned_f1_equals_plain_rule(ds, form):
+    """sigmoid(40) rounds to 1: the learned run takes the plain rule's shifts
+    and never stops early, so it follows the plain run. (Two runs agree to
+    rounding, not bit for bit: the device CSR transpose places the entries of
+    a row of A^T in atomic order, so A^T Y sums in a run-dependent order.)"""
+    A, prm = datagen.make_config(1, scale=0.1)
+    k, s = prm["k"], prm["s"]
+    U0, S0, V0, i0, t0 = _run(ds, A, k, s, 10, 1e-3, form=form)
+    U1, S1, V1, i1, t1 = _run(ds, A, k, s, 10, 1e-3, weights=_const_net(40.0, -40.0), form=form)
+    assert i1.passes == i0.passes
+    assert np.allclose([r[1] for r in t1], [r[1] for r in t0], rtol=1e-4, atol=0)
+    assert np.max(np.abs(S1 - S0) / S0) < 1e-4  # BF16x3 rounding level in the precision form
+
+
+def test_learned_fixed_fraction_matches_oracle(ds):
+    """A constant network with f = sigmoid(0) = 1/2 against the oracle's run
+    with the same policy (plain FP32 form: sigma to 1e-4)."""
+    A, prm = datagen.make_config(1, scale=0.1)
+    k, s = prm["k"], prm["s"]
+    w = _const_net(0.0, -40.0)
+    U, S, V, info, tr = _run(ds, A, k, s, 6, 0.0, weights=w)
+    ref = oracle.dashsvd(A.to_scipy(), k, s, p_max=6, tol=0.0, seed=0x5EED, policy=M.policy_fp32(w))
+    assert info.passes == ref.passes == 6
+    a_gpu = np.array([r[1] for r in tr])
+    a_ref = np.array([t.alpha_used for t in ref.trace])
+    assert np.allclose(a_gpu, a_ref, rtol=1e-4, atol=0)
+    assert np.max(np.abs(S - ref.S) / ref.S) < 1e-4
+
+
+def test_learned_stop_gate(ds):
+    """An always-stop network stops at the first pass j >= 2 whose surrogate
+    ratio is at most 3 tol (taken from the plain run's trace), and earlier than
+    the plain rule would."""
+    A, prm = datagen.make_config(1, scale=0.1)
+    k, s = prm["k"], prm["s"]
+    tol = 1e-3
+    _, _, _, i0, t0 = _run(ds, A, k, s, 12, 1e-14)
+    ratios = [r[2] for r in t0]
+    expect = next(j for j, r in enumerate(ratios, start=1) if j >= 2 and r <= 3 * tol)
+    _, _, _, i1, _ = _run(ds, A, k, s, 12, tol, weights=_const_net(40.0, 40.0))
+    assert i1.passes == expect
+    assert i1.status == ds.DASHSVD_OK
+
+
+def test_trained_network_gain(ds):
+    """What the committed network gains over the plain rule on held-out
+    matrices of the training family (seeds the training script never saw):
+    fewer passes on average, and no run over the tolerance where the plain
+    rule's run meets it."""
+    from paper_2404_09276_gb300 import learn
+
+    w, ship = learn.load_weights()
+    assert w is not None, "the trained weights file is missing"
+    rows = learn.compare(ds, [datagen.VAL_SEED0 + 1000 + i for i in range(12)], w)
+    s = learn.summarize(rows)
+    print("learned-form gain on 12 held-out matrices:", s)
+    assert s["failures"] == 0, s["fail_seeds"]
+    assert s["learned_passes"] <= s["plain_passes"]
