@@ -85,7 +85,10 @@ typedef struct {
                               run, the choice cached per matrix); else 0..5 = work split
                               (0 warp per row, 1 merge path) + 2 * configuration (0: two
                               nonzeros per team in flight, 1: four, 2: two with registers
-                              capped for four blocks per SM) */
+                              capped for four blocks per SM); 6, 7 = merge path with the
+                              gathered rows staged in shared memory by bulk copies (TMA)
+                              in per-warp rings of 16 / 8 rows (FP32 operands only, so
+                              not with gather_bf16) */
   int32_t record_trace;    /* 1: keep the per-pass Shat / shift history (get_trace) */
   int32_t shift;           /* 1: dynamic shifts (dashSVD); 0: alpha = 0 (Alg. 1 form) */
   int32_t gather_bf16;     /* precision form only: 1 stores the gathered operands Q and Y
@@ -215,8 +218,10 @@ int dashsvd_csr_transpose(dashsvd_handle h, const dashsvd_csr* A, int32_t* rowpt
 
 /* Y = A X (Alg. 5 step 4, inner product A Q; also B = A Q, step 9).
  * X: A.n x ldx, Y: A.m x ldy, both with ld % 4 == 0 and ld >= l; Y's columns
- * l .. ldy-1 are set to 0. variant: -1 (merge path, configuration 0) or 0..5
- * as in dashsvd_options.spmm_variant. */
+ * l .. ldy-1 are set to 0. variant: -1 (merge path, configuration 0) or 0..7
+ * as in dashsvd_options.spmm_variant. Variants 6 and 7 wait for their bulk
+ * copies with a bounded poll; this call then waits for its own work and
+ * returns DASHSVD_ETIMEOUT if a wait ran out. */
 int dashsvd_spmm(dashsvd_handle h, const dashsvd_csr* A, const float* X, int64_t ldx, int l,
                  float* Y, int64_t ldy, int variant);
 
@@ -231,7 +236,7 @@ int dashsvd_spmm_shift(dashsvd_handle h, const dashsvd_csr* At, const float* Y, 
 /* Precision-form sparse products with a BF16 dense operand (row-major, ld
  * in elements, ld % 4 == 0): Y = A X with Y in BF16 (y_bf16 = 1) or FP32, or
  * Y = A X - alpha Q with a BF16 Q (alpha a DEVICE pointer to a double, or
- * NULL). FP32 accumulation; shapes and variants as in dashsvd_spmm. */
+ * NULL). FP32 accumulation; shapes as in dashsvd_spmm, variants 0..5. */
 int dashsvd_spmm_bf16(dashsvd_handle h, const dashsvd_csr* A, const void* X, int64_t ldx, int l, void* Y,
                       int y_bf16, int64_t ldy, const double* alpha, const void* Q, int64_t ldq, int variant);
 

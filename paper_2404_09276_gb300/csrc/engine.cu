@@ -213,7 +213,7 @@ cudaError_t launch_prologue(dashsvd_handle h, const RunPlan& p, unsigned long lo
   if ((e = launch_gaussian(h->opt.seed, p.mw, p.l, 0, as<float>(h->Y), p.ld, st)) != cudaSuccess) return e;
   // step 2: Z = A^T Omega, Q = eigSVD(Z)
   if ((e = launch_spmm(p.AwT, p.part_bwd, as<float>(h->Y), p.ld, p.l, as<float>(h->Z), p.ld, nullptr, nullptr, 0,
-                       p.var_bwd32, p.scr, h->num_sms, st)) != cudaSuccess)
+                       p.var_bwd32, p.scr, h->num_sms, st, as<int>(h->errw))) != cudaSuccess)
     return e;
   if ((e = eigsvd_step(h, p, as<float>(h->Z), p.nw, kModeInit, cond, st)) != cudaSuccess) return e;
   return project_basis(h, p, st);
@@ -232,10 +232,10 @@ cudaError_t launch_pass(dashsvd_handle h, const RunPlan& p, unsigned long long c
       return e;
   } else {
     if ((e = launch_spmm(p.Aw, p.part_fwd, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld, nullptr, nullptr, 0,
-                         p.var_fwd, p.scr, h->num_sms, st)) != cudaSuccess)
+                         p.var_fwd, p.scr, h->num_sms, st, as<int>(h->errw))) != cudaSuccess)
       return e;
     if ((e = launch_spmm(p.AwT, p.part_bwd, as<float>(h->Y), p.ld, p.l, as<float>(h->Z), p.ld, &ctl->alpha,
-                         as<float>(h->Q), p.ld, p.var_bwd, p.scr, h->num_sms, st)) != cudaSuccess)
+                         as<float>(h->Q), p.ld, p.var_bwd, p.scr, h->num_sms, st, as<int>(h->errw))) != cudaSuccess)
       return e;
   }
   // steps 5-7 run inside the eig kernels' control tail
@@ -247,7 +247,7 @@ cudaError_t launch_final(dashsvd_handle h, const RunPlan& p, cudaStream_t st) {
   cudaError_t e;
   // step 9: B = A Q (into Y), from the FP32 basis in both forms
   if ((e = launch_spmm(p.Aw, p.part_fwd, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld, nullptr, nullptr, 0,
-                       p.var_fwd32, p.scr, h->num_sms, st)) != cudaSuccess)
+                       p.var_fwd32, p.scr, h->num_sms, st, as<int>(h->errw))) != cudaSuccess)
     return e;
   // steps 10-11: eigSVD(B); U = B V_k S_k^-1; V = Q V_k
   if ((e = eigsvd_step(h, p, as<float>(h->Y), p.mw, kModeFinal, 0, st)) != cudaSuccess) return e;
@@ -317,7 +317,9 @@ int build_graph(dashsvd_handle h, const RunPlan& p) {
   return DASHSVD_OK;
 }
 
-constexpr int kSpmmVariants = 6;  // split (warp per row, merge path) x 3 configurations
+constexpr int kSpmmVariants = 8;  // 0-5: split (warp per row, merge path) x 3 configurations;
+                                  // 6, 7: merge path with bulk-copy (TMA) staging (FP32 operands)
+constexpr int kSpmmVariantsBf16 = 6;
 
 // Time every SpMM variant once on this matrix (after one warm-up launch each)
 // for both products of a pass, with FP32 operands and, in the precision form,
@@ -345,7 +347,7 @@ int autotune_spmm(dashsvd_handle h, RunPlan& p, const dashsvd_csr& A) {
   int arg[4] = {1, 1, 1, 1};
   cudaError_t err = cudaSuccess;
   for (int prod = 0; prod < nprod && err == cudaSuccess; ++prod) {
-    for (int v = 0; v < kSpmmVariants && err == cudaSuccess; ++v) {
+    for (int v = 0; v < (prod < 2 ? kSpmmVariants : kSpmmVariantsBf16) && err == cudaSuccess; ++v) {
       float ms = 0.f;
       for (int rep = 0; rep < 2 && err == cudaSuccess; ++rep) {
         if (rep == 1) err = cudaEventRecord(e0, st);
@@ -353,11 +355,11 @@ int autotune_spmm(dashsvd_handle h, RunPlan& p, const dashsvd_csr& A) {
         switch (prod) {
           case 0:  // FP32 A Q
             err = launch_spmm(p.Aw, p.part_fwd, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld, nullptr, nullptr,
-                              0, v, p.scr, h->num_sms, st);
+                              0, v, p.scr, h->num_sms, st, as<int>(h->errw));
             break;
           case 1:  // FP32 A^T Y - alpha Q
             err = launch_spmm(p.AwT, p.part_bwd, as<float>(h->Y), p.ld, p.l, as<float>(h->Z), p.ld, &ctl->alpha,
-                              as<float>(h->Q), p.ld, v, p.scr, h->num_sms, st);
+                              as<float>(h->Q), p.ld, v, p.scr, h->num_sms, st, as<int>(h->errw));
             break;
           case 2:  // BF16 A Q -> BF16
             err = launch_spmm_bf16(p.Aw, p.part_fwd, h->Qb.p, p.ld, p.l, h->Y.p, true, p.ld, nullptr, nullptr, 0, v,
@@ -452,6 +454,7 @@ int dashsvd_create(dashsvd_handle* out, const dashsvd_options* opt, void* cuda_s
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = prepare_project();
   if (e == cudaSuccess) e = prepare_eig();
+  if (e == cudaSuccess) e = prepare_spmm();
   if (e == cudaSuccess) e = prepare_gram_tc();
   if (e == cudaSuccess) e = prepare_project_tc();
   if (e != cudaSuccess) {
@@ -549,6 +552,7 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
   const int64_t mn = A->m < A->n ? A->m : A->n;
   if (l > mn || l > DASHSVD_MAX_L) return DASHSVD_EINVAL;
   if (h->opt.gather_bf16 && !precision(h)) return DASHSVD_EINVAL;
+  if (h->opt.gather_bf16 && h->opt.spmm_variant >= kSpmmVariantsBf16) return DASHSVD_EINVAL;
   if (h->opt.learned && !h->mlp_loaded) return DASHSVD_EINVAL;
   if ((h->opt.form != DASHSVD_FORM_PLAIN && h->opt.form != DASHSVD_FORM_PRECISION) || h->opt.learned < 0 ||
       h->opt.learned > 1)
@@ -740,8 +744,16 @@ static int spmm_common(dashsvd_handle h, const dashsvd_csr* A, const float* X, i
   part.seg_row = as<int32_t>(h->seg_fwd);
   part.seg_nnz = part.seg_row + part.segments + 1;
   const int var = variant < 0 ? 1 : variant;
-  if (var & 1) DS_CUDA(launch_spmm_partition(*A, part, h->stream));
-  DS_CUDA(launch_spmm(*A, part, X, ldx, l, Y, ldy, alpha, Q, ldq, var, scr, h->num_sms, h->stream));
+  if ((rc = ensure(h->errw, 16, &moved))) return rc;
+  if (var >= 6) DS_CUDA(cudaMemsetAsync(h->errw.p, 0, sizeof(int), h->stream));
+  if ((var & 1) || var >= 6) DS_CUDA(launch_spmm_partition(*A, part, h->stream));
+  DS_CUDA(launch_spmm(*A, part, X, ldx, l, Y, ldy, alpha, Q, ldq, var, scr, h->num_sms, h->stream, as<int>(h->errw)));
+  if (var >= 6) {  // the bulk-copy variants wait on barriers with a bound: report a timeout
+    int werr = 0;
+    DS_CUDA(cudaMemcpyAsync(&werr, h->errw.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    DS_CUDA(cudaStreamSynchronize(h->stream));
+    if (werr) return DASHSVD_ETIMEOUT;
+  }
   return DASHSVD_OK;
 }
 
@@ -761,7 +773,7 @@ int dashsvd_spmm_bf16(dashsvd_handle h, const dashsvd_csr* A, const void* X, int
   if (ldx < l || ldy < l || ldx % 4 || ldy % 4 || ((uintptr_t)X & 7u) || ((uintptr_t)Y & (y_bf16 ? 7u : 15u)))
     return DASHSVD_EINVAL;
   if (alpha && (!Q || ldq < l || ldq % 4 || ((uintptr_t)Q & 7u))) return DASHSVD_EINVAL;
-  if (variant < -1 || variant >= kSpmmVariants) return DASHSVD_EINVAL;
+  if (variant < -1 || variant >= kSpmmVariantsBf16) return DASHSVD_EINVAL;
   SpmmPart part;
   part.segments = spmm_segments(*A, h->num_sms);
   const int64_t ldc = ((l + 3) / 4) * 4;

@@ -85,7 +85,7 @@ int64_t spmm_segments(const dashsvd_csr& A, int num_sms);
 cudaError_t launch_spmm_partition(const dashsvd_csr& A, SpmmPart& part, cudaStream_t st);
 cudaError_t launch_spmm(const dashsvd_csr& A, const SpmmPart& part, const float* X, int64_t ldx, int l, float* Y,
                         int64_t ldy, const double* alpha, const float* Q, int64_t ldq, int variant,
-                        const SpmmScratch& scr, int num_sms, cudaStream_t st);
+                        const SpmmScratch& scr, int num_sms, cudaStream_t st, int* err = nullptr);
 // BF16 dense operand (and BF16 Q): Y in BF16 (y_bf16) or FP32
 cudaError_t launch_spmm_bf16(const dashsvd_csr& A, const SpmmPart& part, const void* X, int64_t ldx, int l, void* Y,
                              bool y_bf16, int64_t ldy, const double* alpha, const void* Q, int64_t ldq, int variant,
@@ -155,6 +155,7 @@ cudaError_t launch_project(const float* C, int64_t rows, int l, int64_t ldc, con
 // before any launch is captured into a graph.
 cudaError_t prepare_project();
 cudaError_t prepare_eig();
+cudaError_t prepare_spmm();
 
 // ---- error plumbing --------------------------------------------------------
 void set_last_error(const char* what, cudaError_t e, const char* file, int line);

@@ -4,6 +4,9 @@
 #include <cuda_bf16.h>
 
 #include "internal.cuh"
+#include "tc_common.cuh"
+
+#include <type_traits>
 
 namespace dsvd {
 namespace spmm_detail {
@@ -308,12 +311,18 @@ __global__ void __launch_bounds__(kThreads, MINB) spmm_merge_kernel(const int32_
 }
 
 // One warp per carry slot; the first slot of each split row sums all of the
-// row's pieces in segment order and writes the row with the epilogue.
+// row's pieces in segment order and writes the row with the epilogue. The
+// pieces are found 32 slots at a time (one coalesced read of carry_row and a
+// ballot), and up to 8 of them are loaded before they are added, in slot
+// order, so long chains (hot rows split over thousands of segments) cost a few
+// loads' latency per 8 pieces rather than per piece. Lanes own float4 column
+// slots `lane` and `lane + 32`.
 template <typename TOut, typename TQ>
 __global__ void __launch_bounds__(kThreads) spmm_fixup_kernel(const float* __restrict__ carry,
                                                               const int32_t* __restrict__ carry_row, int64_t slots,
                                                               int ldc, TOut* __restrict__ Y, int64_t ldy,
                                                               Epilogue<TQ> ep) {
+  constexpr int kBatch = 8;
   const int lane = threadIdx.x & 31;
   const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   if (s >= slots) return;
@@ -322,21 +331,221 @@ __global__ void __launch_bounds__(kThreads) spmm_fixup_kernel(const float* __res
   int64_t t = s - 1;
   while (t >= 0 && carry_row[t] < 0) --t;
   if (t >= 0 && carry_row[t] == row) return;  // not the first piece
-  const float alpha = ep.alpha ? (float)*ep.alpha : 0.f;
   const int ldy4 = (int)(ldy >> 2), ldc4 = ldc >> 2;
-  TOut* y = Y + (int64_t)row * ldy;
-  for (int slot = lane; slot < ldy4; slot += 32) {
-    float4 acc = f4_zero();
-    if (slot < ldc4) {
-      for (int64_t u = s; u < slots; ++u) {
-        const int32_t ru = carry_row[u];
-        if (ru < 0) continue;
-        if (ru != row) break;
-        acc = f4_add(acc, reinterpret_cast<const float4*>(carry + u * (int64_t)ldc)[slot]);
+  const bool in0 = lane < ldc4, in1 = lane + 32 < ldc4;
+  float4 acc0 = f4_zero(), acc1 = f4_zero();
+  for (int64_t base = s;; base += 32) {
+    const int64_t u = base + lane;
+    const int32_t v = u < slots ? carry_row[u] : -2;  // -2: past the last slot
+    unsigned mine = __ballot_sync(kFull, v == row);
+    const unsigned other = __ballot_sync(kFull, v != row && v != -1);
+    if (other) mine &= (1u << (__ffs(other) - 1)) - 1u;  // pieces before the chain ends
+    while (mine) {
+      int idx[kBatch];
+      int n = 0;
+#pragma unroll
+      for (int b = 0; b < kBatch; ++b) {
+        idx[b] = mine ? __ffs(mine) - 1 : -1;
+        if (mine) {
+          mine &= mine - 1;
+          ++n;
+        }
+      }
+      float4 x0[kBatch], x1[kBatch];
+#pragma unroll
+      for (int b = 0; b < kBatch; ++b) {
+        const float4* c = reinterpret_cast<const float4*>(carry + (base + (idx[b] < 0 ? 0 : idx[b])) * (int64_t)ldc);
+        x0[b] = (b < n && in0) ? c[lane] : f4_zero();
+        x1[b] = (b < n && in1) ? c[lane + 32] : f4_zero();
+      }
+#pragma unroll
+      for (int b = 0; b < kBatch; ++b) {
+        if (b < n) {
+          acc0 = f4_add(acc0, x0[b]);
+          acc1 = f4_add(acc1, x1[b]);
+        }
       }
     }
-    store4(y, slot, apply_epilogue(acc, slot, row, ep, alpha));
+    if (other) break;
   }
+  const float alpha = ep.alpha ? (float)*ep.alpha : 0.f;
+  TOut* y = Y + (int64_t)row * ldy;
+  for (int slot = lane; slot < ldy4; slot += 32) {
+    const float4 v = slot < 32 ? acc0 : (slot < 64 ? acc1 : f4_zero());
+    store4(y, slot, apply_epilogue(slot < ldc4 ? v : f4_zero(), slot, row, ep, alpha));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Merge-path product with the gathered rows staged by bulk copies (TMA).
+// Each warp keeps a ring of R row buffers in shared memory, one mbarrier per
+// buffer: lane 0 (R lanes at a segment start) issues cp.async.bulk copies of
+// the rows of X that the next R nonzeros of its segment gather, and the warp
+// consumes one nonzero at a time from shared memory, lanes across columns
+// (lane t owns float4 slots t and t + 32), so no cross-lane reduction is
+// needed at row ends. The bytes in flight per SM are set by the ring size,
+// not by registers. Rows that cross segment boundaries go through the same
+// carry slots and fix-up kernel as the register variant.
+constexpr int kTmaWarps = 8;
+constexpr uint32_t kTmaWaitLimit = 1u << 20;
+
+template <int R>
+size_t tma_smem_bytes(int nslot) {
+  return (size_t)kTmaWarps * R * (sizeof(uint64_t) + (size_t)nslot * 16);
+}
+
+template <int R, typename TOut, typename TQ>
+__global__ void __launch_bounds__(kTmaWarps * 32) spmm_tma_kernel(const int32_t* __restrict__ rowptr,
+                                                                  const int32_t* __restrict__ col,
+                                                                  const float* __restrict__ val, int64_t m,
+                                                                  const float* __restrict__ X, int64_t ldx,
+                                                                  TOut* __restrict__ Y, int64_t ldy, int nslot,
+                                                                  Epilogue<TQ> ep, SpmmPart part,
+                                                                  float* __restrict__ carry,
+                                                                  int32_t* __restrict__ carry_row, int ldc,
+                                                                  int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char tsm[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t rowbytes = (uint32_t)nslot * 16;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tsm) + warp * R;
+  unsigned char* ring = tsm + (size_t)kTmaWarps * R * sizeof(uint64_t) + (size_t)warp * R * rowbytes;
+  if (lane < R) tc::mbar_init(&bars[lane], 1);
+  tc::fence_mbar_init();
+  __syncwarp();
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const float alpha = ep.alpha ? (float)*ep.alpha : 0.f;
+  const int ldy4 = (int)(ldy >> 2), ldc4 = ldc >> 2;
+  const bool two = lane + 32 < nslot;  // this lane owns a second float4 slot
+  uint32_t cnt = 0;                    // nonzeros consumed by this warp so far (ring position)
+  uint32_t issued = 0;                 // bulk copies issued by this warp so far
+  bool ok = true;
+  for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < part.segments && ok; w += warps) {
+    const int64_t r0 = part.seg_row[w], k0 = part.seg_nnz[w];
+    const int64_t r1 = part.seg_row[w + 1], k1 = part.seg_nnz[w + 1];
+    const bool split_head = r0 < m && (int64_t)rowptr[r0] < k0;
+    int32_t head_row = -1, tail_row = -1;
+    // (col, val) of nonzeros [wb, wb + 32) and [wb + 32, wb + 64) across the lanes
+    int64_t wb = k0;
+    int c0, c1;
+    float a0, a1;
+    load_pairs(col, val, wb, k1, lane, c0, a0);
+    load_pairs(col, val, wb + 32, k1, lane, c1, a1);
+    // prologue: the first R nonzeros of the segment, one bulk copy per lane
+    if (lane < R && k0 + lane < k1) {
+      const uint32_t slot = (cnt + lane) % R;
+      tc::mbar_arrive_expect_tx(&bars[slot], rowbytes);
+      tc::bulk_g2s(ring + slot * rowbytes, X + (int64_t)c0 * ldx, rowbytes, &bars[slot]);
+    }
+    issued += (uint32_t)(k1 - k0 < R ? k1 - k0 : R);
+    int64_t rw = r0;
+    int rp = rowptr[(rw + 1 + lane) < m ? (rw + 1 + lane) : m];
+    float4 acc0 = f4_zero(), acc1 = f4_zero();
+    int64_t r = r0, pos = k0;
+    while (r < r1 || (r == r1 && r1 < m && pos < k1)) {
+      int64_t e;
+      if (r < r1) {
+        if (r - rw >= 32) {
+          rw = r;
+          rp = rowptr[(rw + 1 + lane) < m ? (rw + 1 + lane) : m];
+        }
+        e = __shfl_sync(kFull, rp, (int)(r - rw));
+      } else {
+        e = k1;
+      }
+      for (; pos < e; ++pos, ++cnt) {
+        if (pos - wb >= 32) {  // slide the (col, val) windows
+          wb += 32;
+          c0 = c1;
+          a0 = a1;
+          load_pairs(col, val, wb + 32, k1, lane, c1, a1);
+        }
+        const float a = __shfl_sync(kFull, a0, (int)(pos - wb));
+        const int64_t nxt = pos + R;  // the nonzero whose row refills this buffer
+        const int cn = __shfl_sync(kFull, nxt - wb < 32 ? c0 : c1, (int)((nxt - wb) & 31));
+        const uint32_t slot = cnt % R;
+        if (!tc::mbar_wait(&bars[slot], (cnt / R) & 1u, kTmaWaitLimit)) {
+          ok = false;
+          break;
+        }
+        const float4* row = reinterpret_cast<const float4*>(ring + slot * rowbytes);
+        acc0 = f4_fma(a, row[lane < nslot ? lane : 0], acc0);
+        if (two) acc1 = f4_fma(a, row[lane + 32], acc1);
+        __syncwarp();  // every lane has read the buffer before it is refilled
+        if (nxt < k1) {
+          if (lane == 0) {
+            tc::mbar_arrive_expect_tx(&bars[slot], rowbytes);
+            tc::bulk_g2s(ring + slot * rowbytes, X + (int64_t)cn * ldx, rowbytes, &bars[slot]);
+          }
+          ++issued;
+        }
+      }
+      if (!ok) break;
+      // the row (or this segment's piece of it) is complete
+      float* cslot = nullptr;
+      if (r == r1) {  // leading or middle piece of a row that ends later
+        const int64_t sl = r0 == r1 ? 2 * w : 2 * w + 1;
+        cslot = carry + sl * (int64_t)ldc;
+        if (r0 == r1)
+          head_row = (int32_t)r1;
+        else
+          tail_row = (int32_t)r1;
+      } else if (r == r0 && split_head) {  // finishing piece of a split row
+        cslot = carry + (2 * w) * (int64_t)ldc;
+        head_row = (int32_t)r;
+      }
+      if (cslot) {
+        if (lane < ldc4) reinterpret_cast<float4*>(cslot)[lane] = lane < nslot ? acc0 : f4_zero();
+        if (lane + 32 < ldc4) reinterpret_cast<float4*>(cslot)[lane + 32] = two ? acc1 : f4_zero();
+      } else {
+        TOut* y = Y + r * ldy;
+        for (int sl = lane; sl < ldy4; sl += 32) {
+          const float4 v = sl < 32 ? acc0 : (sl < 64 ? acc1 : f4_zero());
+          store4(y, sl, apply_epilogue(sl < nslot ? v : f4_zero(), sl, r, ep, alpha));
+        }
+      }
+      acc0 = f4_zero();
+      acc1 = f4_zero();
+      ++r;
+    }
+    if (lane == 0) {
+      carry_row[2 * w] = head_row;
+      carry_row[2 * w + 1] = tail_row;
+    }
+  }
+  if (!ok) {
+    // a buffer never arrived: report, and let every copy still in flight land
+    // (bounded) before the CTA's shared memory is released
+    if (lane == 0) {
+      atomicExch(err, 1);
+      for (uint32_t c = cnt; c < issued; ++c) tc::mbar_wait(&bars[c % R], (c / R) & 1u, kTmaWaitLimit);
+    }
+    __syncwarp();
+  }
+}
+
+template <int R, typename TOut, typename TQ>
+cudaError_t prepare_tma() {
+  return cudaFuncSetAttribute(spmm_tma_kernel<R, TOut, TQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)tma_smem_bytes<R>(64));
+}
+
+template <int R, typename TOut, typename TQ>
+cudaError_t launch_tma(const dashsvd_csr& A, const SpmmPart& part, const float* X, int64_t ldx, int l, TOut* Y,
+                       int64_t ldy, const Epilogue<TQ>& ep, const SpmmScratch& scr, int* err, int num_sms,
+                       cudaStream_t st) {
+  const int nslot = (l + 3) / 4;
+  if (A.m <= 0) return cudaSuccess;
+  if (part.segments > scr.max_segments || scr.ldc < nslot * 4 || nslot > 64 || !err) return cudaErrorInvalidValue;
+  const size_t smem = tma_smem_bytes<R>(nslot);  // opt-in above 48 KB: prepare_tma<R, TOut, TQ>()
+  const int64_t need = ds_ceil_div(part.segments * 32, kTmaWarps * 32);
+  const int64_t grid = (int64_t)num_sms * 4;
+  spmm_tma_kernel<R, TOut, TQ><<<(unsigned)(need < grid ? need : grid), kTmaWarps * 32, smem, st>>>(
+      A.rowptr, A.colidx, A.val, A.m, X, ldx, Y, ldy, nslot, ep, part, scr.carry, scr.carry_row, scr.ldc, err);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  spmm_fixup_kernel<TOut, TQ><<<(unsigned)ds_ceil_div(2 * part.segments * 32, kThreads), kThreads, 0, st>>>(
+      scr.carry, scr.carry_row, 2 * part.segments, scr.ldc, Y, ldy, ep);
+  return cudaGetLastError();
 }
 
 template <int V, int U, int MINB, typename TIn, typename TOut, typename TQ>
@@ -366,7 +575,9 @@ cudaError_t launch_vc(const dashsvd_csr& A, const SpmmPart& part, const TIn* X, 
 
 // variant = split (0 warp per row, 1 merge path) + 2 * configuration, where
 // configuration 0: two entries per team per round; 1: four entries per round;
-// 2: two entries per round with registers capped for four blocks per SM
+// 2: two entries per round with registers capped for four blocks per SM;
+// variants 6 and 7 (FP32 operands): merge path with the gathered rows staged
+// by bulk copies in per-warp rings of 16 and 8 rows
 template <int V, typename TIn, typename TOut, typename TQ>
 cudaError_t launch_v(const dashsvd_csr& A, const SpmmPart& part, const TIn* X, int64_t ldx, int l, TOut* Y,
                      int64_t ldy, const Epilogue<TQ>& ep, int variant, const SpmmScratch& scr, int num_sms,
@@ -383,8 +594,16 @@ cudaError_t launch_v(const dashsvd_csr& A, const SpmmPart& part, const TIn* X, i
 template <typename TIn, typename TOut, typename TQ>
 cudaError_t dispatch(const dashsvd_csr& A, const SpmmPart& part, const TIn* X, int64_t ldx, int l, TOut* Y,
                      int64_t ldy, const double* alpha, const TQ* Q, int64_t ldq, int variant, const SpmmScratch& scr,
-                     int num_sms, cudaStream_t st) {
+                     int num_sms, cudaStream_t st, int* err = nullptr) {
   Epilogue<TQ> ep{alpha, Q, ldq, l};
+  if (variant == 6 || variant == 7) {
+    if constexpr (std::is_same<TIn, float>::value) {
+      return variant == 6 ? launch_tma<16, TOut, TQ>(A, part, X, ldx, l, Y, ldy, ep, scr, err, num_sms, st)
+                          : launch_tma<8, TOut, TQ>(A, part, X, ldx, l, Y, ldy, ep, scr, err, num_sms, st);
+    } else {
+      return cudaErrorInvalidValue;
+    }
+  }
   const int V = ((l + 3) / 4 + 7) / 8;
   switch (V) {
     case 1: return launch_v<1>(A, part, X, ldx, l, Y, ldy, ep, variant, scr, num_sms, st);

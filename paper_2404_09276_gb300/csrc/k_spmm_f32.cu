@@ -21,6 +21,10 @@
 //              of split rows go to per-segment carry slots that a fix-up
 //              kernel adds in segment order, so the result does not depend on
 //              scheduling.
+//   variants 6, 7  merge path with the gathered rows of X staged in shared
+//              memory by bulk copies (TMA), in a per-warp ring of 16 or 8 rows
+//              (see spmm_tma_kernel): the bytes in flight no longer depend on
+//              how many registers hold loads.
 #include "k_spmm.cuh"
 
 namespace dsvd {
@@ -47,8 +51,14 @@ cudaError_t launch_spmm_partition(const dashsvd_csr& A, SpmmPart& part, cudaStre
 
 cudaError_t launch_spmm(const dashsvd_csr& A, const SpmmPart& part, const float* X, int64_t ldx, int l, float* Y,
                         int64_t ldy, const double* alpha, const float* Q, int64_t ldq, int variant,
-                        const SpmmScratch& scr, int num_sms, cudaStream_t st) {
-  return dispatch<float, float, float>(A, part, X, ldx, l, Y, ldy, alpha, Q, ldq, variant, scr, num_sms, st);
+                        const SpmmScratch& scr, int num_sms, cudaStream_t st, int* err) {
+  return dispatch<float, float, float>(A, part, X, ldx, l, Y, ldy, alpha, Q, ldq, variant, scr, num_sms, st, err);
+}
+
+cudaError_t prepare_spmm() {
+  cudaError_t e = prepare_tma<16, float, float>();
+  if (e == cudaSuccess) e = prepare_tma<8, float, float>();
+  return e;
 }
 
 }  // namespace dsvd

@@ -114,7 +114,7 @@ def _spmm_check(A, X, Y, l):
 
 @pytest.mark.parametrize("name", list(MATRICES))
 @pytest.mark.parametrize("l", [1, 7, 30, 150, 160, 220])
-@pytest.mark.parametrize("variant", range(6))
+@pytest.mark.parametrize("variant", range(8))
 def test_spmm_matches_fp64(ds, h, name, l, variant):
     A = MATRICES[name]()
     rng = np.random.default_rng(l)
@@ -127,7 +127,7 @@ def test_spmm_matches_fp64(ds, h, name, l, variant):
 
 
 @pytest.mark.parametrize("name", ["social", "mixed"])
-@pytest.mark.parametrize("variant", range(6))
+@pytest.mark.parametrize("variant", range(8))
 def test_spmm_shift_matches_fp64(ds, h, name, variant):
     import torch
 
@@ -193,6 +193,10 @@ def test_spmm_merge_path_matches_warp_per_row_closely(ds, h):
     y1b = _np(h.spmm(Ad, _t(X), l, variant=1))
     np.testing.assert_array_equal(y1, y1b)  # merge path is deterministic
     np.testing.assert_allclose(y0, y1, rtol=1e-4, atol=1e-4)
+    for v in (6, 7):  # bulk-copy staging: same segments, one nonzero at a time
+        y6 = _np(h.spmm(Ad, _t(X), l, variant=v))
+        np.testing.assert_array_equal(y6, _np(h.spmm(Ad, _t(X), l, variant=v)))
+        np.testing.assert_allclose(y6, y1, rtol=1e-4, atol=1e-4)
 
 
 @pytest.mark.parametrize("rows,l", [(1, 1), (100, 30), (5000, 7), (20011, 150), (3000, 160), (70000, 64),
