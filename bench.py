@@ -227,7 +227,7 @@ FORMS = {
 
 def _launches_per_run(form, passes, var_fwd, var_bwd):
     kpv = lambda v: 2 if (v & 1) else 1  # noqa: E731  kernels per SpMM launch (merge path adds its fix-up)
-    eig = 3 if form == "plain" else 3 + 1 + 2 * 5  # Jacobi, replay, finish (+ FP64 refinement)
+    eig = 3 if form == "plain" else 3 + 1 + 2 * 6  # Jacobi, replay, finish (+ FP64 refinement)
     # (the BF16-gather form tunes BF16 variants for the loop; its prologue and final product stay FP32)
     setup = 5 + 2  # CSR transpose, merge-path partitions
     prologue = 1 + kpv(var_bwd) + 2 + eig + 1

@@ -116,6 +116,7 @@ cudaError_t launch_project_tc(const float* C, int64_t rows, int l, int64_t ldc, 
 constexpr int kMaxSweeps = 30;
 struct EigWork {
   int* hdr;       // [0] sweeps to replay, [1] status bits, [2] sweeps run
+  double* scal;   // FP64 scalars of the refinement (header bytes 128..255)
   float* d;       // kMaxL eigenvalues (unsorted, FP32 Jacobi)
   float* d0;      // kMaxL diagonal entries of G before the iteration
   float* V32;     // l x l eigenvectors (column c = eigenvector c), row-major

@@ -480,6 +480,7 @@ EigWork eig_work_view(void* base) {
   EigWork w;
   char* p = reinterpret_cast<char*>(base);
   w.hdr = reinterpret_cast<int*>(p);
+  w.scal = reinterpret_cast<double*>(p + 128);
   p += 256;
   w.X64 = reinterpret_cast<double*>(p);  // 6 l x l FP64 matrices: X, X', P, S, T, E
   p += 6 * sizeof(double) * L * L;

@@ -27,6 +27,7 @@ constexpr int kThreadsTC = (kConvWarps + 2) * 32;
 constexpr int kOpRows = 256;
 constexpr int kOpBytes = kOpRows * kKB * 2;  // one hi or lo tile: 32 KB
 constexpr int kSmemTC = kStages * 2 * kOpBytes + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int kMaxItems = kOpRows * 8 / (kConvWarps * 32);  // items per converter thread and block (l <= 256)
 
 __global__ void __launch_bounds__(kThreadsTC, 1)
     gram_tc_kernel(const float* __restrict__ C, int64_t rows, int l, int64_t ldc, int Lc, int64_t chunk_rows,
@@ -66,42 +67,62 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   bool ok = true;
 
   if (warp < kConvWarps) {
-    // ---- converters: C block -> hi/lo K-major swizzled tiles
+    // ---- converters: C block -> hi/lo K-major swizzled tiles. A thread's items
+    // of block it + 1 are loaded into registers before block it is converted,
+    // so the global-load latency overlaps the conversion and the MMA wait.
     const int L32 = (l + 31) & ~31;
+    const int nitems = L32 * 8;  // (8-row group kc, column m) pairs per block
+    float cur[kMaxItems][8], nxt[kMaxItems][8];
+    auto load = [&](int it, float (&v)[kMaxItems][8]) {
+      const int64_t r0 = k0 + (int64_t)it * kKB;
+#pragma unroll
+      for (int i = 0; i < kMaxItems; ++i) {
+        const int item = warp * 32 + lane + i * kConvWarps * 32;
+        const int kc = item / L32, m = item - kc * L32;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int64_t r = r0 + 8 * kc + j;
+          v[i][j] = (item < nitems && r < k1 && m < l) ? __ldg(C + r * ldc + m) : 0.f;
+        }
+      }
+    };
+    if (nblk > 0) load(0, cur);
     for (int it = 0; it < nblk && ok; ++it) {
       const int s = it % kStages;
       const uint32_t ph = (uint32_t)(it / kStages) & 1u;
+      if (it + 1 < nblk) load(it + 1, nxt);
       if (!tc::mbar_wait(&empty[s], ph ^ 1u)) {
         ok = false;
         break;
       }
       uint8_t* hi = sm + (size_t)s * 2 * kOpBytes;
       uint8_t* lo = hi + kOpBytes;
-      const int64_t r0 = k0 + (int64_t)it * kKB;
-      for (int item = warp * 32 + lane; item < L32 * 8; item += kConvWarps * 32) {
-        const int kc = item / L32, m = item - kc * L32;
-        float v[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int64_t r = r0 + 8 * kc + j;
-          v[j] = (r < k1 && m < l) ? __ldg(C + r * ldc + m) : 0.f;
-        }
-        uint32_t ph4[4], pl4[4];
+      for (int i = 0; i < kMaxItems; ++i) {
+        const int item = warp * 32 + lane + i * kConvWarps * 32;
+        if (item < nitems) {
+          const int kc = item / L32, m = item - kc * L32;
+          uint32_t ph4[4], pl4[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          __nv_bfloat16 h0, l0, h1, l1;
-          tc::split_bf16(v[2 * j], h0, l0);
-          tc::split_bf16(v[2 * j + 1], h1, l1);
-          ph4[j] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-          pl4[j] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+          for (int j = 0; j < 4; ++j) {
+            __nv_bfloat16 h0, l0, h1, l1;
+            tc::split_bf16(cur[i][2 * j], h0, l0);
+            tc::split_bf16(cur[i][2 * j + 1], h1, l1);
+            ph4[j] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+            pl4[j] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+          }
+          const uint32_t off = tc::sw128_chunk_offset(m, kc);
+          *reinterpret_cast<uint4*>(hi + off) = make_uint4(ph4[0], ph4[1], ph4[2], ph4[3]);
+          *reinterpret_cast<uint4*>(lo + off) = make_uint4(pl4[0], pl4[1], pl4[2], pl4[3]);
         }
-        const uint32_t off = tc::sw128_chunk_offset(m, kc);
-        *reinterpret_cast<uint4*>(hi + off) = make_uint4(ph4[0], ph4[1], ph4[2], ph4[3]);
-        *reinterpret_cast<uint4*>(lo + off) = make_uint4(pl4[0], pl4[1], pl4[2], pl4[3]);
       }
       tc::fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&full[s]);
+#pragma unroll
+      for (int i = 0; i < kMaxItems; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) cur[i][j] = nxt[i][j];
     }
   } else if (warp == kConvWarps + 1) {
     // ---- MMA issuer

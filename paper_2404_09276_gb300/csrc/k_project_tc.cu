@@ -106,51 +106,80 @@ __global__ void __launch_bounds__(kThreadsP, 1) project_tc_kernel(ProjArgs pa) {
   bool ok = true;
 
   if (warp >= 4 && warp < 4 + kConv) {
-    // ---- converters: C rows -> hi/lo K-major tiles
+    // ---- converters: C rows -> hi/lo K-major tiles. A thread's items of the
+    // next block are loaded into registers before the current block is
+    // converted, so global-load latency overlaps the conversion and the MMA.
     const int cw = warp - 4;
-    int64_t it = 0;
-    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    constexpr int kItems = kRows * 8 / (kConv * 32);  // 4 items of 8 values per thread and block
+    float cur[kItems][8], nxt[kItems][8];
+    auto load = [&](int64_t tile, int kb, float (&v)[kItems][8]) {
       const int64_t r0 = tile * kRows;
-      for (int kb = 0; kb < KB; ++kb, ++it) {
-        const int s = (int)(it % kAStages);
-        const uint32_t ph = (uint32_t)(it / kAStages) & 1u;
-        if (!tc::mbar_wait(&empty[s], ph ^ 1u)) {
-          ok = false;
-          break;
-        }
-        uint8_t* hi = Atiles + (size_t)(2 * s) * kATile;
-        uint8_t* lo = hi + kATile;
-        // item = (row r, chunk kc): 8 consecutive K of one row -> one 16-byte chunk
-        for (int item = cw * 32 + lane; item < kRows * 8; item += kConv * 32) {
-          const int r = item >> 3, kc = item & 7;
-          const int64_t row = r0 + r;
-          const int k0 = kb * kKB + 8 * kc;
-          float v[8];
-          if (row < pa.rows && k0 + 8 <= pa.l) {
-            const float4 a = __ldg(reinterpret_cast<const float4*>(pa.C + row * pa.ldc + k0));
-            const float4 b = __ldg(reinterpret_cast<const float4*>(pa.C + row * pa.ldc + k0 + 4));
-            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-          } else {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) v[j] = (row < pa.rows && k0 + j < pa.l) ? pa.C[row * pa.ldc + k0 + j] : 0.f;
-          }
-          uint32_t h[4], o[4];
+      for (int i = 0; i < kItems; ++i) {
+        const int item = cw * 32 + lane + i * kConv * 32;
+        const int r = item >> 3, kc = item & 7;
+        const int64_t row = r0 + r;
+        const int k0 = kb * kKB + 8 * kc;
+        if (row < pa.rows && k0 + 8 <= pa.l) {
+          const float4 a = __ldg(reinterpret_cast<const float4*>(pa.C + row * pa.ldc + k0));
+          const float4 b = __ldg(reinterpret_cast<const float4*>(pa.C + row * pa.ldc + k0 + 4));
+          v[i][0] = a.x; v[i][1] = a.y; v[i][2] = a.z; v[i][3] = a.w;
+          v[i][4] = b.x; v[i][5] = b.y; v[i][6] = b.z; v[i][7] = b.w;
+        } else {
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            __nv_bfloat16 h0, l0, h1, l1;
-            tc::split_bf16(v[2 * j], h0, l0);
-            tc::split_bf16(v[2 * j + 1], h1, l1);
-            h[j] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-            o[j] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-          }
-          const uint32_t off = tc::sw128_chunk_offset(r, kc);
-          *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
-          *reinterpret_cast<uint4*>(lo + off) = make_uint4(o[0], o[1], o[2], o[3]);
+          for (int j = 0; j < 8; ++j)
+            v[i][j] = (row < pa.rows && k0 + j < pa.l) ? pa.C[row * pa.ldc + k0 + j] : 0.f;
         }
-        tc::fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&full[s]);
       }
+    };
+    int64_t it = 0;
+    int64_t tile = blockIdx.x;
+    int kb = 0;
+    if (tile < ntiles) load(tile, kb, cur);
+    while (tile < ntiles && ok) {
+      // the block after (tile, kb)
+      int64_t ntile = tile;
+      int nkb = kb + 1;
+      if (nkb == KB) {
+        nkb = 0;
+        ntile += gridDim.x;
+      }
+      if (ntile < ntiles) load(ntile, nkb, nxt);
+      const int s = (int)(it % kAStages);
+      const uint32_t ph = (uint32_t)(it / kAStages) & 1u;
+      if (!tc::mbar_wait(&empty[s], ph ^ 1u)) {
+        ok = false;
+        break;
+      }
+      uint8_t* hi = Atiles + (size_t)(2 * s) * kATile;
+      uint8_t* lo = hi + kATile;
+#pragma unroll
+      for (int i = 0; i < kItems; ++i) {
+        const int item = cw * 32 + lane + i * kConv * 32;
+        const int r = item >> 3, kc = item & 7;
+        uint32_t h[4], o[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          __nv_bfloat16 h0, l0, h1, l1;
+          tc::split_bf16(cur[i][2 * j], h0, l0);
+          tc::split_bf16(cur[i][2 * j + 1], h1, l1);
+          h[j] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+          o[j] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+        }
+        const uint32_t off = tc::sw128_chunk_offset(r, kc);
+        *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4*>(lo + off) = make_uint4(o[0], o[1], o[2], o[3]);
+      }
+      tc::fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&full[s]);
+#pragma unroll
+      for (int i = 0; i < kItems; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) cur[i][j] = nxt[i][j];
+      tile = ntile;
+      kb = nkb;
+      ++it;
     }
   } else if (warp == 4 + kConv) {
     // ---- MMA issuer

@@ -66,10 +66,10 @@ __device__ double block_sum(double v, double* red) {
   return s;
 }
 
-// lambda, delta and E from S = X^T G X and T = X^T X (one CTA)
-__global__ void __launch_bounds__(1024) refine_step_kernel(const double* __restrict__ S, const double* __restrict__ T,
-                                                           const double* __restrict__ G64, int64_t ldg, int l,
-                                                           double* __restrict__ lam, double* __restrict__ E) {
+// lambda and delta from S = X^T G X and T = X^T X (one CTA: three l x l sums)
+__global__ void __launch_bounds__(1024) refine_norms_kernel(const double* __restrict__ S, const double* __restrict__ T,
+                                                            const double* __restrict__ G64, int64_t ldg, int l,
+                                                            double* __restrict__ lam, double* __restrict__ delta) {
   __shared__ double red[32];
   __shared__ double lm[kMaxL];
   for (int i = threadIdx.x; i < l; i += blockDim.x) {
@@ -90,15 +90,23 @@ __global__ void __launch_bounds__(1024) refine_step_kernel(const double* __restr
   sd = block_sum(sd, red);
   rr = block_sum(rr, red);
   gg = block_sum(gg, red);
-  const double delta = 2.0 * (sqrt(sd) + sqrt(gg) * sqrt(rr));
-  for (int64_t idx = threadIdx.x; idx < (int64_t)l * l; idx += blockDim.x) {
-    const int i = (int)(idx / l), j = (int)(idx - (int64_t)i * l);
-    const double r = (i == j ? 1.0 : 0.0) - T[idx];
-    double e = 0.5 * r;
-    if (i != j && fabs(lm[i] - lm[j]) > delta) e = (S[idx] + lm[j] * r) / (lm[j] - lm[i]);
-    E[idx] = e;
-  }
   for (int i = threadIdx.x; i < l; i += blockDim.x) lam[i] = lm[i];
+  if (threadIdx.x == 0) *delta = 2.0 * (sqrt(sd) + sqrt(gg) * sqrt(rr));
+}
+
+// E from S, T, lambda and delta: one thread per entry, over many CTAs (the
+// FP64 divisions are the costly part on this part's FP64 units)
+__global__ void refine_e_kernel(const double* __restrict__ S, const double* __restrict__ T,
+                                const double* __restrict__ lam, const double* __restrict__ delta, int l,
+                                double* __restrict__ E) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)l * l) return;
+  const int i = (int)(idx / l), j = (int)(idx - (int64_t)i * l);
+  const double r = (i == j ? 1.0 : 0.0) - T[idx];
+  double e = 0.5 * r;
+  const double li = lam[i], lj = lam[j];
+  if (i != j && fabs(li - lj) > *delta) e = (S[idx] + lj * r) / (lj - li);
+  E[idx] = e;
 }
 
 }  // namespace
@@ -120,7 +128,8 @@ cudaError_t launch_refine_fp64(const double* G64, int64_t ldg, const float* V32,
     gemm64_kernel<false, false><<<grid, kT * kT, 0, st>>>(G64, ldg, Xa, l, nullptr, Pm, l);  // P = G X
     gemm64_kernel<true, false><<<grid, kT * kT, 0, st>>>(Xa, l, Pm, l, nullptr, Sm, l);     // S = X^T P
     gemm64_kernel<true, false><<<grid, kT * kT, 0, st>>>(Xa, l, Xa, l, nullptr, Tm, l);     // T = X^T X
-    refine_step_kernel<<<1, 1024, 0, st>>>(Sm, Tm, G64, ldg, l, wk.lam64, Em);
+    refine_norms_kernel<<<1, 1024, 0, st>>>(Sm, Tm, G64, ldg, l, wk.lam64, wk.scal);
+    refine_e_kernel<<<(unsigned)ds_ceil_div((int64_t)l * l, 128), 128, 0, st>>>(Sm, Tm, wk.lam64, wk.scal, l, Em);
     gemm64_kernel<false, true><<<grid, kT * kT, 0, st>>>(Xa, l, Em, l, Xa, Xb, l);  // X' = X + X E
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     double* t = Xa;

@@ -15,6 +15,10 @@ namespace {  // internal linkage: each including unit gets its own kernels
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kThreads = 256;
 
+// Q type of a product without the shift (Y = A X): the kernels instantiated
+// for it keep no registers for the epilogue's Q.
+struct NoShift {};
+
 template <typename TQ>
 struct Epilogue {
   const double* alpha;  // nullptr: plain product
@@ -22,6 +26,8 @@ struct Epilogue {
   int64_t ldq;
   int l;
 };
+template <typename TQ>
+constexpr bool kShift = !std::is_same<TQ, NoShift>::value;
 
 __device__ __forceinline__ float4 f4_fma(float a, float4 x, float4 acc) {
   acc.x = fmaf(a, x.x, acc.x);
@@ -118,12 +124,14 @@ template <typename TQ>
 __device__ __forceinline__ float4 apply_epilogue(float4 s, int slot, int64_t row, const Epilogue<TQ>& ep, float alpha) {
   const int c = 4 * slot;
   if (c >= ep.l) return f4_zero();  // padding columns (no Q read)
-  if (ep.alpha) {
-    const float4 q = load4(ep.Q + row * ep.ldq, slot);
-    s.x = fmaf(-alpha, q.x, s.x);
-    s.y = fmaf(-alpha, q.y, s.y);
-    s.z = fmaf(-alpha, q.z, s.z);
-    s.w = fmaf(-alpha, q.w, s.w);
+  if constexpr (kShift<TQ>) {
+    if (ep.alpha) {
+      const float4 q = load4(ep.Q + row * ep.ldq, slot);
+      s.x = fmaf(-alpha, q.x, s.x);
+      s.y = fmaf(-alpha, q.y, s.y);
+      s.z = fmaf(-alpha, q.z, s.z);
+      s.w = fmaf(-alpha, q.w, s.w);
+    }
   }
   if (c + 1 >= ep.l) s.y = 0.f;
   if (c + 2 >= ep.l) s.z = 0.f;
@@ -131,17 +139,52 @@ __device__ __forceinline__ float4 apply_epilogue(float4 s, int slot, int64_t row
   return s;
 }
 
+// The epilogue with the row's Q slot already in registers (loaded when the row
+// started, so that its latency overlaps the gathers).
+__device__ __forceinline__ float4 apply_epilogue_q(float4 s, int slot, int l, bool shift, float alpha, float4 q) {
+  const int c = 4 * slot;
+  if (c >= l) return f4_zero();
+  if (shift) {
+    s.x = fmaf(-alpha, q.x, s.x);
+    s.y = fmaf(-alpha, q.y, s.y);
+    s.z = fmaf(-alpha, q.z, s.z);
+    s.w = fmaf(-alpha, q.w, s.w);
+  }
+  if (c + 1 >= l) s.y = 0.f;
+  if (c + 2 >= l) s.z = 0.f;
+  if (c + 3 >= l) s.w = 0.f;
+  return s;
+}
+
+// Prefetch the Q slots this lane will write for `row` (team layout: slot t + 8v
+// for the v with v mod 4 == team); qv[v / 4].
+template <int V, typename TQ>
+__device__ __forceinline__ void prefetch_q(const Epilogue<TQ>& ep, int64_t row, int lane, float4 (&qv)[2]) {
+  qv[0] = qv[1] = f4_zero();
+  if constexpr (kShift<TQ>) {
+    const int g = lane >> 3, t = lane & 7;
+    if (!ep.alpha) return;
+    const TQ* q = ep.Q + row * ep.ldq;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const int slot = t + 8 * v;
+      if ((v & 3) == g && 4 * slot < ep.l) qv[v >> 2] = load4(q, slot);
+    }
+  }
+}
+
 // Write a reduced row (teams split the slots), with the epilogue, zero padding to ldy.
 template <int V, typename TOut, typename TQ>
 __device__ __forceinline__ void store_row(const float4 (&acc)[V], int64_t row, TOut* __restrict__ Y, int64_t ldy,
-                                          const Epilogue<TQ>& ep, float alpha, int lane) {
+                                          const Epilogue<TQ>& ep, float alpha, int lane, const float4 (&qv)[2]) {
   const int g = lane >> 3, t = lane & 7;
   TOut* y = Y + row * ldy;
   const int ldy4 = (int)(ldy >> 2);
 #pragma unroll
   for (int v = 0; v < V; ++v) {
     const int slot = t + 8 * v;
-    if ((v & 3) == g && slot < ldy4) store4(y, slot, apply_epilogue(acc[v], slot, row, ep, alpha));
+    if ((v & 3) == g && slot < ldy4)
+      store4(y, slot, apply_epilogue_q(acc[v], slot, ep.l, kShift<TQ> && ep.alpha != nullptr, alpha, qv[v >> 2]));
   }
   for (int slot = 8 * V + lane; slot < ldy4; slot += 32) store4(y, slot, f4_zero());
 }
@@ -173,6 +216,8 @@ __global__ void __launch_bounds__(kThreads, MINB) spmm_rows_kernel(const int32_t
   int c;
   float a;
   load_pairs(col, val, pos, e, lane, c, a);
+  float4 qv[2];
+  prefetch_q<V>(ep, r, lane, qv);
   float4 acc[V];
 #pragma unroll
   for (int v = 0; v < V; ++v) acc[v] = f4_zero();
@@ -193,11 +238,12 @@ __global__ void __launch_bounds__(kThreads, MINB) spmm_rows_kernel(const int32_t
     a = an;
     if (pos + 32 >= e) {  // row done
       team_reduce<V>(acc);
-      store_row<V, TOut, TQ>(acc, r, Y, ldy, ep, alpha, lane);
+      store_row<V, TOut, TQ>(acc, r, Y, ldy, ep, alpha, lane, qv);
 #pragma unroll
       for (int v = 0; v < V; ++v) acc[v] = f4_zero();
       r = rn;
       if (r >= m) break;
+      prefetch_q<V>(ep, r, lane, qv);
       pos = next;
       e = next_e;
     } else {
@@ -263,7 +309,13 @@ __global__ void __launch_bounds__(kThreads, MINB) spmm_merge_kernel(const int32_
 #pragma unroll
     for (int v = 0; v < V; ++v) acc[v] = f4_zero();
     // rows r0 .. r1-1 end inside the segment; row r1 (if any entries here) continues past it
+    float4 qv[2] = {f4_zero(), f4_zero()};
+    int64_t qrow = -1;
     while (r < r1 || (r == r1 && r1 < m && pos < k1)) {
+      if (r != qrow && r < r1 && !(r == r0 && split_head)) {  // the row is written here: prefetch its Q
+        prefetch_q<V>(ep, r, lane, qv);
+        qrow = r;
+      }
       int64_t e;
       if (r < r1) {
         if (r - rw >= 32) {
@@ -296,7 +348,7 @@ __global__ void __launch_bounds__(kThreads, MINB) spmm_merge_kernel(const int32_
           store_carry<V>(acc, carry + (2 * w) * (int64_t)ldc, ldc4, lane);
           head_row = (int32_t)r;
         } else {
-          store_row<V, TOut, TQ>(acc, r, Y, ldy, ep, alpha, lane);
+          store_row<V, TOut, TQ>(acc, r, Y, ldy, ep, alpha, lane, qv);
         }
 #pragma unroll
         for (int v = 0; v < V; ++v) acc[v] = f4_zero();
@@ -395,7 +447,7 @@ size_t tma_smem_bytes(int nslot) {
 }
 
 template <int R, typename TOut, typename TQ>
-__global__ void __launch_bounds__(kTmaWarps * 32) spmm_tma_kernel(const int32_t* __restrict__ rowptr,
+__global__ void __launch_bounds__(kTmaWarps * 32, R <= 8 ? 4 : 2) spmm_tma_kernel(const int32_t* __restrict__ rowptr,
                                                                   const int32_t* __restrict__ col,
                                                                   const float* __restrict__ val, int64_t m,
                                                                   const float* __restrict__ X, int64_t ldx,
@@ -441,7 +493,15 @@ __global__ void __launch_bounds__(kTmaWarps * 32) spmm_tma_kernel(const int32_t*
     int rp = rowptr[(rw + 1 + lane) < m ? (rw + 1 + lane) : m];
     float4 acc0 = f4_zero(), acc1 = f4_zero();
     int64_t r = r0, pos = k0;
+    float4 q0 = f4_zero(), q1 = f4_zero();
     while (r < r1 || (r == r1 && r1 < m && pos < k1)) {
+      if constexpr (kShift<TQ>) {
+        if (ep.alpha && r < r1 && !(r == r0 && split_head)) {  // the row is written here: prefetch its Q
+          const TQ* q = ep.Q + r * ep.ldq;
+          q0 = 4 * lane < ep.l ? load4(q, lane) : f4_zero();
+          q1 = 4 * (lane + 32) < ep.l ? load4(q, lane + 32) : f4_zero();
+        }
+      }
       int64_t e;
       if (r < r1) {
         if (r - rw >= 32) {
@@ -500,7 +560,8 @@ __global__ void __launch_bounds__(kTmaWarps * 32) spmm_tma_kernel(const int32_t*
         TOut* y = Y + r * ldy;
         for (int sl = lane; sl < ldy4; sl += 32) {
           const float4 v = sl < 32 ? acc0 : (sl < 64 ? acc1 : f4_zero());
-          store4(y, sl, apply_epilogue(sl < nslot ? v : f4_zero(), sl, r, ep, alpha));
+          store4(y, sl, apply_epilogue_q(sl < nslot ? v : f4_zero(), sl, ep.l, kShift<TQ> && ep.alpha != nullptr, alpha,
+                                         sl < 32 ? q0 : q1));
         }
       }
       acc0 = f4_zero();
@@ -592,10 +653,26 @@ cudaError_t launch_v(const dashsvd_csr& A, const SpmmPart& part, const TIn* X, i
 }
 
 template <typename TIn, typename TOut, typename TQ>
+cudaError_t dispatch_ep(const dashsvd_csr& A, const SpmmPart& part, const TIn* X, int64_t ldx, int l, TOut* Y,
+                        int64_t ldy, const Epilogue<TQ>& ep, int variant, const SpmmScratch& scr, int num_sms,
+                        cudaStream_t st, int* err);
+
+// The product Y = A X (alpha == nullptr) or Y = A X - alpha Q.
+template <typename TIn, typename TOut, typename TQ>
 cudaError_t dispatch(const dashsvd_csr& A, const SpmmPart& part, const TIn* X, int64_t ldx, int l, TOut* Y,
                      int64_t ldy, const double* alpha, const TQ* Q, int64_t ldq, int variant, const SpmmScratch& scr,
                      int num_sms, cudaStream_t st, int* err = nullptr) {
-  Epilogue<TQ> ep{alpha, Q, ldq, l};
+  if (!alpha)
+    return dispatch_ep<TIn, TOut, NoShift>(A, part, X, ldx, l, Y, ldy, Epilogue<NoShift>{nullptr, nullptr, 0, l},
+                                           variant, scr, num_sms, st, err);
+  return dispatch_ep<TIn, TOut, TQ>(A, part, X, ldx, l, Y, ldy, Epilogue<TQ>{alpha, Q, ldq, l}, variant, scr, num_sms,
+                                    st, err);
+}
+
+template <typename TIn, typename TOut, typename TQ>
+cudaError_t dispatch_ep(const dashsvd_csr& A, const SpmmPart& part, const TIn* X, int64_t ldx, int l, TOut* Y,
+                        int64_t ldy, const Epilogue<TQ>& ep, int variant, const SpmmScratch& scr, int num_sms,
+                        cudaStream_t st, int* err) {
   if (variant == 6 || variant == 7) {
     if constexpr (std::is_same<TIn, float>::value) {
       return variant == 6 ? launch_tma<16, TOut, TQ>(A, part, X, ldx, l, Y, ldy, ep, scr, err, num_sms, st)

@@ -58,6 +58,8 @@ cudaError_t launch_spmm(const dashsvd_csr& A, const SpmmPart& part, const float*
 cudaError_t prepare_spmm() {
   cudaError_t e = prepare_tma<16, float, float>();
   if (e == cudaSuccess) e = prepare_tma<8, float, float>();
+  if (e == cudaSuccess) e = prepare_tma<16, float, NoShift>();
+  if (e == cudaSuccess) e = prepare_tma<8, float, NoShift>();
   return e;
 }
 
