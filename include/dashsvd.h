@@ -87,8 +87,11 @@ typedef struct {
                               nonzeros per team in flight, 1: four, 2: two with registers
                               capped for four blocks per SM); 6, 7 = merge path with the
                               gathered rows staged in shared memory by bulk copies (TMA)
-                              in per-warp rings of 16 / 8 rows (FP32 operands only, so
-                              not with gather_bf16) */
+                              in per-warp rings of 16 / 8 rows; 8, 9 = merge path over
+                              column slabs of 32 (one launch per slab, so the slab of
+                              the gathered block can stay in L2), two / four nonzeros
+                              per team in flight (6-9: FP32 operands only, so not with
+                              gather_bf16) */
   int32_t record_trace;    /* 1: keep the per-pass Shat / shift history (get_trace) */
   int32_t shift;           /* 1: dynamic shifts (dashSVD); 0: alpha = 0 (Alg. 1 form) */
   int32_t gather_bf16;     /* precision form only: 1 stores the gathered operands Q and Y
@@ -141,6 +144,12 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
  * eigensolve, then Shat_1..Shat_l of the pass.
  * Writes at most `cap` doubles; *count receives the number of records. */
 int dashsvd_get_trace(dashsvd_handle h, double* out, int64_t cap, int64_t* count, int* l);
+
+/* The SpMM autotuner's measurements from the last run that tuned (HOST
+ * buffer of at least 40 floats): ms[10 * product + variant] = best time of that
+ * variant in ms (0 = not timed), products 0: A Q, 1: A^T Y - alpha Q (FP32),
+ * 2, 3: the same with BF16 gathers. */
+int dashsvd_get_tuning(dashsvd_handle h, float* ms, int64_t cap);
 
 /* ---- learned form --------------------------------------------------------
  * The paper has no learned component; this is an addition. A network
@@ -218,7 +227,7 @@ int dashsvd_csr_transpose(dashsvd_handle h, const dashsvd_csr* A, int32_t* rowpt
 
 /* Y = A X (Alg. 5 step 4, inner product A Q; also B = A Q, step 9).
  * X: A.n x ldx, Y: A.m x ldy, both with ld % 4 == 0 and ld >= l; Y's columns
- * l .. ldy-1 are set to 0. variant: -1 (merge path, configuration 0) or 0..7
+ * l .. ldy-1 are set to 0. variant: -1 (merge path, configuration 0) or 0..9
  * as in dashsvd_options.spmm_variant. Variants 6 and 7 wait for their bulk
  * copies with a bounded poll; this call then waits for its own work and
  * returns DASHSVD_ETIMEOUT if a wait ran out. */

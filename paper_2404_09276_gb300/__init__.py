@@ -40,6 +40,7 @@ EXPORTS = (
     "dashsvd_gram_bf16x3",
     "dashsvd_project", "dashsvd_project_bf16x3", "dashsvd_eigsvd", "dashsvd_gram_noalloc",
     "dashsvd_mlp_features", "dashsvd_mlp_forward", "dashsvd_mlp_loss_grad", "dashsvd_mlp_adam",
+    "dashsvd_get_tuning",
 )
 MLP_PARAMS = 1218
 MLP_IN = 16
@@ -97,6 +98,7 @@ def _load():
         "dashsvd_eigsvd": (I, [P, P, I64, I, I64, P, I64, P, P, I]),
         "dashsvd_gram_noalloc": (I, [P, I64, I, I64, P, I64, P]),
         "dashsvd_mlp_features": (I, [P, P, I64, I, I, I, D, P]),
+        "dashsvd_get_tuning": (I, [P, P, I64]),
         "dashsvd_mlp_forward": (I, [P, P, P, I64, P]),
         "dashsvd_mlp_loss_grad": (I, [P, P, P, P, P, I64, P, P]),
         "dashsvd_mlp_adam": (I, [P, P, P, P, P, I, C.c_float, C.c_float, C.c_float, C.c_float]),
@@ -137,6 +139,7 @@ dashsvd_project_bf16x3 = _export("dashsvd_project_bf16x3")
 dashsvd_eigsvd = _export("dashsvd_eigsvd")
 dashsvd_gram_noalloc = _export("dashsvd_gram_noalloc")
 dashsvd_mlp_features = _export("dashsvd_mlp_features")
+dashsvd_get_tuning = _export("dashsvd_get_tuning")
 dashsvd_mlp_forward = _export("dashsvd_mlp_forward")
 dashsvd_mlp_loss_grad = _export("dashsvd_mlp_loss_grad")
 dashsvd_mlp_adam = _export("dashsvd_mlp_adam")
@@ -339,6 +342,14 @@ class Handle:
         check(dashsvd_project_bf16x3(self.h, Cm.data_ptr(), Cm.shape[0], l, Cm.stride(0), W.data_ptr(), W.stride(0),
                                      cols, out.data_ptr(), out.stride(0)), "dashsvd_project_bf16x3")
         return out
+
+    def tuning(self):
+        """The autotuner's last measurements: (4 products x 10 variants) ms, 0 = not timed."""
+        import numpy as np
+
+        buf = np.zeros(40, dtype=np.float32)
+        check(dashsvd_get_tuning(self.h, buf.ctypes.data, buf.size), "dashsvd_get_tuning")
+        return buf.reshape(4, 10)
 
     # -- learned form ------------------------------------------------------------
     def load_mlp(self, weights):

@@ -106,6 +106,7 @@ struct dashsvd_handle_s {
     int l, form, gather, var_fwd32, var_bwd32, var_fwd, var_bwd;
   };
   std::vector<Tune> tuned;
+  float tune_ms[4][10] = {};  // last autotuning: best time per (product, variant), ms; 0 = not timed
 };
 
 namespace {
@@ -317,8 +318,9 @@ int build_graph(dashsvd_handle h, const RunPlan& p) {
   return DASHSVD_OK;
 }
 
-constexpr int kSpmmVariants = 8;  // 0-5: split (warp per row, merge path) x 3 configurations;
-                                  // 6, 7: merge path with bulk-copy (TMA) staging (FP32 operands)
+constexpr int kSpmmVariants = 10;  // 0-5: split (warp per row, merge path) x 3 configurations;
+                                   // 6, 7: merge path with bulk-copy (TMA) staging (FP32 operands);
+                                   // 8, 9: merge path over column slabs of 32 (FP32 operands)
 constexpr int kSpmmVariantsBf16 = 6;
 
 // Time every SpMM variant on this matrix (after one warm-up launch each) for
@@ -336,6 +338,7 @@ int autotune_spmm(dashsvd_handle h, RunPlan& p, const dashsvd_csr& A) {
       return DASHSVD_OK;
     }
   cudaStream_t st = h->stream;
+  std::memset(h->tune_ms, 0, sizeof(h->tune_ms));
   DS_CUDA(cudaMemsetAsync(h->Q.p, 0, h->Q.bytes, st));
   DS_CUDA(cudaMemsetAsync(h->Y.p, 0, h->Y.bytes, st));
   if (h->Qb.p) DS_CUDA(cudaMemsetAsync(h->Qb.p, 0, h->Qb.bytes, st));
@@ -363,9 +366,10 @@ int autotune_spmm(dashsvd_handle h, RunPlan& p, const dashsvd_csr& A) {
                                 v, p.scr, h->num_sms, st);
     }
   };
-  // one timed launch (after a warm-up launch) of the variant
+  // one timed launch of the variant, after a warm-up launch; A^T Y is preceded by
+  // the chosen A Q instead, which leaves the caches as a pass does
   auto time1 = [&](int prod, int v, float* ms) -> cudaError_t {
-    cudaError_t e = launch(prod, v);
+    cudaError_t e = (prod & 1) ? launch(prod - 1, arg[prod - 1]) : launch(prod, v);
     if (e == cudaSuccess) e = cudaEventRecord(e0, st);
     if (e == cudaSuccess) e = launch(prod, v);
     if (e == cudaSuccess) e = cudaEventRecord(e1, st);
@@ -387,11 +391,13 @@ int autotune_spmm(dashsvd_handle h, RunPlan& p, const dashsvd_csr& A) {
         err = time1(prod, v, &ms);
         t[v] = std::min(t[v], ms);
       }
-    for (int v = 0; v < nv; ++v)
+    for (int v = 0; v < nv; ++v) {
+      h->tune_ms[prod][v] = t[v];
       if (t[v] < best[prod]) {
         best[prod] = t[v];
         arg[prod] = v;
       }
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -542,6 +548,13 @@ int dashsvd_mlp_adam(dashsvd_handle h, float* W, const float* grad, float* m, fl
       !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
     return DASHSVD_EINVAL;
   DS_CUDA(launch_mlp_adam(W, grad, m, v, step, lr, beta1, beta2, eps, h->stream));
+  return DASHSVD_OK;
+}
+
+int dashsvd_get_tuning(dashsvd_handle h, float* ms, int64_t cap) {
+  if (!h || !ms || cap < 40) return DASHSVD_EINVAL;
+  for (int p = 0; p < 4; ++p)
+    for (int v = 0; v < 10; ++v) ms[p * 10 + v] = h->tune_ms[p][v];
   return DASHSVD_OK;
 }
 
@@ -760,7 +773,7 @@ static int spmm_common(dashsvd_handle h, const dashsvd_csr* A, const float* X, i
   const int var = variant < 0 ? 1 : variant;
   if ((rc = ensure(h->errw, 16, &moved))) return rc;
   if (var >= 6) DS_CUDA(cudaMemsetAsync(h->errw.p, 0, sizeof(int), h->stream));
-  if ((var & 1) || var >= 6) DS_CUDA(launch_spmm_partition(*A, part, h->stream));
+  if ((var & 1) || var >= 6) DS_CUDA(launch_spmm_partition(*A, part, h->stream));  // merge-path variants
   DS_CUDA(launch_spmm(*A, part, X, ldx, l, Y, ldy, alpha, Q, ldq, var, scr, h->num_sms, h->stream, as<int>(h->errw)));
   if (var >= 6) {  // the bulk-copy variants wait on barriers with a bound: report a timeout
     int werr = 0;

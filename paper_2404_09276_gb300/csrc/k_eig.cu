@@ -219,18 +219,27 @@ __global__ void __launch_bounds__(kReplayWarps * 32) eigvec_replay_kernel(EigWor
   for (int j = lane; j < N; j += 32) x[j] = j == c ? 1.f : 0.f;
   const int nbatch = (nsteps + kBatch - 1) / kBatch;
   // batch b covers steps [nsteps - (b+1) kBatch, nsteps - b kBatch)
+  // batches are staged by asynchronous copies (cp.async), two buffers deep:
+  // batch b + 1 lands while batch b is applied
   auto stage = [&](int b, int buf) {
-    const int t1 = nsteps - b * kBatch;
-    const int t0 = t1 - kBatch > 0 ? t1 - kBatch : 0;
-    const float2* src = wk.log + (int64_t)t0 * P;
-    float2* dst = rs.logb[buf];
-    const int n = (t1 - t0) * P;
-    for (int i = tid; i < n; i += nt) dst[i] = src[i];
+    if (b < nbatch) {
+      const int t1 = nsteps - b * kBatch;
+      const int t0 = t1 - kBatch > 0 ? t1 - kBatch : 0;
+      const float2* src = wk.log + (int64_t)t0 * P;
+      float2* dst = rs.logb[buf];
+      const int n = (t1 - t0) * P;
+      for (int i = tid; i < n; i += nt)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst + i)),
+                     "l"(src + i)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
   };
-  if (nbatch > 0) stage(0, 0);
-  __syncthreads();
+  stage(0, 0);
   for (int b = 0; b < nbatch; ++b) {
-    if (b + 1 < nbatch) stage(b + 1, (b + 1) & 1);  // next batch loads while this one is applied
+    stage(b + 1, (b + 1) & 1);
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // this thread's copies of batch b are in
+    __syncthreads();                                         // ... and everyone's
     const int t1 = nsteps - b * kBatch;
     const int t0 = t1 - kBatch > 0 ? t1 - kBatch : 0;
     const float2* lg = rs.logb[b & 1];
@@ -251,8 +260,9 @@ __global__ void __launch_bounds__(kReplayWarps * 32) eigvec_replay_kernel(EigWor
         __syncwarp();
       }
     }
-    __syncthreads();
+    __syncthreads();  // buffer b & 1 is refilled by the stage call of iteration b + 1
   }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
   if (c < l)
     for (int j = lane; j < l; j += 32) wk.V32[(int64_t)j * l + c] = x[j];
 }

@@ -26,8 +26,10 @@ constexpr int kConv = 8;         // converter warps
 constexpr int kWarps = 4 + kConv + 1;
 constexpr int kThreadsP = kWarps * 32;
 constexpr int kATile = kRows * kKB * 2;  // 16 KB (hi or lo)
-constexpr int kBMax = 150 * 1024;        // W^T hi + lo budget
-constexpr int kSmemP = 2 * kAStages * kATile + kBMax + 1024 + 512;
+constexpr int kBMax = 150 * 1024;        // W^T hi + lo budget (l = 150: 160 x 192 x 4 B = 120 KB)
+constexpr int kStgLd = 17;                                // epilogue staging: 32 rows x 16 columns, padded
+constexpr int kStgBytes = 4 * 32 * kStgLd * 4;            // one 32 x 16 tile per epilogue warp
+constexpr int kSmemP = 2 * kAStages * kATile + kBMax + 1024 + 512 + kStgBytes;
 
 struct ProjArgs {
   const float* C;
@@ -55,6 +57,7 @@ __global__ void __launch_bounds__(kThreadsP, 1) project_tc_kernel(ProjArgs pa) {
   uint64_t* tfull = bars + 2 * kAStages;    // [2]
   uint64_t* tempty = bars + 2 * kAStages + 2;  // [2]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kAStages + 4);
+  float* stg = reinterpret_cast<float*>(Btiles + kBMax + 512);  // epilogue staging (after the barriers)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int Nc = pa.Nc, KB = pa.Kp / kKB;
   const int c0 = blockIdx.y * Nc;
@@ -235,19 +238,28 @@ __global__ void __launch_bounds__(kThreadsP, 1) project_tc_kernel(ProjArgs pa) {
         break;
       }
       tc::tc_fence_after();
-      const int64_t row = tile * kRows + 32 * warp + lane;
+      // TMEM gives one row per thread; the 32 x 16 block goes through shared
+      // memory so that stores run along rows (two 64-byte row pieces per store)
+      float* ws = stg + warp * 32 * kStgLd;
+      const int64_t rbase = tile * kRows + 32 * warp;
       for (int n0 = 0; n0 < Nc; n0 += 16) {
         float v[16];
         tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(b * Nc + n0), v);
-        if (row < pa.rows) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int c = c0 + n0 + i;
-            const float x = c < pa.cols ? v[i] : 0.f;
+        for (int i = 0; i < 16; ++i) ws[lane * kStgLd + i] = c0 + n0 + i < pa.cols ? v[i] : 0.f;
+        __syncwarp();
+        const int cl = lane & 15, c = c0 + n0 + cl;
+#pragma unroll 4
+        for (int rr = 0; rr < 16; ++rr) {
+          const int rl = 2 * rr + (lane >> 4);
+          const int64_t row = rbase + rl;
+          const float x = ws[rl * kStgLd + cl];
+          if (row < pa.rows) {
             if (want_f32 && c < pa.ldf) pa.outF[row * pa.ldf + c] = x;
             if (pa.outB && c < pa.ldb) pa.outB[row * pa.ldb + c] = __float2bfloat16_rn(x);
           }
         }
+        __syncwarp();
       }
       tc::tc_fence_before();
       __syncwarp();

@@ -25,6 +25,7 @@ struct Epilogue {
   const TQ* Q;
   int64_t ldq;
   int l;
+  int yw4;  // float4 slots of each output row that the kernel writes (the rest is left alone)
 };
 template <typename TQ>
 constexpr bool kShift = !std::is_same<TQ, NoShift>::value;
@@ -179,7 +180,7 @@ __device__ __forceinline__ void store_row(const float4 (&acc)[V], int64_t row, T
                                           const Epilogue<TQ>& ep, float alpha, int lane, const float4 (&qv)[2]) {
   const int g = lane >> 3, t = lane & 7;
   TOut* y = Y + row * ldy;
-  const int ldy4 = (int)(ldy >> 2);
+  const int ldy4 = ep.yw4;
 #pragma unroll
   for (int v = 0; v < V; ++v) {
     const int slot = t + 8 * v;
@@ -383,7 +384,7 @@ __global__ void __launch_bounds__(kThreads) spmm_fixup_kernel(const float* __res
   int64_t t = s - 1;
   while (t >= 0 && carry_row[t] < 0) --t;
   if (t >= 0 && carry_row[t] == row) return;  // not the first piece
-  const int ldy4 = (int)(ldy >> 2), ldc4 = ldc >> 2;
+  const int ldy4 = ep.yw4, ldc4 = ldc >> 2;
   const bool in0 = lane < ldc4, in1 = lane + 32 < ldc4;
   float4 acc0 = f4_zero(), acc1 = f4_zero();
   for (int64_t base = s;; base += 32) {
@@ -466,7 +467,7 @@ __global__ void __launch_bounds__(kTmaWarps * 32, R <= 8 ? 4 : 2) spmm_tma_kerne
   __syncwarp();
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const float alpha = ep.alpha ? (float)*ep.alpha : 0.f;
-  const int ldy4 = (int)(ldy >> 2), ldc4 = ldc >> 2;
+  const int ldy4 = ep.yw4, ldc4 = ldc >> 2;
   const bool two = lane + 32 < nslot;  // this lane owns a second float4 slot
   uint32_t cnt = 0;                    // nonzeros consumed by this warp so far (ring position)
   uint32_t issued = 0;                 // bulk copies issued by this warp so far
@@ -638,7 +639,8 @@ cudaError_t launch_vc(const dashsvd_csr& A, const SpmmPart& part, const TIn* X, 
 // configuration 0: two entries per team per round; 1: four entries per round;
 // 2: two entries per round with registers capped for four blocks per SM;
 // variants 6 and 7 (FP32 operands): merge path with the gathered rows staged
-// by bulk copies in per-warp rings of 16 and 8 rows
+// by bulk copies in per-warp rings of 16 and 8 rows; 8 and 9 (FP32): merge
+// path over column slabs of 32, two or four nonzeros per team in flight
 template <int V, typename TIn, typename TOut, typename TQ>
 cudaError_t launch_v(const dashsvd_csr& A, const SpmmPart& part, const TIn* X, int64_t ldx, int l, TOut* Y,
                      int64_t ldy, const Epilogue<TQ>& ep, int variant, const SpmmScratch& scr, int num_sms,
@@ -663,16 +665,38 @@ cudaError_t dispatch(const dashsvd_csr& A, const SpmmPart& part, const TIn* X, i
                      int64_t ldy, const double* alpha, const TQ* Q, int64_t ldq, int variant, const SpmmScratch& scr,
                      int num_sms, cudaStream_t st, int* err = nullptr) {
   if (!alpha)
-    return dispatch_ep<TIn, TOut, NoShift>(A, part, X, ldx, l, Y, ldy, Epilogue<NoShift>{nullptr, nullptr, 0, l},
-                                           variant, scr, num_sms, st, err);
-  return dispatch_ep<TIn, TOut, TQ>(A, part, X, ldx, l, Y, ldy, Epilogue<TQ>{alpha, Q, ldq, l}, variant, scr, num_sms,
-                                    st, err);
+    return dispatch_ep<TIn, TOut, NoShift>(A, part, X, ldx, l, Y, ldy,
+                                           Epilogue<NoShift>{nullptr, nullptr, 0, l, (int)(ldy >> 2)}, variant, scr,
+                                           num_sms, st, err);
+  return dispatch_ep<TIn, TOut, TQ>(A, part, X, ldx, l, Y, ldy, Epilogue<TQ>{alpha, Q, ldq, l, (int)(ldy >> 2)}, variant,
+                                    scr, num_sms, st, err);
 }
 
 template <typename TIn, typename TOut, typename TQ>
 cudaError_t dispatch_ep(const dashsvd_csr& A, const SpmmPart& part, const TIn* X, int64_t ldx, int l, TOut* Y,
                         int64_t ldy, const Epilogue<TQ>& ep, int variant, const SpmmScratch& scr, int num_sms,
                         cudaStream_t st, int* err) {
+  if (variant == 8 || variant == 9) {
+    // column slabs of 32: each launch gathers 128-byte row pieces, so the
+    // gathered slab of X (n x 32 floats) can stay in L2 while A is streamed
+    if constexpr (std::is_same<TIn, float>::value) {
+      const int ldy4 = (int)(ldy >> 2);
+      for (int c0 = 0; c0 < l; c0 += 32) {
+        Epilogue<TQ> es = ep;
+        es.l = l - c0 < 32 ? l - c0 : 32;
+        if constexpr (kShift<TQ>) es.Q = ep.Q ? ep.Q + c0 : nullptr;
+        es.yw4 = c0 + 32 >= l ? ldy4 - c0 / 4 : 8;
+        const cudaError_t e =
+            variant == 8
+                ? launch_vc<1, 2, 4, TIn, TOut, TQ>(A, part, X + c0, ldx, es.l, Y + c0, ldy, es, 1, scr, num_sms, st)
+                : launch_vc<1, 4, 4, TIn, TOut, TQ>(A, part, X + c0, ldx, es.l, Y + c0, ldy, es, 1, scr, num_sms, st);
+        if (e != cudaSuccess) return e;
+      }
+      return cudaSuccess;
+    } else {
+      return cudaErrorInvalidValue;
+    }
+  }
   if (variant == 6 || variant == 7) {
     if constexpr (std::is_same<TIn, float>::value) {
       return variant == 6 ? launch_tma<16, TOut, TQ>(A, part, X, ldx, l, Y, ldy, ep, scr, err, num_sms, st)

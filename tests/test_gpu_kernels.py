@@ -114,7 +114,7 @@ def _spmm_check(A, X, Y, l):
 
 @pytest.mark.parametrize("name", list(MATRICES))
 @pytest.mark.parametrize("l", [1, 7, 30, 150, 160, 220])
-@pytest.mark.parametrize("variant", range(8))
+@pytest.mark.parametrize("variant", range(10))
 def test_spmm_matches_fp64(ds, h, name, l, variant):
     A = MATRICES[name]()
     rng = np.random.default_rng(l)
@@ -127,7 +127,7 @@ def test_spmm_matches_fp64(ds, h, name, l, variant):
 
 
 @pytest.mark.parametrize("name", ["social", "mixed"])
-@pytest.mark.parametrize("variant", range(8))
+@pytest.mark.parametrize("variant", range(10))
 def test_spmm_shift_matches_fp64(ds, h, name, variant):
     import torch
 
