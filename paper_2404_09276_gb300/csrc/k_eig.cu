@@ -35,6 +35,10 @@ namespace {
 constexpr int kJacThreads = 1024;
 constexpr int kMaxN = kMaxL;  // N <= 256
 constexpr float kEps32 = 1.1920929e-07f;
+// Jacobi skip threshold (relative, |G_pq| <= tol sqrt(G_pp G_qq)) when the
+// result is refined in FP64 afterwards: two refinement steps take an
+// off-diagonal residue of 1e-4 to below 1e-15
+constexpr float kRefinedJacobiTol = 1e-4f;
 
 
 // Packed upper triangle: element (a, b), a <= b, of an N x N matrix at
@@ -81,7 +85,7 @@ size_t jacobi_smem(int l) {
 // block table, and a barrier. A sweep starts only if some pair is above the
 // skip threshold, so no sweep is spent just to see that none rotates.
 __global__ void __launch_bounds__(kJacThreads) jacobi_f32_kernel(const float* __restrict__ Gin, int64_t ldg, int l,
-                                                                 EigWork wk) {
+                                                                 EigWork wk, float rel_tol) {
   extern __shared__ __align__(16) float dyn[];
   __shared__ JacSmem js;
   const int N = l + (l & 1), P = N / 2, M = N - 1;
@@ -123,7 +127,7 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_f32_kernel(const float* __
       const int a = idx / N, b = idx - a * N;
       if (b <= a || b >= l) continue;
       const float g = fabsf(G[pk_off(a, N) + b]);
-      found = g > kEps32 * sqrtf(fabsf(d[a]) * fabsf(d[b])) && g > tiny;
+      found = g > rel_tol * sqrtf(fabsf(d[a]) * fabsf(d[b])) && g > tiny;
     }
     if (!__syncthreads_or(found)) {
       converged = true;
@@ -138,7 +142,7 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_f32_kernel(const float* __
         float c = 1.f, sn = 0.f;
         if (p < l && q < l) {
           const float app = d[p], aqq = d[q], apq = G[p < q ? op + q : oq + p];
-          const float thr = kEps32 * sqrtf(fabsf(app) * fabsf(aqq));
+          const float thr = rel_tol * sqrtf(fabsf(app) * fabsf(aqq));
           if (fabsf(apq) > thr && fabsf(apq) > tiny) {
             // correctly rounded sqrt and division keep c^2 + s^2 = 1 to an ulp,
             // so that rotations do not rescale G and V over many sweeps
@@ -515,7 +519,7 @@ cudaError_t prepare_eig() {
 
 cudaError_t launch_eig_f32(const float* G, int64_t ldg, const EigArgs& a, const EigWork& wk, cudaStream_t st) {
   if (a.l < 1 || a.l > kMaxL) return cudaErrorInvalidValue;
-  jacobi_f32_kernel<<<1, kJacThreads, jacobi_smem(a.l), st>>>(G, ldg, a.l, wk);
+  jacobi_f32_kernel<<<1, kJacThreads, jacobi_smem(a.l), st>>>(G, ldg, a.l, wk, kEps32);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   eigvec_replay_kernel<<<(unsigned)ds_ceil_div(a.l, kReplayWarps), kReplayWarps * 32, 0, st>>>(wk, a.l);
@@ -530,7 +534,9 @@ cudaError_t launch_eig_f32(const float* G, int64_t ldg, const EigArgs& a, const 
 cudaError_t launch_eig_refined(const float* G32, int64_t ldg32, const double* G64, int64_t ldg64, double eps_null,
                                int iters, const EigArgs& a, const EigWork& wk, cudaStream_t st) {
   if (a.l < 1 || a.l > kMaxL) return cudaErrorInvalidValue;
-  jacobi_f32_kernel<<<1, kJacThreads, jacobi_smem(a.l), st>>>(G32, ldg32, a.l, wk);
+  // the FP64 refinement converges quadratically from the Jacobi basis, so the
+  // sweeps stop at a looser threshold (pairs below kRefinedJacobiTol are left)
+  jacobi_f32_kernel<<<1, kJacThreads, jacobi_smem(a.l), st>>>(G32, ldg32, a.l, wk, kRefinedJacobiTol);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   eigvec_replay_kernel<<<(unsigned)ds_ceil_div(a.l, kReplayWarps), kReplayWarps * 32, 0, st>>>(wk, a.l);
