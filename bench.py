@@ -253,6 +253,19 @@ def _sigma_ref(cfg, scale):
     return np.loadtxt(p, comments="#")
 
 
+def _max_over_ranks(value: float, world: int, device: str) -> float:
+    """The slowest rank's time: every rank runs one replica of the workload
+    (the path does not shard), so the job takes as long as its slowest rank."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _measure_form(form, args, ds, torch, A, Ad, prm, stream, flush, barrier, world, local, sigma_ref):
     """Time `steps` full runs of one form, plus its trace, e2e and per-kernel times."""
     k, s, p_max, tol = prm["k"], prm["s"], prm["p_max"], prm["tol"]
@@ -272,7 +285,8 @@ def _measure_form(form, args, ds, torch, A, Ad, prm, stream, flush, barrier, wor
         h.load_mlp(mlp)
     At = h.csr_transpose(Ad)
     h.run(Ad, k, s, p_max, tol, U, S, V)  # first run: autotuning
-    tuning = [[round(float(x), 3) for x in row] for row in h.tuning()[: (4 if gb else 2)]]
+    tn = h.tuning()
+    tuning = [[round(float(x), 3) for x in row] for row in tn[: (4 if gb else 2)]] + [[round(float(tn[4][0]), 3)]]
 
     def timed(tol_run):
         for _ in range(args.warmup):
@@ -302,14 +316,11 @@ def _measure_form(form, args, ds, torch, A, Ad, prm, stream, flush, barrier, wor
         if eps is None or eps <= tol:
             break
         tol_run /= 2
-    t_step = statistics.median(times)
-    if world > 1:
-        t = torch.tensor([t_step], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_step = float(t.item())
+    t_step = _max_over_ranks(statistics.median(times), world, "cuda")
     info = infos[-1]
     passes = info.passes
     var_fwd, var_bwd = info.spmm_variant & 0xFF, (info.spmm_variant >> 8) & 0xFF
+    fused = bool((info.spmm_variant >> 16) & 1)
 
     # one untimed run with the per-pass trace (shift, PVE ratio, Jacobi sweeps)
     with ds.Handle(stream=stream, record_trace=1, form=fcode, gather_bf16=gb, learned=learned) as ht:
@@ -347,7 +358,7 @@ def _measure_form(form, args, ds, torch, A, Ad, prm, stream, flush, barrier, wor
         e2e_step()
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
-    e2e = {"value": statistics.median(e2e_times), "unit": "s",
+    e2e = {"value": _max_over_ranks(statistics.median(e2e_times), world, "cuda"), "unit": "s",
            "h2d_bytes_per_step": A.rowptr.nbytes + A.colidx.nbytes + A.val.nbytes,
            "d2h_bytes_per_step": (A.m * k + k + A.n * k) * 4}
 
@@ -395,7 +406,7 @@ def _measure_form(form, args, ds, torch, A, Ad, prm, stream, flush, barrier, wor
         "eig": (passes + 2) * kt["eig"],
     }
     spmm = {"fwd_gbs": bytes_fwd / kt["spmm_fwd"] / 1e9, "bwd_gbs": bytes_bwd / kt["spmm_bwd"] / 1e9,
-            "fwd_bytes": bytes_fwd, "bwd_bytes": bytes_bwd, "variants": [var_fwd, var_bwd]}
+            "fwd_bytes": bytes_fwd, "bwd_bytes": bytes_bwd, "variants": [var_fwd, var_bwd], "fused_pass_product": fused}
     h.close()
     return {"form": form, "value": t_step, "times": times, "passes": passes, "status": info.status,
             "accuracy": {"eps_pve": attempts[-1]["eps_pve"], "tol_used": tol_run, "attempts": attempts},

@@ -91,7 +91,9 @@ typedef struct {
                               column slabs of 32 (one launch per slab, so the slab of
                               the gathered block can stay in L2), two / four nonzeros
                               per team in flight (6-9: FP32 operands only, so not with
-                              gather_bf16) */
+                              gather_bf16); 10 = the fused pass product of
+                              dashsvd_spmm_fused for the power-iteration passes (the
+                              prologue and final products use variant 1) */
   int32_t record_trace;    /* 1: keep the per-pass Shat / shift history (get_trace) */
   int32_t shift;           /* 1: dynamic shifts (dashSVD); 0: alpha = 0 (Alg. 1 form) */
   int32_t gather_bf16;     /* precision form only: 1 stores the gathered operands Q and Y
@@ -146,9 +148,11 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
 int dashsvd_get_trace(dashsvd_handle h, double* out, int64_t cap, int64_t* count, int* l);
 
 /* The SpMM autotuner's measurements from the last run that tuned (HOST
- * buffer of at least 40 floats): ms[10 * product + variant] = best time of that
+ * buffer of at least 50 floats): ms[10 * product + variant] = best time of that
  * variant in ms (0 = not timed), products 0: A Q, 1: A^T Y - alpha Q (FP32),
- * 2, 3: the same with BF16 gathers. */
+ * 2, 3: the same with BF16 gathers, 4 (variant slot 0): the fused pass product
+ * of dashsvd_spmm_fused. The run uses the fused product when it beats the best
+ * A Q plus the best A^T Y - alpha Q (dashsvd_info.spmm_variant bit 16). */
 int dashsvd_get_tuning(dashsvd_handle h, float* ms, int64_t cap);
 
 /* ---- learned form --------------------------------------------------------
@@ -241,6 +245,16 @@ int dashsvd_spmm(dashsvd_handle h, const dashsvd_csr* A, const float* X, int64_t
 int dashsvd_spmm_shift(dashsvd_handle h, const dashsvd_csr* At, const float* Y, int64_t ldy,
                        int l, const double* alpha, const float* Q, int64_t ldq, float* Z,
                        int64_t ldz, int variant);
+
+/* Both products of a pass in one read of A (Alg. 5 step 4, fused):
+ * Z = A^T (A Q) - alpha Q with A the m x n CSR (not its transpose), Q and Z
+ * n x ld (ld % 4 == 0, ld >= l). Z is first set to -alpha Q (alpha a DEVICE
+ * pointer to one double, or NULL for 0); then each row i of A gathers
+ * y_i = sum_j a_ij q_j and adds a_ij y_i into row j of Z with atomic adds, so
+ * Y is never stored and the summation order of Z is the hardware's
+ * (reproducible to rounding only). Columns l .. ld-1 of Z are set to 0. */
+int dashsvd_spmm_fused(dashsvd_handle h, const dashsvd_csr* A, const float* Q, int64_t ldq, int l,
+                       const double* alpha, float* Z, int64_t ldz);
 
 /* Precision-form sparse products with a BF16 dense operand (row-major, ld
  * in elements, ld % 4 == 0): Y = A X with Y in BF16 (y_bf16 = 1) or FP32, or

@@ -40,7 +40,7 @@ EXPORTS = (
     "dashsvd_gram_bf16x3",
     "dashsvd_project", "dashsvd_project_bf16x3", "dashsvd_eigsvd", "dashsvd_gram_noalloc",
     "dashsvd_mlp_features", "dashsvd_mlp_forward", "dashsvd_mlp_loss_grad", "dashsvd_mlp_adam",
-    "dashsvd_get_tuning",
+    "dashsvd_get_tuning", "dashsvd_spmm_fused",
 )
 MLP_PARAMS = 1218
 MLP_IN = 16
@@ -99,6 +99,7 @@ def _load():
         "dashsvd_gram_noalloc": (I, [P, I64, I, I64, P, I64, P]),
         "dashsvd_mlp_features": (I, [P, P, I64, I, I, I, D, P]),
         "dashsvd_get_tuning": (I, [P, P, I64]),
+        "dashsvd_spmm_fused": (I, [P, P, P, I64, I, P, P, I64]),
         "dashsvd_mlp_forward": (I, [P, P, P, I64, P]),
         "dashsvd_mlp_loss_grad": (I, [P, P, P, P, P, I64, P, P]),
         "dashsvd_mlp_adam": (I, [P, P, P, P, P, I, C.c_float, C.c_float, C.c_float, C.c_float]),
@@ -140,6 +141,7 @@ dashsvd_eigsvd = _export("dashsvd_eigsvd")
 dashsvd_gram_noalloc = _export("dashsvd_gram_noalloc")
 dashsvd_mlp_features = _export("dashsvd_mlp_features")
 dashsvd_get_tuning = _export("dashsvd_get_tuning")
+dashsvd_spmm_fused = _export("dashsvd_spmm_fused")
 dashsvd_mlp_forward = _export("dashsvd_mlp_forward")
 dashsvd_mlp_loss_grad = _export("dashsvd_mlp_loss_grad")
 dashsvd_mlp_adam = _export("dashsvd_mlp_adam")
@@ -344,12 +346,22 @@ class Handle:
         return out
 
     def tuning(self):
-        """The autotuner's last measurements: (4 products x 10 variants) ms, 0 = not timed."""
+        """The autotuner's last measurements: (5 products x 10 variants) ms, 0 = not timed."""
         import numpy as np
 
-        buf = np.zeros(40, dtype=np.float32)
+        buf = np.zeros(50, dtype=np.float32)
         check(dashsvd_get_tuning(self.h, buf.ctypes.data, buf.size), "dashsvd_get_tuning")
-        return buf.reshape(4, 10)
+        return buf.reshape(5, 10)
+
+    def spmm_fused(self, A: CsrDevice, Q, l: int, alpha_dev=None, out=None):
+        """Z = A^T (A Q) - alpha Q in one read of A (atomic scatter)."""
+        import torch
+
+        out = torch.empty((A.n, Q.shape[1]), dtype=torch.float32, device=Q.device) if out is None else out
+        check(dashsvd_spmm_fused(self.h, C.byref(A.struct()), Q.data_ptr(), Q.stride(0), l,
+                                 alpha_dev.data_ptr() if alpha_dev is not None else None, out.data_ptr(),
+                                 out.stride(0)), "dashsvd_spmm_fused")
+        return out
 
     # -- learned form ------------------------------------------------------------
     def load_mlp(self, weights):

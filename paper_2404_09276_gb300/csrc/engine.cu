@@ -104,9 +104,11 @@ struct dashsvd_handle_s {
     const void *rowptr, *colidx;
     int64_t m, n, nnz;
     int l, form, gather, var_fwd32, var_bwd32, var_fwd, var_bwd;
+    bool fused;
   };
   std::vector<Tune> tuned;
-  float tune_ms[4][10] = {};  // last autotuning: best time per (product, variant), ms; 0 = not timed
+  float tune_ms[5][10] = {};  // last autotuning: best time per (product, variant), ms; 0 = not timed
+                             // (product 4, variant 0: the fused pass product)
 };
 
 namespace {
@@ -139,6 +141,7 @@ struct RunPlan {
   float *Uw, *Vw, *S;  // outputs on the working side
   int var_fwd, var_bwd;      // SpMM variants of the pass (BF16 operands in the precision form)
   int var_fwd32, var_bwd32;  // FP32 variants (prologue, final, plain form)
+  bool fused = false;        // pass product as one fused A^T (A Q) - alpha Q (FP32 gathers only)
   SpmmPart part_fwd, part_bwd;
   SpmmScratch scr;
 };
@@ -231,6 +234,10 @@ cudaError_t launch_pass(dashsvd_handle h, const RunPlan& p, unsigned long long c
     if ((e = launch_spmm_bf16(p.AwT, p.part_bwd, h->Y.p, p.ld, p.l, h->Z.p, false, p.ld, &ctl->alpha, h->Qb.p, p.ld,
                               p.var_bwd, p.scr, h->num_sms, st)) != cudaSuccess)
       return e;
+  } else if (p.fused) {  // one read of A: Z = A^T (A Q) - alpha Q, Y never stored
+    if ((e = launch_spmm_fused(p.Aw, as<float>(h->Q), p.ld, p.l, &ctl->alpha, as<float>(h->Z), p.ld, h->num_sms,
+                               st)) != cudaSuccess)
+      return e;
   } else {
     if ((e = launch_spmm(p.Aw, p.part_fwd, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld, nullptr, nullptr, 0,
                          p.var_fwd, p.scr, h->num_sms, st, as<int>(h->errw))) != cudaSuccess)
@@ -322,6 +329,7 @@ constexpr int kSpmmVariants = 10;  // 0-5: split (warp per row, merge path) x 3 
                                    // 6, 7: merge path with bulk-copy (TMA) staging (FP32 operands);
                                    // 8, 9: merge path over column slabs of 32 (FP32 operands)
 constexpr int kSpmmVariantsBf16 = 6;
+constexpr int kSpmmFused = 10;  // options.spmm_variant value that forces the fused pass product
 
 // Time every SpMM variant on this matrix (after one warm-up launch each) for
 // both products of a pass, with FP32 operands and, with BF16 gathers, with
@@ -335,6 +343,7 @@ int autotune_spmm(dashsvd_handle h, RunPlan& p, const dashsvd_csr& A) {
       p.var_bwd32 = t.var_bwd32;
       p.var_fwd = t.var_fwd;
       p.var_bwd = t.var_bwd;
+      p.fused = t.fused;
       return DASHSVD_OK;
     }
   cudaStream_t st = h->stream;
@@ -399,6 +408,25 @@ int autotune_spmm(dashsvd_handle h, RunPlan& p, const dashsvd_csr& A) {
       }
     }
   }
+  // the fused pass product against the two tuned products (FP32 gathers only)
+  p.fused = false;
+  if (err == cudaSuccess && !bf16_gathers(h)) {
+    float tf = 3.4e38f;
+    for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
+      err = launch_spmm_fused(p.Aw, as<float>(h->Q), p.ld, p.l, &ctl->alpha, as<float>(h->Z), p.ld, h->num_sms, st);
+      if (err == cudaSuccess) err = cudaEventRecord(e0, st);
+      if (err == cudaSuccess)
+        err = launch_spmm_fused(p.Aw, as<float>(h->Q), p.ld, p.l, &ctl->alpha, as<float>(h->Z), p.ld, h->num_sms, st);
+      if (err == cudaSuccess) err = cudaEventRecord(e1, st);
+      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+      tf = std::min(tf, ms);
+      if (rep == 0 && tf > 1.5f * (best[0] + best[1])) break;  // far behind: no re-timing
+    }
+    h->tune_ms[4][0] = tf;
+    p.fused = err == cudaSuccess && tf < best[0] + best[1];
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   DS_CUDA(err);
@@ -407,8 +435,7 @@ int autotune_spmm(dashsvd_handle h, RunPlan& p, const dashsvd_csr& A) {
   p.var_fwd = bf16_gathers(h) ? arg[2] : arg[0];
   p.var_bwd = bf16_gathers(h) ? arg[3] : arg[1];
   h->tuned.push_back({A.rowptr, A.colidx, A.m, A.n, A.nnz, p.l, h->opt.form, h->opt.gather_bf16, p.var_fwd32,
-                      p.var_bwd32, p.var_fwd,
-                      p.var_bwd});
+                      p.var_bwd32, p.var_fwd, p.var_bwd, p.fused});
   return DASHSVD_OK;
 }
 
@@ -463,7 +490,7 @@ int dashsvd_create(dashsvd_handle* out, const dashsvd_options* opt, void* cuda_s
   else
     dashsvd_options_init(&h->opt);
   if ((h->opt.alpha_prev_mode != 0 && h->opt.alpha_prev_mode != 1) || h->opt.spmm_variant < -1 ||
-      h->opt.spmm_variant >= kSpmmVariants) {
+      h->opt.spmm_variant > kSpmmFused) {
     delete h;
     return DASHSVD_EINVAL;
   }
@@ -552,9 +579,17 @@ int dashsvd_mlp_adam(dashsvd_handle h, float* W, const float* grad, float* m, fl
 }
 
 int dashsvd_get_tuning(dashsvd_handle h, float* ms, int64_t cap) {
-  if (!h || !ms || cap < 40) return DASHSVD_EINVAL;
-  for (int p = 0; p < 4; ++p)
+  if (!h || !ms || cap < 50) return DASHSVD_EINVAL;
+  for (int p = 0; p < 5; ++p)
     for (int v = 0; v < 10; ++v) ms[p * 10 + v] = h->tune_ms[p][v];
+  return DASHSVD_OK;
+}
+
+int dashsvd_spmm_fused(dashsvd_handle h, const dashsvd_csr* A, const float* Q, int64_t ldq, int l,
+                       const double* alpha, float* Z, int64_t ldz) {
+  if (!h || !csr_ok(A) || !Q || !Z || l < 1 || l > DASHSVD_MAX_L) return DASHSVD_EINVAL;
+  if (ldq < l || ldz < l || ldq % 4 || ldz % 4 || !aligned16(Q) || !aligned16(Z)) return DASHSVD_EINVAL;
+  DS_CUDA(launch_spmm_fused(*A, Q, ldq, l, alpha, Z, ldz, h->num_sms, h->stream));
   return DASHSVD_OK;
 }
 
@@ -651,8 +686,10 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
   p.part_bwd.seg_row = as<int32_t>(h->seg_bwd);
   p.part_bwd.seg_nnz = p.part_bwd.seg_row + p.part_bwd.segments + 1;
   const int forced = h->opt.spmm_variant;
-  p.var_fwd = p.var_fwd32 = forced >= 0 ? forced : 1;
-  p.var_bwd = p.var_bwd32 = forced >= 0 ? forced : 1;
+  // a forced variant 10 means the fused pass product (the other products use variant 1)
+  p.var_fwd = p.var_fwd32 = forced >= 0 && forced < kSpmmVariants ? forced : 1;
+  p.var_bwd = p.var_bwd32 = forced >= 0 && forced < kSpmmVariants ? forced : 1;
+  p.fused = forced == kSpmmFused;
 
   cudaStream_t st = h->stream;
   DS_CUDA(launch_csr_transpose(*A, as<int32_t>(h->rowptr_b), as<int32_t>(h->col_b), as<float>(h->val_b),
@@ -678,7 +715,7 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
     key.shift = h->opt.shift;
     key.record_trace = h->opt.record_trace;
     key.var_fwd = p.var_fwd | (p.var_fwd32 << 8);
-    key.var_bwd = p.var_bwd | (p.var_bwd32 << 8);
+    key.var_bwd = p.var_bwd | (p.var_bwd32 << 8) | ((int)p.fused << 16);
     key.form = h->opt.form;
     key.gather = h->opt.gather_bf16;
     key.learned = h->opt.learned;
@@ -710,7 +747,7 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
     info->passes = hc.pass;
     info->status = status;
     info->transposed = tr ? 1 : 0;
-    info->spmm_variant = p.var_fwd | (p.var_bwd << 8);
+    info->spmm_variant = p.var_fwd | (p.var_bwd << 8) | ((int)p.fused << 16);
     info->alpha = hc.alpha;
     info->pve_ratio = hc.ratio;
     int64_t ws = 0;

@@ -87,6 +87,9 @@ cudaError_t launch_spmm(const dashsvd_csr& A, const SpmmPart& part, const float*
                         int64_t ldy, const double* alpha, const float* Q, int64_t ldq, int variant,
                         const SpmmScratch& scr, int num_sms, cudaStream_t st, int* err = nullptr);
 // BF16 dense operand (and BF16 Q): Y in BF16 (y_bf16) or FP32
+// Fused pass product Z = A^T (A Q) - alpha Q (one read of A, atomic scatter into Z).
+cudaError_t launch_spmm_fused(const dashsvd_csr& A, const float* Q, int64_t ldq, int l, const double* alpha, float* Z,
+                              int64_t ldz, int num_sms, cudaStream_t st);
 cudaError_t launch_spmm_bf16(const dashsvd_csr& A, const SpmmPart& part, const void* X, int64_t ldx, int l, void* Y,
                              bool y_bf16, int64_t ldy, const double* alpha, const void* Q, int64_t ldq, int variant,
                              const SpmmScratch& scr, int num_sms, cudaStream_t st);

@@ -149,6 +149,30 @@ def test_spmm_shift_matches_fp64(ds, h, name, variant):
     assert np.all(Z[:, l:] == 0.0)
 
 
+@pytest.mark.parametrize("name", ["cfg1x0.1", "social", "mixed"])
+@pytest.mark.parametrize("l", [7, 30, 150])
+def test_spmm_fused_matches_fp64(ds, h, name, l):
+    """Z = A^T (A Q) - alpha Q in one read of A: y_i in FP32 registers, then
+    atomic FP32 adds into Z. Bound: both sums are FP32 sums of at most K terms
+    of the absolute-value products."""
+    import torch
+
+    A = MATRICES[name]()
+    ld = ds.ld_for(l)
+    rng = np.random.default_rng(3)
+    Q = _padded(rng.standard_normal((A.n, l)).astype(np.float32), ld)  # NaN padding must be ignored
+    alpha = 0.37
+    ad = torch.tensor([alpha], dtype=torch.float64, device="cuda")
+    Z = _np(h.spmm_fused(ds.CsrDevice.from_host(A), _t(Q), l, ad))
+    As = A.to_scipy(np.float64)
+    Q64 = Q[:, :l].astype(np.float64)
+    ref = As.T @ (As @ Q64) - np.float32(alpha) * Q64
+    bound = abs(As.T) @ (abs(As) @ np.abs(Q64)) + alpha * np.abs(Q64)
+    K = int(np.diff(A.rowptr).max()) + int(np.bincount(A.colidx, minlength=A.n).max()) + 4
+    assert np.all(np.abs(Z[:, :l] - ref) <= K * EPS32 * bound + 1e-30)
+    assert np.all(Z[:, l:] == 0.0)
+
+
 @pytest.mark.parametrize("name", ["social", "mixed"])
 @pytest.mark.parametrize("variant", [0, 1, 3, 5])
 def test_spmm_bf16_matches_fp64(ds, h, name, variant):
