@@ -114,7 +114,10 @@ typedef struct {
   double pve_ratio;     /* last surrogate PVE ratio (Alg. 5 step 5 left-hand side) */
   int64_t workspace_bytes; /* device workspace held by the handle */
   int32_t eig_sweeps;   /* Jacobi sweeps of the last eigensolve */
-  int32_t reserved[5];
+  int32_t setup_reused; /* 1: the CSR of the transpose and the merge-path partitions were
+                           kept from the previous run (same arrays, sizes and 64-bit
+                           content fingerprint); 0: rebuilt */
+  int32_t reserved[4];
 } dashsvd_info;
 
 /* Fill *opt with defaults: plain form, no MLP, seed 0x5EED, alpha_prev_mode 0,
@@ -136,7 +139,12 @@ int dashsvd_destroy(dashsvd_handle h);
  * Outputs (device, caller-owned): U m x k row-major, S k values (descending),
  * V n x k row-major. Returns DASHSVD_OK when the PVE test stopped the loop,
  * DASHSVD_MAX_PASSES when p_max passes ran (or pve_tol <= 0), else an error.
- * `info` (host pointer, may be NULL) receives run statistics. */
+ * `info` (host pointer, may be NULL) receives run statistics.
+ * Setup: the CSR of the transpose and the merge-path partitions are built on
+ * the first run and kept while later runs pass the same arrays with the same
+ * sizes and the same 64-bit fingerprint of their contents (computed on the
+ * device every run, then read by the host); any change rebuilds them.
+ * Step-level SpMM calls on the handle also drop them. */
 int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_passes,
                 double pve_tol, float* U, float* S, float* V, dashsvd_info* info);
 

@@ -66,7 +66,8 @@ class dashsvd_info(C.Structure):
     _fields_ = [
         ("passes", C.c_int32), ("status", C.c_int32), ("transposed", C.c_int32),
         ("spmm_variant", C.c_int32), ("alpha", C.c_double), ("pve_ratio", C.c_double),
-        ("workspace_bytes", C.c_int64), ("eig_sweeps", C.c_int32), ("reserved", C.c_int32 * 5),
+        ("workspace_bytes", C.c_int64), ("eig_sweeps", C.c_int32), ("setup_reused", C.c_int32),
+        ("reserved", C.c_int32 * 4),
     ]
 
 

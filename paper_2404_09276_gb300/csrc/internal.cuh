@@ -67,6 +67,9 @@ cudaError_t launch_csr_transpose(const dashsvd_csr& A, int32_t* rowptr_t, int32_
                                  float* val_t, int32_t* cursor, int32_t* scan_tmp,
                                  cudaStream_t st);
 size_t scan_tmp_ints(int64_t n);
+// 64-bit order-independent fingerprint of the three CSR arrays (m, n, nnz are
+// compared separately), to recognize a matrix that has not changed.
+cudaError_t launch_fingerprint(const dashsvd_csr& A, unsigned long long* out, int num_sms, cudaStream_t st);
 
 // SpMM Y = A X (alpha == nullptr) or Y = A X - alpha Q.
 struct SpmmPart {          // merge-path partition of one sparse matrix

@@ -251,14 +251,24 @@ __global__ void __launch_bounds__(kReplayWarps * 32) eigvec_replay_kernel(EigWor
       for (int t = t1 - 1; t >= t0; --t) {
         const int step = t % (N - 1);
         const float2* lgt = lg + (t - t0) * P;
-        for (int i = lane; i < P; i += 32) {
-          const float2 cs = lgt[i];
-          if (cs.y != 0.f) {
-            int p, q;
-            rr_pair_fast(i, step, N - 1, p, q);
-            const float xp = x[p], xq = x[q];
-            x[p] = cs.x * xp + cs.y * xq;
-            x[q] = -cs.y * xp + cs.x * xq;
+        // the pairs of a step are disjoint: load all of this lane's pairs
+        // (up to 4) before any store, so their latencies overlap
+        float2 cs[4];
+        int pp[4], qq[4];
+        float xp[4], xq[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = lane + 32 * u;
+          cs[u] = i < P ? lgt[i] : make_float2(1.f, 0.f);
+          rr_pair_fast(i < P ? i : 0, step, N - 1, pp[u], qq[u]);
+          xp[u] = x[pp[u]];
+          xq[u] = x[qq[u]];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (cs[u].y != 0.f) {
+            x[pp[u]] = cs[u].x * xp[u] + cs[u].y * xq[u];
+            x[qq[u]] = -cs[u].y * xp[u] + cs[u].x * xq[u];
           }
         }
         __syncwarp();

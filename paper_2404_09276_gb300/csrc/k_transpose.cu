@@ -110,6 +110,32 @@ __global__ void scatter_kernel(const int32_t* __restrict__ rowptr, const int32_t
   }
 }
 
+// SplitMix64's output function (Steele, Lea and Flood, OOPSLA 2014): a
+// bijective 64-bit mix, so that equal inputs at different positions differ.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+// Order-independent 64-bit fingerprint of a CSR matrix: the wrapping sum of
+// mixed (position, value) words of rowptr, colidx and the bit patterns of val.
+__global__ void fingerprint_kernel(const int32_t* __restrict__ rowptr, int64_t m, const int32_t* __restrict__ col,
+                                   const float* __restrict__ val, int64_t nnz, unsigned long long* __restrict__ out) {
+  unsigned long long acc = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += stride) {
+    const unsigned long long pos = (unsigned long long)e << 2;
+    acc += mix64(pos ^ ((unsigned long long)(uint32_t)col[e] << 34) ^ 0x1ull);
+    acc += mix64(pos ^ ((unsigned long long)__float_as_uint(val[e]) << 34) ^ 0x2ull);
+  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= m; i += stride)
+    acc += mix64(((unsigned long long)i << 2) ^ ((unsigned long long)(uint32_t)rowptr[i] << 34) ^ 0x3ull);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
 }  // namespace
 
 size_t scan_tmp_ints(int64_t n) { return (size_t)ds_ceil_div(n, kScanTile) + 1; }
@@ -144,4 +170,13 @@ cudaError_t launch_csr_transpose(const dashsvd_csr& A, int32_t* rowptr_t, int32_
   return cudaGetLastError();
 }
 
+}  // namespace dsvd
+
+namespace dsvd {
+cudaError_t launch_fingerprint(const dashsvd_csr& A, unsigned long long* out, int num_sms, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  fingerprint_kernel<<<(unsigned)(num_sms * 4), 256, 0, st>>>(A.rowptr, A.m, A.colidx, A.val, A.nnz, out);
+  return cudaGetLastError();
+}
 }  // namespace dsvd
