@@ -36,8 +36,8 @@ constexpr int kJacThreads = 1024;
 constexpr int kMaxN = kMaxL;  // N <= 256
 constexpr float kEps32 = 1.1920929e-07f;
 // Jacobi skip threshold (relative, |G_pq| <= tol sqrt(G_pp G_qq)) when the
-// result is refined in FP64 afterwards: two refinement steps take an
-// off-diagonal residue of 1e-4 to below 1e-15
+// result is refined in FP64 afterwards: two quadratically convergent
+// refinement steps take an off-diagonal residue of 1e-4 to FP64 rounding
 constexpr float kRefinedJacobiTol = 1e-4f;
 
 

@@ -104,13 +104,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
           const int kc = item / L32, m = item - kc * L32;
           uint32_t ph4[4], pl4[4];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            __nv_bfloat16 h0, l0, h1, l1;
-            tc::split_bf16(cur[i][2 * j], h0, l0);
-            tc::split_bf16(cur[i][2 * j + 1], h1, l1);
-            ph4[j] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-            pl4[j] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-          }
+          for (int j = 0; j < 4; ++j) tc::split_bf16x2(cur[i][2 * j], cur[i][2 * j + 1], ph4[j], pl4[j]);
           const uint32_t off = tc::sw128_chunk_offset(m, kc);
           *reinterpret_cast<uint4*>(hi + off) = make_uint4(ph4[0], ph4[1], ph4[2], ph4[3]);
           *reinterpret_cast<uint4*>(lo + off) = make_uint4(pl4[0], pl4[1], pl4[2], pl4[3]);

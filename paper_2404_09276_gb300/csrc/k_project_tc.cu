@@ -162,13 +162,7 @@ __global__ void __launch_bounds__(kThreadsP, 1) project_tc_kernel(ProjArgs pa) {
         const int r = item >> 3, kc = item & 7;
         uint32_t h[4], o[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          __nv_bfloat16 h0, l0, h1, l1;
-          tc::split_bf16(cur[i][2 * j], h0, l0);
-          tc::split_bf16(cur[i][2 * j + 1], h1, l1);
-          h[j] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-          o[j] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-        }
+        for (int j = 0; j < 4; ++j) tc::split_bf16x2(cur[i][2 * j], cur[i][2 * j + 1], h[j], o[j]);
         const uint32_t off = tc::sw128_chunk_offset(r, kc);
         *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
         *reinterpret_cast<uint4*>(lo + off) = make_uint4(o[0], o[1], o[2], o[3]);

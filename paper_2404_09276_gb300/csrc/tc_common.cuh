@@ -132,6 +132,15 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bflo
   lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
+// The same split for two values at once, packed as the K-major operand tiles
+// hold them (first value in the low 16 bits): one paired conversion per part.
+__device__ __forceinline__ void split_bf16x2(float a, float b, uint32_t& hi2, uint32_t& lo2) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  const __nv_bfloat162 o = __floats2bfloat162_rn(a - __low2float(h), b - __high2float(h));
+  hi2 = *reinterpret_cast<const uint32_t*>(&h);
+  lo2 = *reinterpret_cast<const uint32_t*>(&o);
+}
+
 // Byte offset of the 16-byte chunk holding elements [8c, 8c + 8) of row r in a
 // K-major 128-byte-swizzled tile (64 elements per row).
 __device__ __forceinline__ uint32_t sw128_chunk_offset(int r, int c) {
