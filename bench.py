@@ -418,6 +418,35 @@ def _measure_form(form, args, ds, torch, A, Ad, prm, stream, flush, barrier, wor
             "bytes": {"spmm_fwd": bytes_fwd, "spmm_bwd": bytes_bwd}}
 
 
+def _git_blob_sha1(path):
+    """The git blob id of a file (sha1 of "blob <size>\\0" + contents)."""
+    import hashlib
+
+    data = open(path, "rb").read()
+    return hashlib.sha1(b"blob %d\0" % len(data) + data).hexdigest()
+
+
+def _traffic(kernel, variant):
+    """DRAM bytes per launch of the dominant kernel from a committed ncu summary
+    (`traffic_per_launch:` lines under profiles/), or None when there is none or
+    the kernel's source has changed since the counters were taken."""
+    srcs = [os.path.join(ROOT, "paper_2404_09276_gb300", "csrc", f) for f in ("k_spmm.cuh", "k_spmm_f32.cu")]
+    if not all(os.path.exists(p) for p in srcs):
+        return None
+    sha = "+".join(_git_blob_sha1(p)[:12] for p in srcs)
+    pdir = os.path.join(ROOT, "profiles")
+    for fn in sorted(os.listdir(pdir)) if os.path.isdir(pdir) else []:
+        if not fn.endswith((".md", ".txt")):
+            continue
+        for line in open(os.path.join(pdir, fn)):
+            if not line.startswith("traffic_per_launch:"):
+                continue
+            kv = dict(x.split("=", 1) for x in line.split(":", 1)[1].split())
+            if kv.get("kernel") == kernel and int(kv.get("variant", -1)) == variant and kv.get("source") == sha:
+                return int(kv["bytes"])
+    return None
+
+
 def _roofline(r, A, l, pk):
     kt, per_run = r["kernels_s"], r["kernel_s_per_run"]
     # the dominant single kernel: "eig" is a chain of 3 (plain) or 14 (precision) small
@@ -426,8 +455,10 @@ def _roofline(r, A, l, pk):
     fp32_peak = NUM_SMS_GB300 * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     if dom in ("spmm_fwd", "spmm_bwd"):
         gbs = r["bytes"][dom] / kt[dom] / 1e9
-        return {"kernel": dom, "bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": gbs / pk["hbm_gbs"], "traffic": None, "peak_source": pk["source"] + " HBM copy bandwidth"}
+        var = r["spmm"]["variants"][0 if dom == "spmm_fwd" else 1]
+        return {"kernel": dom, "variant": var, "bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": gbs / pk["hbm_gbs"], "traffic": _traffic(dom, var),
+                "peak_source": pk["source"] + " HBM copy bandwidth (burst: the kernel is timed alone)"}
     if dom in ("gram", "project") and r["form"] == "plain":  # FP32 SIMT
         tf = 2 * A.n * l * l / kt[dom] / 1e12
         return {"kernel": dom, "bound": "alu", "achieved": tf, "peak": fp32_peak, "unit": "TFLOP/s",

@@ -95,7 +95,10 @@ typedef struct {
                               dashsvd_spmm_fused for the power-iteration passes (the
                               prologue and final products use variant 1) */
   int32_t record_trace;    /* 1: keep the per-pass Shat / shift history (get_trace) */
-  int32_t shift;           /* 1: dynamic shifts (dashSVD); 0: alpha = 0 (Alg. 1 form) */
+  int32_t shift;           /* 1: dynamic shifts (dashSVD, Alg. 5 step 6); 0: alpha = 0 (the
+                              basic randomized SVD, Alg. 1 form); 2: the shift of the first
+                              pass ((Shat_l + 0) / 2), then kept fixed (the paper's Alg. 2*
+                              comparison of Sec. 4, Fig. 1); the learned form needs 1 */
   int32_t gather_bf16;     /* precision form only: 1 stores the gathered operands Q and Y
                               of the power-iteration products (Alg. 5 step 4) in BF16 (half
                               the gather bytes; the PVE surrogate then settles near the

@@ -126,7 +126,7 @@ def dashsvd(
     tol: float,
     seed: int,
     alpha_prev_mode: int = 0,
-    shift: bool = True,
+    shift=True,
     keep_q: bool = False,
     Omega: np.ndarray | None = None,
     policy=None,
@@ -136,7 +136,8 @@ def dashsvd(
     ``A`` is a scipy sparse matrix (or dense array). ``tol <= 0`` disables the
     stop test, which gives the fixed-p dashSVD of Alg. 4. ``shift=False`` keeps
     alpha = 0, which is the basic randomized SVD with eigSVD orthonormalization
-    (Alg. 1 in the m >= n form). ``Omega`` overrides the Philox block.
+    (Alg. 1 in the m >= n form); ``shift="fixed"`` takes the first pass's shift
+    (Shat_l / 2) and keeps it (the fixed-shift variant Alg. 2* of Sec. 4). ``Omega`` overrides the Philox block.
     ``policy`` (learned form) maps the features of a pass (``mlp_ref.features``)
     to (f, o_1): the next shift is f times the plain rule's value, clamped to
     [0, that value], and o_1 > 0 stops the run from pass 2 on while the
@@ -182,7 +183,10 @@ def dashsvd(
             break
         alpha_used = alpha
         ratio_prev = ratio
-        if shift:  # step 6 (learned form: a fraction of the same bound)
+        if shift == "fixed":  # Alg. 2*: alpha = sigma_l(A A^T Q) / 2 from the first pass, then fixed
+            if j == 1:
+                alpha = 0.5 * S[l - 1]
+        elif shift:  # step 6 (learned form: a fraction of the same bound)
             bound = 0.5 * (S[l - 1] + alpha) if S[l - 1] > alpha else alpha
             alpha = min(max(f * bound, 0.0), bound) if np.isfinite(f) else bound
         S_prev = S  # step 7

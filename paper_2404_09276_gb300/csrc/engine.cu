@@ -499,7 +499,8 @@ int dashsvd_create(dashsvd_handle* out, const dashsvd_options* opt, void* cuda_s
     h->opt = *opt;
   else
     dashsvd_options_init(&h->opt);
-  if ((h->opt.alpha_prev_mode != 0 && h->opt.alpha_prev_mode != 1) || h->opt.spmm_variant < -1 ||
+  if ((h->opt.alpha_prev_mode != 0 && h->opt.alpha_prev_mode != 1) || h->opt.shift < 0 || h->opt.shift > 2 ||
+      h->opt.spmm_variant < -1 ||
       h->opt.spmm_variant > kSpmmFused) {
     delete h;
     return DASHSVD_EINVAL;
@@ -625,7 +626,7 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
   if (l > mn || l > DASHSVD_MAX_L) return DASHSVD_EINVAL;
   if (h->opt.gather_bf16 && !precision(h)) return DASHSVD_EINVAL;
   if (h->opt.gather_bf16 && h->opt.spmm_variant >= kSpmmVariantsBf16) return DASHSVD_EINVAL;
-  if (h->opt.learned && !h->mlp_loaded) return DASHSVD_EINVAL;
+  if (h->opt.learned && (!h->mlp_loaded || h->opt.shift != 1)) return DASHSVD_EINVAL;
   if ((h->opt.form != DASHSVD_FORM_PLAIN && h->opt.form != DASHSVD_FORM_PRECISION) || h->opt.learned < 0 ||
       h->opt.learned > 1)
     return DASHSVD_ENOTIMPL;

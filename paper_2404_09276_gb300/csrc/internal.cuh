@@ -46,7 +46,7 @@ struct EigArgs {
   int mode;          // EigMode
   int pmax;          // p_max (pass mode)
   int alpha_prev_mode;
-  int shift;         // 1 dynamic shifts, 0 alpha = 0
+  int shift;         // 1 dynamic shifts, 0 alpha = 0, 2 fixed after the first pass (Alg. 2*)
   double tol;        // PVE tolerance (<= 0: no test)
   float* W;          // l x ldw: V S^-1 (sorted, signed)  [final: V_k S_k^-1]
   float* W2;         // final: V_k (l x ldw); eigsvd: V (l x l, ld l)

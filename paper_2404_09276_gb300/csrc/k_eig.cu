@@ -454,9 +454,11 @@ __global__ void __launch_bounds__(kVecWarps * 32) finish_kernel(const T* __restr
       if (!stop && a.tol > 0.0 && j >= 2 && ratio <= kMlpSoftTol * a.tol && o1 > 0.f && !nonfinite) stop = 1;
     }
     double alpha_next = alpha;
-    if (!stop && a.shift) {
+    if (!stop && a.shift == 1) {
       const double bound = mlp_safe_bound(fs.S[l - 1], alpha);
       alpha_next = fmin(fmax(f * bound, 0.0), bound);
+    } else if (!stop && a.shift == 2 && j == 1) {  // Alg. 2*: the shift of the first pass, then fixed
+      alpha_next = mlp_safe_bound(fs.S[l - 1], alpha);
     }
     ctl->pass = j;
     ctl->ratio = ratio;

@@ -1,0 +1,111 @@
+"""The paper's dataset-free experiments, run with the GPU library.
+
+fig1      PVE error against the power parameter p for the basic randomized
+          SVD (Alg. 1, no shift), the fixed-shift variant (Alg. 2*, the first
+          pass's shift kept) and dashSVD's dynamic shifts (Alg. 2/4), k = 100,
+          s = 50, on the paper's two dense test matrices (Sec. 4, Fig. 1):
+          Dense1 = a 1000 x 1000 Gaussian matrix, Dense2 = 1000 x 1000 with
+          sigma_i = 1 / sqrt(i) and random orthogonal factors. Medians over
+          seeds (one matrix and one Omega per seed).
+variance  Spread of the error metrics over repeated runs with different Omega
+          (App. B, Fig. 11: 100 runs of dashSVD per p in {0, 4, 8, 12, 16, 20},
+          k = 100) on a seeded stand-in for the SNAP graph (the social-graph
+          recipe at 100k x 100k).
+
+The metrics (Sec. 4) are computed on the host from the returned U, S, V and
+exact singular values (LAPACK on the dense matrices; for the graph, a long
+FP64-accumulated run of the library itself with a wide sketch):
+  eps_PVE   = max_i |sigma_i^2 - ||A^T u_i||^2| / sigma_{k+1}^2
+  eps_sigma = max_i |sigma_i - s_i| / sigma_i
+  eps_res   = max_i ||A^T u_i - s_i v_i|| / sigma_i
+
+Usage (GPU):
+    python -m paper_2404_09276_gb300.experiments fig1 --seeds 5
+    python -m paper_2404_09276_gb300.experiments variance --runs 100
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ALGS = (("Alg. 1", 0), ("Alg. 2*", 2), ("Alg. 2", 1))
+
+
+def _metrics(As, U, S, V, sigma, k):
+    AtU = np.asarray(As.T @ U[:, :k])
+    cap = np.einsum("ij,ij->j", AtU, AtU)
+    pve = float(np.max(np.abs(sigma[:k] ** 2 - cap)) / sigma[k] ** 2)
+    es = float(np.max(np.abs(sigma[:k] - S[:k]) / sigma[:k]))
+    res = float(np.max(np.linalg.norm(AtU - V[:, :k] * S[None, :k], axis=0) / sigma[:k]))
+    return pve, es, res
+
+
+def _run(ds, Ad, k, s, p, shift, seed):
+    with ds.Handle(shift=shift, seed=seed) as h:
+        U, S, V, info = h.run(Ad, k, s, p, 0.0)
+        f = lambda x: x.cpu().numpy().astype(np.float64)  # noqa: E731
+        return f(U), f(S), f(V)
+
+
+def fig1(ds, seeds, ps, k=100, s=50):
+    import datagen
+
+    out = {}
+    for name in ("Dense1", "Dense2"):
+        rows = {alg: {p: [] for p in ps} for alg, _ in ALGS}
+        for sd in range(seeds):
+            if name == "Dense1":
+                A = np.random.default_rng(2000 + sd).standard_normal((1000, 1000))
+            else:
+                A = datagen.dense_with_spectrum(1000, 1000, 1 / np.sqrt(np.arange(1, 1001)), 2000 + sd)
+            sigma = np.linalg.svd(A, compute_uv=False)
+            Ac = datagen.dense_as_csr(A.astype(np.float32))
+            As = Ac.to_scipy()
+            Ad = ds.CsrDevice.from_host(Ac)
+            for alg, shift in ALGS:
+                for p in ps:
+                    U, S, V = _run(ds, Ad, k, s, p, shift, 0x5EED + sd)
+                    rows[alg][p].append(_metrics(As, U, S, V, sigma, k)[0])
+        out[name] = {alg: {p: float(np.median(v)) for p, v in d.items()} for alg, d in rows.items()}
+    return out
+
+
+def variance(ds, runs, ps, k=100, s=50):
+    import datagen
+
+    A, _ = datagen.make_config(2, scale=0.1)
+    As = A.to_scipy()
+    Ad = ds.CsrDevice.from_host(A)
+    with ds.Handle() as h:  # reference sigma: wide sketch, many passes
+        _, S, _, _ = h.run(Ad, k + 1, 100, 40, 0.0)
+        sigma = S.cpu().numpy().astype(np.float64)
+    res = {}
+    for p in ps:
+        m = np.array([_metrics(As, *_run(ds, Ad, k, s, p, 1, 0x5EED + r), sigma, k) for r in range(runs)])
+        res[p] = {name: {"mean": float(m[:, i].mean()), "std_over_mean": float(m[:, i].std() / m[:, i].mean())}
+                  for i, name in enumerate(("eps_pve", "eps_sigma", "eps_res"))}
+    return {"matrix": f"social-graph recipe {A.m} x {A.n}, nnz {A.nnz}", "runs": runs, "k": k, "by_p": res}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("which", choices=["fig1", "variance"])
+    ap.add_argument("--seeds", type=int, default=5)
+    ap.add_argument("--runs", type=int, default=100)
+    a = ap.parse_args(argv)
+    sys.path.insert(0, os.path.dirname(HERE))
+    import paper_2404_09276_gb300 as ds
+
+    if a.which == "fig1":
+        print(json.dumps(fig1(ds, a.seeds, [0, 1, 2, 3, 4, 6, 8, 10])))
+    else:
+        print(json.dumps(variance(ds, a.runs, [0, 4, 8, 12, 16, 20])))
+
+
+if __name__ == "__main__":
+    main()

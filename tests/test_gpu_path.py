@@ -171,7 +171,8 @@ def test_gather_bf16_needs_precision_form(ds):
 def test_modes_match_oracle(ds):
     A, prm = datagen.make_config(1, scale=0.05)
     k, s = 8, 4
-    for opts, ref_kw in [({"alpha_prev_mode": 1}, {"alpha_prev_mode": 1}), ({"shift": 0}, {"shift": False})]:
+    for opts, ref_kw in [({"alpha_prev_mode": 1}, {"alpha_prev_mode": 1}), ({"shift": 0}, {"shift": False}),
+                         ({"shift": 2}, {"shift": "fixed"})]:
         U, S, V, info, _ = _run(ds, A, k, s, 8, 1e-3, **opts)
         ref = oracle.dashsvd(A.to_scipy(), k, s, p_max=8, tol=1e-3, seed=0x5EED, **ref_kw)
         assert abs(info.passes - ref.passes) <= 1
