@@ -65,6 +65,9 @@ def _args():
     ap.add_argument("--form", default="both", choices=["both", "plain", "precision", "precision_learned"],
                     help="both: time the plain FP32 form, the precision form and (when its validation let "
                          "it ship) the precision form with the learned network; the last is the chosen form")
+    ap.add_argument("--spmm-variant", type=int, default=-1,
+                    help="force one SpMM variant for both products (-1: autotuned; profiling under ncu, whose "
+                         "serialised launches mislead the autotuner)")
     ap.add_argument("--with-bf16-gathers", action="store_true",
                     help="also time the precision form with BF16 gathered operands")
     ap.add_argument("--no-graph", action="store_true",
@@ -280,7 +283,8 @@ def _measure_form(form, args, ds, torch, A, Ad, prm, stream, flush, barrier, wor
     U = torch.empty((A.m, k), dtype=torch.float32, device="cuda")
     S = torch.empty((k,), dtype=torch.float32, device="cuda")
     V = torch.empty((A.n, k), dtype=torch.float32, device="cuda")
-    h = ds.Handle(stream=stream, use_graph=0 if args.no_graph else 1, form=fcode, gather_bf16=gb, learned=learned)
+    h = ds.Handle(stream=stream, use_graph=0 if args.no_graph else 1, form=fcode, gather_bf16=gb, learned=learned,
+                  spmm_variant=args.spmm_variant)
     if learned:
         h.load_mlp(mlp)
     At = h.csr_transpose(Ad)
@@ -324,7 +328,8 @@ def _measure_form(form, args, ds, torch, A, Ad, prm, stream, flush, barrier, wor
     fused = bool((info.spmm_variant >> 16) & 1)
 
     # one untimed run with the per-pass trace (shift, PVE ratio, Jacobi sweeps)
-    with ds.Handle(stream=stream, record_trace=1, form=fcode, gather_bf16=gb, learned=learned) as ht:
+    with ds.Handle(stream=stream, record_trace=1, form=fcode, gather_bf16=gb, learned=learned,
+                   spmm_variant=args.spmm_variant) as ht:
         if learned:
             ht.load_mlp(mlp)
         ht.run(Ad, k, s, p_max, tol_run, U, S, V)
