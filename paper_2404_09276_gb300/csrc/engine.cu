@@ -343,8 +343,8 @@ constexpr int kSpmmFused = 10;  // options.spmm_variant value that forces the fu
 
 // Time every SpMM variant on this matrix (after one warm-up launch each) for
 // both products of a pass, with FP32 operands and, with BF16 gathers, with
-// BF16 operands too; the variants within 30 % of the fastest are timed twice
-// more, and the best time of each decides.
+// BF16 operands too; the variants within 30 % of the fastest are timed four
+// more times, interleaved, and the median of each decides.
 int autotune_spmm(dashsvd_handle h, RunPlan& p, const dashsvd_csr& A) {
   for (const auto& t : h->tuned)
     if (t.rowptr == A.rowptr && t.colidx == A.colidx && t.m == A.m && t.n == A.n && t.nnz == A.nnz && t.l == p.l &&
@@ -401,14 +401,18 @@ int autotune_spmm(dashsvd_handle h, RunPlan& p, const dashsvd_csr& A) {
     float t[kSpmmVariants];
     for (int v = 0; v < nv && err == cudaSuccess; ++v) err = time1(prod, v, &t[v]);
     if (err != cudaSuccess) break;
-    // the close contenders (within 30 % of the fastest) are timed twice more; each keeps its best time
-    float lead = *std::min_element(t, t + nv);
-    for (int rep = 0; rep < 2 && err == cudaSuccess; ++rep)
-      for (int v = 0; v < nv && err == cudaSuccess; ++v) {
-        if (t[v] > 1.3f * lead) continue;
-        float ms = 0.f;
-        err = time1(prod, v, &ms);
-        t[v] = std::min(t[v], ms);
+    // the close contenders (within 30 % of the fastest) are timed four more
+    // times, interleaved; each is then judged by its median of five
+    const float lead = *std::min_element(t, t + nv);
+    float reps[kSpmmVariants][5];
+    for (int v = 0; v < nv; ++v) reps[v][0] = t[v];
+    for (int rep = 1; rep < 5 && err == cudaSuccess; ++rep)
+      for (int v = 0; v < nv && err == cudaSuccess; ++v)
+        if (t[v] <= 1.3f * lead) err = time1(prod, v, &reps[v][rep]);
+    for (int v = 0; v < nv && err == cudaSuccess; ++v)
+      if (t[v] <= 1.3f * lead) {
+        std::sort(reps[v], reps[v] + 5);
+        t[v] = reps[v][2];
       }
     for (int v = 0; v < nv; ++v) {
       h->tune_ms[prod][v] = t[v];
