@@ -461,9 +461,14 @@ def _roofline(r, A, l, pk):
     if dom in ("spmm_fwd", "spmm_bwd"):
         gbs = r["bytes"][dom] / kt[dom] / 1e9
         var = r["spmm"]["variants"][0 if dom == "spmm_fwd" else 1]
+        traffic = _traffic(dom, var)
         return {"kernel": dom, "variant": var, "bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": gbs / pk["hbm_gbs"], "traffic": _traffic(dom, var),
-                "peak_source": pk["source"] + " HBM copy bandwidth (burst: the kernel is timed alone)"}
+                "frac": gbs / pk["hbm_gbs"], "traffic": traffic,
+                "dram_gbs": traffic / kt[dom] / 1e9 if traffic else None,
+                "gathered_gbs": A.nnz * l * 4 / kt[dom] / 1e9,
+                "peak_source": pk["source"] + " HBM copy bandwidth (burst: the kernel is timed alone)",
+                "note": "achieved = compulsory bytes / time; dram_gbs = ncu DRAM bytes / time; gathered_gbs = "
+                        "nnz * l * 4 / time (the rows the gathers request)"}
     if dom in ("gram", "project") and r["form"] == "plain":  # FP32 SIMT
         tf = 2 * A.n * l * l / kt[dom] / 1e12
         return {"kernel": dom, "bound": "alu", "achieved": tf, "peak": fp32_peak, "unit": "TFLOP/s",

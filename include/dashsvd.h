@@ -105,7 +105,17 @@ typedef struct {
                               BF16 rounding level of hub-localized singular vectors, so it
                               suits pve_tol of a few 1e-2 and up); 0 keeps them in FP32.
                               EINVAL in the plain form. */
-  int32_t reserved[6];
+  int32_t pve_mode;        /* 0: the PVE test of Alg. 5 step 5 on the surrogate
+                              Shat + alpha (dashSVD); 1: without the surrogate (the
+                              comparison of Sec. 4.3, Table 4): after each pass the
+                              singular values of B = A Q are computed (one more
+                              A Q product is not needed, the next pass reuses it, but
+                              one more Gram and eigensolve of the m x l block are) and
+                              the criterion of Eq. 19 is applied to them against those
+                              of the pass before (p = 0 for the first pass). EINVAL with
+                              learned or gather_bf16; the fused pass product is not
+                              used (B must be stored). */
+  int32_t reserved[5];
 } dashsvd_options;
 
 typedef struct {

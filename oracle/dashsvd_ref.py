@@ -38,6 +38,11 @@ R6  An eigenvalue at the rounding level of the Gram entries it is made of,
 R8  Each eigenvector column is signed so that its largest-magnitude entry
     (lowest index on ties) is positive; ties in D are ordered by lower index.
 R10 ``p_max`` counts power iterations (loop passes); passes over A = 2p + 2.
+R16 The control without the surrogate (Sec. 4.3, Table 4; the paper gives no
+    listing): Eq. 19 on the singular values of B = A Q taken after each pass's
+    basis update, sigma^(j-1) for j = 1 being those of the basis of step 2
+    (p = 0); the shift update of the pass is made before the test, and on a stop
+    the tested B is the B of step 9. Denominator floored as in R3 (squared).
 """
 from __future__ import annotations
 
@@ -118,6 +123,16 @@ def pve_ratio(S_prev, alpha_prev, S, alpha, k):
     return float(np.max(np.abs(S_prev[:k] + alpha_prev - S[:k] - alpha)) / denom)
 
 
+def direct_pve_ratio(Sd_prev, Sd, k):
+    """max_{i<=k} |s'_i^2 - s_i^2| / max(s_{k+1}^2, floor): Eq. 19 of
+    Sec. 3.2 on singular values s of B = A Q (this pass) and s' (the pass
+    before), with the floor of R3 at the squared scale (reading R16)."""
+    denom = max(Sd[k] ** 2, 64.0 * EPS64 * Sd[0] ** 2)
+    if denom <= 0.0:
+        return np.inf
+    return float(np.max(np.abs(Sd_prev[:k] ** 2 - Sd[:k] ** 2)) / denom)
+
+
 def dashsvd(
     A,
     k: int,
@@ -130,6 +145,7 @@ def dashsvd(
     keep_q: bool = False,
     Omega: np.ndarray | None = None,
     policy=None,
+    pve_mode: str = "surrogate",
 ) -> Result:
     """dashSVD with PVE accuracy control (Alg. 5) in FP64.
 
@@ -142,6 +158,11 @@ def dashsvd(
     to (f, o_1): the next shift is f times the plain rule's value, clamped to
     [0, that value], and o_1 > 0 stops the run from pass 2 on while the
     surrogate ratio is at most 3 tol.
+    ``pve_mode="direct"`` runs the accuracy control without the surrogate
+    (the comparison of Sec. 4.3, Table 4): after each pass the singular values
+    of B = A Q are computed and Eq. 19 is applied to them
+    literally, sigma^(j) against sigma^(j-1), sigma^(0) being those of the
+    basis before the first pass (p = 0); the shift rule is unchanged.
     """
     import scipy.sparse as sp
 
@@ -156,8 +177,14 @@ def dashsvd(
         raise ValueError("need k >= 1, s >= 1 and k + s <= min(m, n)")
     At = A.T.tocsr()
 
+    if pve_mode not in ("surrogate", "direct"):
+        raise ValueError("pve_mode is 'surrogate' or 'direct'")
+    direct = pve_mode == "direct"
+    if direct and policy is not None:
+        raise ValueError("the learned policy works on the surrogate")
     Om = gaussian_block(seed, m, l) if Omega is None else np.asarray(Omega, dtype=np.float64)
     Q, _, _, _ = eigsvd(At @ Om)  # step 2
+    Sd_prev = eigsvd(A @ Q)[1] if direct else None  # sigma^(0): singular values of A Q_0
     alpha = 0.0
     alpha_prev = 0.0
     ratio_prev = 0.0
@@ -171,7 +198,7 @@ def dashsvd(
         Q, S, _, _ = eigsvd(C)
         passes = j
         ratio = pve_ratio(S_prev, alpha_prev, S, alpha, k)
-        stop = tol > 0 and ratio <= tol  # step 5
+        stop = tol > 0 and ratio <= tol and not direct  # step 5
         f = 1.0
         if policy is not None:
             x = mlp_features(S, alpha, ratio, ratio_prev if j > 1 else ratio, j, p_max, tol, k)
@@ -191,6 +218,14 @@ def dashsvd(
             alpha = min(max(f * bound, 0.0), bound) if np.isfinite(f) else bound
         S_prev = S  # step 7
         alpha_prev = alpha_used if alpha_prev_mode == 0 else alpha
+        if direct:  # sigma^(j) of B = A Q against sigma^(j-1)
+            Sd = eigsvd(A @ Q)[1]
+            ratio = direct_pve_ratio(Sd_prev, Sd, k)
+            Sd_prev = Sd
+            if tol > 0 and ratio <= tol:
+                trace.append(PassRecord(j, alpha_used, S, ratio, True, alpha, Q_in))
+                converged = True
+                break
         trace.append(PassRecord(j, alpha_used, S, ratio, False, alpha, Q_in))
 
     B = A @ Q  # step 9

@@ -58,7 +58,7 @@ class dashsvd_options(C.Structure):
         ("form", C.c_int32), ("learned", C.c_int32), ("seed", C.c_uint64),
         ("alpha_prev_mode", C.c_int32), ("use_graph", C.c_int32), ("spmm_variant", C.c_int32),
         ("record_trace", C.c_int32), ("shift", C.c_int32), ("gather_bf16", C.c_int32),
-        ("reserved", C.c_int32 * 6),
+        ("pve_mode", C.c_int32), ("reserved", C.c_int32 * 5),
     ]
 
 
@@ -166,7 +166,10 @@ def check(status: int, what: str = "dashsvd", ok=(DASHSVD_OK,)) -> int:
 def options(**kw) -> dashsvd_options:
     o = dashsvd_options()
     check(dashsvd_options_init(C.byref(o)), "dashsvd_options_init")
+    names = {f[0] for f in o._fields_}
     for k, v in kw.items():
+        if k not in names or k == "reserved":
+            raise TypeError(f"unknown dashsvd option {k!r}")
         setattr(o, k, v)
     return o
 

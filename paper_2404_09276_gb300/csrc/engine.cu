@@ -67,7 +67,7 @@ struct GraphKey {
   double tol;
   float *U, *S, *V;
   uint64_t seed;
-  int alpha_prev_mode, shift, record_trace, var_fwd, var_bwd, form, gather, learned;
+  int alpha_prev_mode, shift, record_trace, var_fwd, var_bwd, form, gather, learned, pve_mode;
   bool operator==(const GraphKey& o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
 };
 
@@ -171,19 +171,22 @@ EigArgs eig_args(dashsvd_handle h, const RunPlan& p, int mode, unsigned long lon
   a.W2 = as<float>(h->W2);
   a.S_out = p.S;
   a.ctl = as<Control>(h->ctl);
-  a.trace = (mode == kModePass && h->opt.record_trace) ? as<double>(h->trace) : nullptr;
+  a.trace = ((mode == kModePass || mode == kModeDirect) && h->opt.record_trace) ? as<double>(h->trace) : nullptr;
   a.cond = cond;
   a.use_cond = cond != 0;
   a.mlp = (mode == kModePass && h->opt.learned) ? as<float>(h->mlpw) : nullptr;
+  a.direct = h->opt.pve_mode == 1;
   return a;
 }
 
 bool precision(dashsvd_handle h) { return h->opt.form == DASHSVD_FORM_PRECISION; }
 // BF16 storage of the gathered operands Q and Y (an option of the precision form)
 bool bf16_gathers(dashsvd_handle h) { return precision(h) && h->opt.gather_bf16; }
+// PVE control on sigma(A Q) of every pass instead of the surrogate
+bool direct_pve(dashsvd_handle h) { return h->opt.pve_mode == 1; }
 
 // Refinement iterations of the precision form's FP64 eigensolve, and the
-// rounding level of its BF16x3 Gram used by the null-column test (R6).
+// rounding level of its BF16x3 Gram, which scales the null-column test of eigSVD.
 constexpr int kRefineIters = 2;
 constexpr double kEpsBf16x3 = 1.52587890625e-05;  // 2^-16
 
@@ -230,13 +233,33 @@ cudaError_t launch_prologue(dashsvd_handle h, const RunPlan& p, unsigned long lo
                        p.var_bwd32, p.scr, h->num_sms, st, as<int>(h->errw))) != cudaSuccess)
     return e;
   if ((e = eigsvd_step(h, p, as<float>(h->Z), p.nw, kModeInit, cond, st)) != cudaSuccess) return e;
-  return project_basis(h, p, st);
+  if ((e = project_basis(h, p, st)) != cudaSuccess) return e;
+  if (!direct_pve(h)) return cudaSuccess;
+  // PVE control without the surrogate: B = A Q_0 (kept in Y for the first
+  // pass) and its singular values, the p = 0 values of the criterion
+  if ((e = launch_spmm(p.Aw, p.part_fwd, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld, nullptr, nullptr, 0,
+                       p.var_fwd, p.scr, h->num_sms, st, as<int>(h->errw))) != cudaSuccess)
+    return e;
+  return eigsvd_step(h, p, as<float>(h->Y), p.mw, kModeDirect, cond, st);
 }
 
 cudaError_t launch_pass(dashsvd_handle h, const RunPlan& p, unsigned long long cond, cudaStream_t st) {
   cudaError_t e;
   const Control* ctl = as<Control>(h->ctl);
   // step 4: Y = A Q; Z = A^T Y - alpha Q; [Q, Shat] = eigSVD(Z)
+  if (direct_pve(h)) {
+    // Y = A Q is already there (the end of the previous pass or the prologue)
+    if ((e = launch_spmm(p.AwT, p.part_bwd, as<float>(h->Y), p.ld, p.l, as<float>(h->Z), p.ld, &ctl->alpha,
+                         as<float>(h->Q), p.ld, p.var_bwd, p.scr, h->num_sms, st, as<int>(h->errw))) != cudaSuccess)
+      return e;
+    if ((e = eigsvd_step(h, p, as<float>(h->Z), p.nw, kModePass, cond, st)) != cudaSuccess) return e;
+    if ((e = project_basis(h, p, st)) != cudaSuccess) return e;
+    // B = A Q of the new basis, its singular values and the stop test
+    if ((e = launch_spmm(p.Aw, p.part_fwd, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld, nullptr, nullptr, 0,
+                         p.var_fwd, p.scr, h->num_sms, st, as<int>(h->errw))) != cudaSuccess)
+      return e;
+    return eigsvd_step(h, p, as<float>(h->Y), p.mw, kModeDirect, cond, st);
+  }
   if (bf16_gathers(h)) {
     if ((e = launch_spmm_bf16(p.Aw, p.part_fwd, h->Qb.p, p.ld, p.l, h->Y.p, true, p.ld, nullptr, nullptr, 0,
                               p.var_fwd, p.scr, h->num_sms, st)) != cudaSuccess)
@@ -263,9 +286,11 @@ cudaError_t launch_pass(dashsvd_handle h, const RunPlan& p, unsigned long long c
 
 cudaError_t launch_final(dashsvd_handle h, const RunPlan& p, cudaStream_t st) {
   cudaError_t e;
-  // step 9: B = A Q (into Y), from the FP32 basis in both forms
-  if ((e = launch_spmm(p.Aw, p.part_fwd, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld, nullptr, nullptr, 0,
-                       p.var_fwd32, p.scr, h->num_sms, st, as<int>(h->errw))) != cudaSuccess)
+  // step 9: B = A Q (into Y), from the FP32 basis in both forms (already
+  // there when the PVE control works on B directly)
+  if (!direct_pve(h) && (e = launch_spmm(p.Aw, p.part_fwd, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld,
+                                         nullptr, nullptr, 0, p.var_fwd32, p.scr, h->num_sms, st,
+                                         as<int>(h->errw))) != cudaSuccess)
     return e;
   // steps 10-11: eigSVD(B); U = B V_k S_k^-1; V = Q V_k
   if ((e = eigsvd_step(h, p, as<float>(h->Y), p.mw, kModeFinal, 0, st)) != cudaSuccess) return e;
@@ -474,6 +499,7 @@ int dashsvd_options_init(dashsvd_options* opt) {
   opt->spmm_variant = -1;
   opt->record_trace = 0;
   opt->shift = 1;
+  opt->pve_mode = 0;
   return DASHSVD_OK;
 }
 
@@ -631,6 +657,9 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
   if (h->opt.gather_bf16 && !precision(h)) return DASHSVD_EINVAL;
   if (h->opt.gather_bf16 && h->opt.spmm_variant >= kSpmmVariantsBf16) return DASHSVD_EINVAL;
   if (h->opt.learned && (!h->mlp_loaded || h->opt.shift != 1)) return DASHSVD_EINVAL;
+  if (h->opt.pve_mode < 0 || h->opt.pve_mode > 1) return DASHSVD_EINVAL;
+  if (direct_pve(h) && (h->opt.learned || h->opt.gather_bf16 || h->opt.spmm_variant == kSpmmFused))
+    return DASHSVD_EINVAL;
   if ((h->opt.form != DASHSVD_FORM_PLAIN && h->opt.form != DASHSVD_FORM_PRECISION) || h->opt.learned < 0 ||
       h->opt.learned > 1)
     return DASHSVD_ENOTIMPL;
@@ -727,6 +756,7 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
     h->setup_valid = true;
   }
   if (forced < 0 && (rc = autotune_spmm(h, p, *A)) != DASHSVD_OK) return rc;
+  if (direct_pve(h)) p.fused = false;  // B = A Q is stored every pass
   DS_CUDA(cudaMemsetAsync(h->errw.p, 0, sizeof(int), st));
 
   if (h->opt.use_graph) {
@@ -749,6 +779,7 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
     key.form = h->opt.form;
     key.gather = h->opt.gather_bf16;
     key.learned = h->opt.learned;
+    key.pve_mode = h->opt.pve_mode;
     if (moved || !h->have_graph || !(key == h->key)) {
       if ((rc = build_graph(h, p)) != DASHSVD_OK) return rc;
       h->key = key;

@@ -25,6 +25,7 @@ struct Control {
   int32_t pad[3];
   double S_prev[kMaxL];  // Shat' (descending)
   double S[kMaxL];       // Shat of the last eigSVD (descending)
+  double Sd_prev[kMaxL];  // direct PVE control: singular values of B = A Q of the pass before
 };
 
 enum : int32_t {
@@ -37,6 +38,7 @@ enum EigMode : int32_t {
   kModeInit = 1,    // Alg. 5 step 2: W = V S^-1, reset alpha, alpha', Shat'
   kModePass = 2,    // Alg. 5 steps 4-7: W = V S^-1, PVE test, shift update
   kModeFinal = 3,   // Alg. 5 steps 10-11: W_U = V_k S_k^-1, W_V = V_k, S_k out
+  kModeDirect = 4,  // PVE control without the surrogate: stop test on sigma(A Q) of this pass
 };
 
 struct EigArgs {
@@ -56,6 +58,7 @@ struct EigArgs {
   unsigned long long cond;  // cudaGraphConditionalHandle (0: none)
   int use_cond;
   const float* mlp;  // learned form: the shift/stop network's parameters (nullptr: plain rule)
+  int direct;        // 1: the stop test runs in kModeDirect on sigma(A Q), not on the surrogate
 };
 
 // ---- launchers (all asynchronous on `st`) --------------------------------

@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(kVecWarps * 32) finish_kernel(const T* __restr
     const bool null = nonfinite || (double)d[c] <= 16.0 * eps_null * wsum;
     const double inv = null ? 0.0 : 1.0 / fs.S[r];
     const bool keep = a.mode != kModeFinal || r < a.k;
-    for (int j = lane; j < l; j += 32) {
+    for (int j = lane; j < l && a.mode != kModeDirect; j += 32) {
       const double v = sg * (double)V[(int64_t)j * l + c];
       a.W[(int64_t)j * a.ldw + r] = keep ? (float)(v * inv) : 0.f;
       if (a.mode == kModeFinal) a.W2[(int64_t)j * a.ldw + r] = keep ? (float)v : 0.f;
@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(kVecWarps * 32) finish_kernel(const T* __restr
     }
   }
   // padding columns of W (and W2) beyond l
-  if (blockIdx.x == 0) {
+  if (blockIdx.x == 0 && a.mode != kModeDirect) {
     const int pad = a.ldw - l;
     for (int idx = tid; idx < l * pad; idx += nt) {
       const int j = idx / pad, r = l + idx - j * pad;
@@ -389,6 +389,7 @@ __global__ void __launch_bounds__(kVecWarps * 32) finish_kernel(const T* __restr
   if (a.mode == kModeInit) {
     for (int r = tid; r < kMaxL; r += nt) {
       ctl->S_prev[r] = 0.0;
+      ctl->Sd_prev[r] = 0.0;
       ctl->S[r] = r < l ? fs.S[r] : 0.0;
     }
     if (tid == 0) {
@@ -402,6 +403,48 @@ __global__ void __launch_bounds__(kVecWarps * 32) finish_kernel(const T* __restr
       ctl->cont = (!nonfinite && a.pmax > 0) ? 1 : 0;
       if (a.use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond, (unsigned)ctl->cont);
     }
+    return;
+  }
+
+  if (a.mode == kModeDirect) {
+    // PVE control without the surrogate (the comparison of Sec. 4.3, Table 4):
+    // Eq. 19 on the singular values of B = A Q after pass j
+    // against those after pass j - 1 (after the prologue, p = 0, for j = 1):
+    // max_i<=k |s'_i^2 - s_i^2| / max(s_{k+1}^2, 64 eps s_1^2) <= tol
+    const int k = a.k;
+    if (ctl->pass == 0) {  // the prologue's B = A Q_0 only seeds s'
+      for (int r = tid; r < l; r += nt) ctl->Sd_prev[r] = fs.S[r];
+      if (tid == 0 && nonfinite) {
+        ctl->status |= kStatusNonFinite;
+        ctl->cont = 0;
+        if (a.use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond, 0u);
+      }
+      return;
+    }
+    double mx = 0.0;
+    for (int i = tid; i < k; i += nt) mx = fmax(mx, fabs(ctl->Sd_prev[i] * ctl->Sd_prev[i] - fs.S[i] * fs.S[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) fs.red[warp] = mx;
+    __syncthreads();
+    if (tid == 0) {
+      double m2 = 0.0;
+      for (int w = 0; w < (nt >> 5); ++w) m2 = fmax(m2, fs.red[w]);
+      const double floor_ = 64.0 * 2.220446049250313e-16 * fs.S[0] * fs.S[0];
+      double denom = fs.S[k] * fs.S[k];
+      if (denom < floor_) denom = floor_;
+      const double ratio = denom > 0.0 ? m2 / denom : INFINITY;
+      const int j = ctl->pass;
+      const int stop = (a.tol > 0.0 && ratio <= a.tol && !nonfinite) ? 1 : 0;
+      ctl->ratio = ratio;
+      ctl->stop = stop;
+      if (nonfinite) ctl->status |= kStatusNonFinite;
+      ctl->cont = (!stop && !nonfinite && j < a.pmax) ? 1 : 0;
+      if (a.trace && j >= 1) a.trace[(int64_t)(j - 1) * (5 + l) + 2] = ratio;
+      if (a.use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond, (unsigned)ctl->cont);
+    }
+    __syncthreads();
+    for (int r = tid; r < l; r += nt) ctl->Sd_prev[r] = fs.S[r];
     return;
   }
 
@@ -446,7 +489,7 @@ __global__ void __launch_bounds__(kVecWarps * 32) finish_kernel(const T* __restr
   if (tid == 0) {
     const double ratio = fs.ratio;
     const int j = ctl->pass + 1;
-    int stop = (a.tol > 0.0 && ratio <= a.tol && !nonfinite) ? 1 : 0;
+    int stop = (!a.direct && a.tol > 0.0 && ratio <= a.tol && !nonfinite) ? 1 : 0;
     double f = 1.0;  // fraction of the safe bound taken as the next shift
     if (a.mlp) {
       const float o0 = fs.out[0], o1 = fs.out[1];

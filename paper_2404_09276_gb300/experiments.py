@@ -7,6 +7,11 @@ fig1      PVE error against the power parameter p for the basic randomized
           Dense1 = a 1000 x 1000 Gaussian matrix, Dense2 = 1000 x 1000 with
           sigma_i = 1 / sqrt(i) and random orthogonal factors. Medians over
           seeds (one matrix and one Omega per seed).
+table4    The accuracy control with the surrogate (Alg. 5) against the control
+          without it (Sec. 4.3, Table 4: the singular values of B = A Q taken
+          every pass, ``pve_mode=1``) at tol = 1e-2 on the seeded stand-ins for
+          the paper's matrices: passes N_p, run time (median of CUDA-event
+          timed runs after a warm-up) and the true eps_PVE, for both forms.
 variance  Spread of the error metrics over repeated runs with different Omega
           (App. B, Fig. 11: 100 runs of dashSVD per p in {0, 4, 8, 12, 16, 20},
           k = 100) on a seeded stand-in for the SNAP graph (the social-graph
@@ -22,6 +27,7 @@ FP64-accumulated run of the library itself with a wide sketch):
 Usage (GPU):
     python -m paper_2404_09276_gb300.experiments fig1 --seeds 5
     python -m paper_2404_09276_gb300.experiments variance --runs 100
+    python -m paper_2404_09276_gb300.experiments table4 --configs 2 3
 """
 from __future__ import annotations
 
@@ -75,6 +81,54 @@ def fig1(ds, seeds, ps, k=100, s=50):
     return out
 
 
+def _reference_sigma(ds, Ad, cfg, k):
+    """sigma_1..sigma_{k+1}: the stored FP64 values for the 1M social graph,
+    else a long run of the library with a wide sketch."""
+    p = os.path.join(os.path.dirname(HERE), "tests", "golden", "social_graph_1m_sigma.txt")
+    if cfg == 2 and os.path.exists(p):
+        return np.loadtxt(p, comments="#"), "FP64 oracle, stored"
+    with ds.Handle() as h:
+        kk = k + 1
+        s = min(100, 256 - kk)
+        _, S, _, _ = h.run(Ad, kk, s, 40, 0.0)
+        return S.cpu().numpy().astype(np.float64), f"library, k={kk} s={s} 40 passes"
+
+
+def table4(ds, cfgs, reps=3):
+    import torch
+
+    import datagen
+
+    rows = []
+    for cfg in cfgs:
+        A, prm = datagen.make_config(cfg)
+        k, s, pmax, tol = prm["k"], prm["s"], prm["p_max"], prm["tol"]
+        Ad = ds.CsrDevice.from_host(A)
+        sigma, src = _reference_sigma(ds, Ad, cfg, k)
+        for form in (ds.DASHSVD_FORM_PLAIN, ds.DASHSVD_FORM_PRECISION):
+            for mode in (0, 1):
+                with ds.Handle(form=form, pve_mode=mode) as h:
+                    st = torch.cuda.current_stream()
+                    h.run(Ad, k, s, pmax, tol)  # setup, tuning and graph build
+                    ts = []
+                    for _ in range(reps):
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(st)
+                        U, S, V, info = h.run(Ad, k, s, pmax, tol)
+                        e1.record(st)
+                        e1.synchronize()
+                        ts.append(e0.elapsed_time(e1))
+                    At = h.csr_transpose(Ad)
+                    cap = (h.spmm(At, U, k).double() ** 2).sum(0).cpu().numpy()
+                    pve = float(np.max(np.abs(sigma[:k] ** 2 - cap)) / sigma[k] ** 2)
+                rows.append({"config": cfg, "matrix": f"{A.m} x {A.n}, nnz {A.nnz}", "k": k, "s": s, "tol": tol,
+                             "form": "plain" if form == ds.DASHSVD_FORM_PLAIN else "precision",
+                             "control": "surrogate" if mode == 0 else "without surrogate",
+                             "passes": info.passes, "status": info.status, "ms": float(np.median(ts)),
+                             "eps_pve": pve, "sigma_ref": src})
+    return rows
+
+
 def variance(ds, runs, ps, k=100, s=50):
     import datagen
 
@@ -94,15 +148,19 @@ def variance(ds, runs, ps, k=100, s=50):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("which", choices=["fig1", "variance"])
+    ap.add_argument("which", choices=["fig1", "variance", "table4"])
     ap.add_argument("--seeds", type=int, default=5)
     ap.add_argument("--runs", type=int, default=100)
+    ap.add_argument("--configs", type=int, nargs="+", default=[2, 3])
     a = ap.parse_args(argv)
     sys.path.insert(0, os.path.dirname(HERE))
     import paper_2404_09276_gb300 as ds
 
     if a.which == "fig1":
         print(json.dumps(fig1(ds, a.seeds, [0, 1, 2, 3, 4, 6, 8, 10])))
+    elif a.which == "table4":
+        for r in table4(ds, a.configs):
+            print(json.dumps(r))
     else:
         print(json.dumps(variance(ds, a.runs, [0, 4, 8, 12, 16, 20])))
 

@@ -151,6 +151,11 @@ def test_load_mlp_validation(ds):
         bad[5] = np.nan
         with pytest.raises(ds.DashSvdError):
             h.load_mlp(bad)
+    with ds.Handle(learned=1, pve_mode=1) as h:  # the policy reads the surrogate
+        h.load_mlp(_const_net(0.0, -40.0))
+        with pytest.raises(ds.DashSvdError) as e:
+            h.run(ds.CsrDevice.from_host(A), 8, 4, 2, 0.0)
+        assert e.value.status == ds.DASHSVD_EINVAL
 
 
 @pytest.mark.parametrize("form", [0, 1])

@@ -264,3 +264,58 @@ def test_setup_kept_while_matrix_unchanged(ds):
     A2 = datagen.Csr(A.m, A.n, A.rowptr, A.colidx, Ad.val.cpu().numpy(), A.name)
     ref = oracle.dashsvd(A2.to_scipy(), k, s, p_max=4, tol=0.0, seed=0x5EED)
     assert np.max(np.abs(S3 - ref.S) / ref.S) < 1e-4
+
+
+# ------------------------------ accuracy control without the surrogate (pve_mode 1)
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_direct_pve_control_matches_oracle(ds, form):
+    """The control of Sec. 4.3's Table 4 comparison (Eq. 19 on sigma(A Q) of
+    every pass) on the 2000 x 1000 recipe: the stop pass within one of the
+    oracle's, the per-pass ratios equal to the oracle's where both ran, and the
+    factors at the oracle's bar when the passes agree."""
+    A, prm = datagen.make_config(1, scale=0.1)
+    k, s = prm["k"], prm["s"]
+    for tol in (1e-2, 1e-3):
+        U, S, V, info, tr = _run(ds, A, k, s, 10, tol, record_trace=1, pve_mode=1, form=form)
+        ref = oracle.dashsvd(A.to_scipy(), k, s, p_max=10, tol=tol, seed=0x5EED, pve_mode="direct")
+        assert abs(info.passes - ref.passes) <= 1
+        assert info.status == (ds.DASHSVD_OK if ref.converged else ds.DASHSVD_MAX_PASSES)
+        got = np.array([r[2] for r in tr])
+        want = np.array([t.ratio for t in ref.trace])
+        n = min(len(got), len(want))
+        np.testing.assert_allclose(got[:n], want[:n], rtol=2e-2, atol=2e-4)
+        assert info.pve_ratio == got[-1]
+        if info.passes == ref.passes:
+            _compare(U, S, V, ref, k, sig_tol=1e-4 if form == 0 else 1e-3, ang_tol=1e-3 if form == 0 else 1e-2)
+
+
+def test_direct_pve_control_without_stop_equals_surrogate_run(ds):
+    """With tol = 0 the two controls run the same iteration (the direct one
+    only adds the Gram and eigensolve of B = A Q per pass)."""
+    A, prm = datagen.make_config(1, scale=0.1)
+    k, s = prm["k"], prm["s"]
+    a = _run(ds, A, k, s, 5, 0.0, pve_mode=1, spmm_variant=1)
+    b = _run(ds, A, k, s, 5, 0.0, pve_mode=0, spmm_variant=1)
+    assert a[3].passes == b[3].passes == 5
+    np.testing.assert_allclose(a[1], b[1], rtol=1e-5)
+    assert abs(a[3].alpha - b[3].alpha) <= 1e-5 * b[3].alpha
+
+
+def test_direct_pve_graph_and_host_loop_agree(ds):
+    A, prm = datagen.make_config(2, scale=0.01)
+    k, s = 16, 8
+    a = _run(ds, A, k, s, 8, 1e-2, use_graph=1, pve_mode=1)
+    b = _run(ds, A, k, s, 8, 1e-2, use_graph=0, pve_mode=1)
+    assert a[3].passes == b[3].passes and a[3].status == b[3].status
+    np.testing.assert_allclose(a[1], b[1], rtol=1e-5)
+
+
+def test_direct_pve_control_argument_checks(ds):
+    A, _ = datagen.make_config(1, scale=0.05)
+    for opts in ({"pve_mode": 2}, {"pve_mode": -1}, {"pve_mode": 1, "spmm_variant": 10},
+                 {"pve_mode": 1, "form": 1, "gather_bf16": 1}):
+        with pytest.raises(ds.DashSvdError) as ei:
+            _run(ds, A, 8, 4, 2, 1e-2, **opts)
+        assert ei.value.status == ds.DASHSVD_EINVAL, opts

@@ -264,6 +264,79 @@ def test_config1_shape_runs_and_meets_tolerance():
     assert metrics.eps_sigma(r.S, sv, prm["k"]) < 0.1
 
 
+# ------------------------------------- accuracy control without the surrogate
+
+
+def _eq19_stop_pass(A, k, s, tol, p_max, seed):
+    """The first pass j >= 1 at which Eq. 19 holds, with sigma^(j) the singular
+    values of A Q from a separate fixed-p run (Alg. 4, tol = 0) for each p = j."""
+    sig = []
+    for p in range(p_max + 1):
+        r = dashsvd(A, k, s, p_max=p, tol=0.0, seed=seed)
+        sig.append(np.linalg.svd(np.asarray(A @ r.Q), compute_uv=False))
+    for j in range(1, p_max + 1):
+        if np.max(np.abs(sig[j][:k] ** 2 - sig[j - 1][:k] ** 2)) / sig[j][k] ** 2 <= tol:
+            return j
+    return None
+
+
+_DIRECT_CASES = {
+    "dense2": lambda: datagen.dense_with_spectrum(200, 150, 1 / np.sqrt(np.arange(1, 151)), 7),
+    "geometric": lambda: datagen.dense_with_spectrum(200, 150, 0.5 ** np.arange(150), 8),
+    "config1": lambda: datagen.make_config(1, scale=0.05)[0].to_scipy(),
+}
+
+
+@pytest.mark.parametrize("case", sorted(_DIRECT_CASES))
+def test_direct_pve_mode_stops_where_eq19_first_holds(case):
+    """pve_mode="direct" (Table 4's control without the surrogate) stops at the
+    first p whose fixed-p result satisfies Eq. 19 against the p - 1 result, and
+    returns that fixed-p run's factors. On the fast-decaying spectrum p = 0 is
+    already close, so the test can pass at j = 1 (sigma^(0) from step 2's basis)."""
+    A = _DIRECT_CASES[case]()
+    k, s, p_max, seed = 10, 5, 12, 3
+    stops = []
+    for tol in (0.5, 1e-1, 1e-2, 1e-3, 1e-4):
+        d = dashsvd(A, k, s, p_max=p_max, tol=tol, seed=seed, pve_mode="direct")
+        expect = _eq19_stop_pass(A, k, s, tol, p_max, seed)
+        assert expect is not None and d.converged and d.passes == expect, (tol, d.passes, expect)
+        f = dashsvd(A, k, s, p_max=d.passes, tol=0.0, seed=seed)
+        assert np.array_equal(d.S, f.S) and np.array_equal(d.U, f.U) and np.array_equal(d.V, f.V)
+        stops.append(d.passes)
+    assert stops == sorted(stops)  # a tighter tolerance never stops earlier
+    if case == "geometric":
+        assert stops[0] == 1
+
+
+def test_direct_pve_mode_only_changes_the_stop():
+    """Without a stop test (tol = 0) both controls run the same iteration."""
+    A = _DIRECT_CASES["config1"]()
+    d = dashsvd(A, 12, 6, p_max=5, tol=0.0, seed=4, pve_mode="direct")
+    r = dashsvd(A, 12, 6, p_max=5, tol=0.0, seed=4)
+    assert d.passes == r.passes == 5 and not d.converged
+    assert np.array_equal(d.S, r.S) and np.array_equal(d.U, r.U)
+    assert [t.alpha_used for t in d.trace] == [t.alpha_used for t in r.trace]
+
+
+def test_direct_pve_mode_needs_same_or_one_fewer_pass():
+    """The paper's Table 4 observation: without the surrogate, N_p is the same
+    or one smaller (here on the three seeded cases over five tolerances)."""
+    for mk in _DIRECT_CASES.values():
+        A = mk()
+        for tol in (0.5, 1e-1, 1e-2, 1e-3, 1e-4):
+            d = dashsvd(A, 10, 5, p_max=12, tol=tol, seed=3, pve_mode="direct")
+            r = dashsvd(A, 10, 5, p_max=12, tol=tol, seed=3)
+            assert r.passes - 1 <= d.passes <= r.passes, (tol, d.passes, r.passes)
+
+
+def test_direct_pve_mode_rejects_bad_arguments():
+    A = _DIRECT_CASES["config1"]()
+    with pytest.raises(ValueError):
+        dashsvd(A, 4, 2, p_max=2, tol=0.0, seed=1, pve_mode="exact")
+    with pytest.raises(ValueError):
+        dashsvd(A, 4, 2, p_max=2, tol=0.0, seed=1, pve_mode="direct", policy=lambda x: (1.0, -1.0))
+
+
 # ------------------------------------------------------ planted mistakes
 
 
@@ -287,3 +360,32 @@ def test_pins_catch_planted_mistakes(monkeypatch, mutant):
     monkeypatch.setattr(ref, "eigsvd", mutant)
     r = ref.dashsvd(A, 9, 5, p_max=2, tol=0.0, seed=11)
     assert not np.allclose(r.S, Sr[:9], rtol=1e-6)
+
+
+@pytest.mark.parametrize("mutant", ["unsquared", "pre_update_basis"])
+def test_direct_pin_catches_planted_mistakes(monkeypatch, mutant):
+    """Plant a mistake in the oracle's direct control (ratio on unsquared
+    values; the test taken on the basis from before the pass) and check that the
+    Eq. 19 pin disagrees for at least one tolerance."""
+    import oracle.dashsvd_ref as ref
+
+    A = _DIRECT_CASES["dense2"]()
+    if mutant == "unsquared":
+        monkeypatch.setattr(ref, "direct_pve_ratio",
+                            lambda a, b, k: float(np.max(np.abs(a[:k] - b[:k])) / b[k]))
+    else:
+        real = ref.direct_pve_ratio
+        hist = []
+
+        def lagged(a, b, k):  # compares the pass before's values instead of this pass's
+            hist.append(b)
+            return real(hist[-3], hist[-2], k) if len(hist) >= 3 else np.inf
+
+        monkeypatch.setattr(ref, "direct_pve_ratio", lagged)
+    got, want = [], []
+    for tol in (0.5, 1e-1, 1e-2, 1e-3, 1e-4):
+        got.append(ref.dashsvd(A, 10, 5, p_max=12, tol=tol, seed=3, pve_mode="direct").passes)
+    monkeypatch.undo()
+    for tol in (0.5, 1e-1, 1e-2, 1e-3, 1e-4):
+        want.append(_eq19_stop_pass(A, 10, 5, tol, 12, 3))
+    assert got != want
