@@ -5,10 +5,12 @@
 //   G ~= C_hi^T C_hi + C_hi^T C_lo + C_lo^T C_hi, accumulated in FP32 in TMEM.
 //
 // One CTA per SM takes a contiguous chunk of rows. Eight converter warps load
-// 64-row blocks of C (coalesced along the row), split every value into
-// hi/lo BF16 and store them transposed into K-major 128-byte-swizzled operand
-// tiles (row m of a tile = column m of C, 64 K values = 64 rows of C), three
-// stages deep. One thread issues tcgen05.mma: since A = C^T and B^T = C^T
+// 64-row blocks of C, split every value into hi/lo BF16 and store them
+// transposed into K-major 128-byte-swizzled operand tiles (row m of a tile =
+// column m of C, 64 K values = 64 rows of C), three stages deep. A converter
+// thread takes 8 rows x 4 columns at a time (one 16-byte load per row): the
+// 8 lanes of a group take the 8 row groups of one column quad, so each of its
+// four 16-byte shared-memory stores fills one whole 128-byte tile row. One thread issues tcgen05.mma: since A = C^T and B^T = C^T
 // come from the same tile, D0 = rows 0..127 of G (all columns) and, when
 // l > 128, D1 = rows 128.. x columns 128.. of G (the rest follows by symmetry).
 // Per-CTA FP32 partials are summed in chunk order in FP64 by a second kernel.
@@ -27,7 +29,7 @@ constexpr int kThreadsTC = (kConvWarps + 2) * 32;
 constexpr int kOpRows = 256;
 constexpr int kOpBytes = kOpRows * kKB * 2;  // one hi or lo tile: 32 KB
 constexpr int kSmemTC = kStages * 2 * kOpBytes + 1024 /*align*/ + 256 /*barriers*/;
-constexpr int kMaxItems = kOpRows * 8 / (kConvWarps * 32);  // items per converter thread and block (l <= 256)
+constexpr int kMaxQuads = kOpRows / 4 * 8 / (kConvWarps * 32);  // (row group, column quad) pairs per thread (l <= 256)
 
 __global__ void __launch_bounds__(kThreadsTC, 1)
     gram_tc_kernel(const float* __restrict__ C, int64_t rows, int l, int64_t ldc, int Lc, int64_t chunk_rows,
@@ -67,22 +69,33 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   bool ok = true;
 
   if (warp < kConvWarps) {
-    // ---- converters: C block -> hi/lo K-major swizzled tiles. A thread's items
+    // ---- converters: C block -> hi/lo K-major swizzled tiles. A thread's quads
     // of block it + 1 are loaded into registers before block it is converted,
     // so the global-load latency overlaps the conversion and the MMA wait.
-    const int L32 = (l + 31) & ~31;
-    const int nitems = L32 * 8;  // (8-row group kc, column m) pairs per block
-    float cur[kMaxItems][8], nxt[kMaxItems][8];
-    auto load = [&](int it, float (&v)[kMaxItems][8]) {
+    const int nq4 = ((l + 31) & ~31) / 4;  // column quads (columns >= l are zero)
+    const int nquads = nq4 * 8;            // (8-row group kc, column quad) pairs per block
+    const bool vec = (ldc & 3) == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0;
+    float cur[kMaxQuads][8][4], nxt[kMaxQuads][8][4];
+    auto load = [&](int it, float (&v)[kMaxQuads][8][4]) {
       const int64_t r0 = k0 + (int64_t)it * kKB;
 #pragma unroll
-      for (int i = 0; i < kMaxItems; ++i) {
-        const int item = warp * 32 + lane + i * kConvWarps * 32;
-        const int kc = item / L32, m = item - kc * L32;
+      for (int i = 0; i < kMaxQuads; ++i) {
+        const int qd = warp * 32 + lane + i * kConvWarps * 32;
+        const int kc = qd & 7, m0 = 4 * (qd >> 3);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int64_t r = r0 + 8 * kc + j;
-          v[i][j] = (item < nitems && r < k1 && m < l) ? __ldg(C + r * ldc + m) : 0.f;
+          const bool live = qd < nquads && r < k1;
+          if (vec && live && m0 + 4 <= l) {
+            const float4 a = __ldg(reinterpret_cast<const float4*>(C + r * ldc + m0));
+            v[i][j][0] = a.x;
+            v[i][j][1] = a.y;
+            v[i][j][2] = a.z;
+            v[i][j][3] = a.w;
+          } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) v[i][j][e] = (live && m0 + e < l) ? __ldg(C + r * ldc + m0 + e) : 0.f;
+          }
         }
       }
     };
@@ -98,25 +111,30 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       uint8_t* hi = sm + (size_t)s * 2 * kOpBytes;
       uint8_t* lo = hi + kOpBytes;
 #pragma unroll
-      for (int i = 0; i < kMaxItems; ++i) {
-        const int item = warp * 32 + lane + i * kConvWarps * 32;
-        if (item < nitems) {
-          const int kc = item / L32, m = item - kc * L32;
-          uint32_t ph4[4], pl4[4];
+      for (int i = 0; i < kMaxQuads; ++i) {
+        const int qd = warp * 32 + lane + i * kConvWarps * 32;
+        if (qd < nquads) {
+          const int kc = qd & 7, m0 = 4 * (qd >> 3);
 #pragma unroll
-          for (int j = 0; j < 4; ++j) tc::split_bf16x2(cur[i][2 * j], cur[i][2 * j + 1], ph4[j], pl4[j]);
-          const uint32_t off = tc::sw128_chunk_offset(m, kc);
-          *reinterpret_cast<uint4*>(hi + off) = make_uint4(ph4[0], ph4[1], ph4[2], ph4[3]);
-          *reinterpret_cast<uint4*>(lo + off) = make_uint4(pl4[0], pl4[1], pl4[2], pl4[3]);
+          for (int e = 0; e < 4; ++e) {
+            uint32_t ph4[4], pl4[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) tc::split_bf16x2(cur[i][2 * j][e], cur[i][2 * j + 1][e], ph4[j], pl4[j]);
+            const uint32_t off = tc::sw128_chunk_offset(m0 + e, kc);
+            *reinterpret_cast<uint4*>(hi + off) = make_uint4(ph4[0], ph4[1], ph4[2], ph4[3]);
+            *reinterpret_cast<uint4*>(lo + off) = make_uint4(pl4[0], pl4[1], pl4[2], pl4[3]);
+          }
         }
       }
       tc::fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&full[s]);
 #pragma unroll
-      for (int i = 0; i < kMaxItems; ++i)
+      for (int i = 0; i < kMaxQuads; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) cur[i][j] = nxt[i][j];
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) cur[i][j][e] = nxt[i][j][e];
     }
   } else if (warp == kConvWarps + 1) {
     // ---- MMA issuer

@@ -6,11 +6,15 @@
 //
 // W^T (hi and lo, K-major 128-byte swizzled) stays in shared memory for the
 // whole kernel; a persistent CTA walks over 128-row tiles of C:
-//   warps 4..11 (converters) split each 128 x 64 block of C into hi/lo BF16
-//                operand tiles, two stages deep;
-//   warp 12, one thread, issues tcgen05.mma into one of two TMEM accumulators;
-//   warps 0..3 (epilogue) drain the other accumulator (TMEM lanes = rows)
-//                into FP32 and/or BF16 rows of Out, padding columns set to 0.
+//   warps 4..14 (converters) split each 128 x 64 block of C into hi/lo BF16
+//                operand tiles, two stages deep; each thread keeps the loads
+//                of the next two blocks in flight (three register buffers);
+//   warp 15, one thread, issues tcgen05.mma into one of two TMEM accumulators;
+//   warps 0..3 (epilogue) drain the other accumulator into FP32 and/or BF16
+//                rows of Out, padding columns set to 0: warp w reads TMEM
+//                lanes 32 w .. 32 w + 31 (its 32 rows), 16 columns at a time,
+//                the TMEM load of the next 16 in flight while a thread stores
+//                the current 16 values of its row (four 16-byte stores).
 // Output columns beyond what one CTA's shared memory holds for W^T are split
 // across blockIdx.y. Every wait is bounded; a timeout sets the error word.
 #include "internal.cuh"
@@ -22,14 +26,13 @@ namespace {
 constexpr int kRows = 128;       // rows of C per tile (MMA M)
 constexpr int kKB = 64;          // K per operand block
 constexpr int kAStages = 2;
-constexpr int kConv = 8;         // converter warps
-constexpr int kWarps = 4 + kConv + 1;
+constexpr int kEpi = 4;          // epilogue warps (one per TMEM lane quarter)
+constexpr int kConv = 11;        // converter warps (16 warps in all: 4 per SM sub-partition)
+constexpr int kWarps = kEpi + kConv + 1;
 constexpr int kThreadsP = kWarps * 32;
 constexpr int kATile = kRows * kKB * 2;  // 16 KB (hi or lo)
-constexpr int kBMax = 150 * 1024;        // W^T hi + lo budget (l = 150: 160 x 192 x 4 B = 120 KB)
-constexpr int kStgLd = 17;                                // epilogue staging: 32 rows x 16 columns, padded
-constexpr int kStgBytes = 4 * 32 * kStgLd * 4;            // one 32 x 16 tile per epilogue warp
-constexpr int kSmemP = 2 * kAStages * kATile + kBMax + 1024 + 512 + kStgBytes;
+constexpr int kBMax = 160 * 1024;        // W^T hi + lo budget (l = 150: 160 x 192 x 4 B = 120 KB; l = 192: 144 KB)
+constexpr int kSmemP = 2 * kAStages * kATile + kBMax + 1024 + 512;
 
 struct ProjArgs {
   const float* C;
@@ -57,7 +60,6 @@ __global__ void __launch_bounds__(kThreadsP, 1) project_tc_kernel(ProjArgs pa) {
   uint64_t* tfull = bars + 2 * kAStages;    // [2]
   uint64_t* tempty = bars + 2 * kAStages + 2;  // [2]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kAStages + 4);
-  float* stg = reinterpret_cast<float*>(Btiles + kBMax + 512);  // epilogue staging (after the barriers)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int Nc = pa.Nc, KB = pa.Kp / kKB;
   const int c0 = blockIdx.y * Nc;
@@ -72,7 +74,7 @@ __global__ void __launch_bounds__(kThreadsP, 1) project_tc_kernel(ProjArgs pa) {
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&tfull[b], 1);
-      tc::mbar_init(&tempty[b], 4);
+      tc::mbar_init(&tempty[b], kEpi);
     }
     tc::fence_mbar_init();
   }
@@ -100,7 +102,7 @@ __global__ void __launch_bounds__(kThreadsP, 1) project_tc_kernel(ProjArgs pa) {
     *reinterpret_cast<uint4*>(Btiles + (size_t)(2 * kb + 1) * btile + off) = make_uint4(o[0], o[1], o[2], o[3]);
   }
   tc::fence_proxy_async_smem();
-  if (warp == 4 + kConv) tc::tmem_alloc(tmem_slot, ncols);
+  if (warp == kEpi + kConv) tc::tmem_alloc(tmem_slot, ncols);
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
@@ -108,14 +110,20 @@ __global__ void __launch_bounds__(kThreadsP, 1) project_tc_kernel(ProjArgs pa) {
   const int64_t ntiles = ds_ceil_div(pa.rows, kRows);
   bool ok = true;
 
-  if (warp >= 4 && warp < 4 + kConv) {
-    // ---- converters: C rows -> hi/lo K-major tiles. A thread's items of the
-    // next block are loaded into registers before the current block is
-    // converted, so global-load latency overlaps the conversion and the MMA.
-    const int cw = warp - 4;
-    constexpr int kItems = kRows * 8 / (kConv * 32);  // 4 items of 8 values per thread and block
-    float cur[kItems][8], nxt[kItems][8];
-    auto load = [&](int64_t tile, int kb, float (&v)[kItems][8]) {
+  if (warp >= kEpi && warp < kEpi + kConv) {
+    // ---- converters: C rows -> hi/lo K-major tiles. The blocks of this CTA
+    // are g = 0, 1, ... (tile blockIdx.x + (g / KB) gridDim.x, K-block g % KB);
+    // block g is converted from one of three register buffers while the
+    // loads of blocks g + 1 and g + 2 are in flight in the other two.
+    const int cw = warp - kEpi;
+    constexpr int kItems = (kRows * 8 + kConv * 32 - 1) / (kConv * 32);  // items of 8 values per thread and block
+    const int64_t my_tiles = blockIdx.x < ntiles ? ds_ceil_div(ntiles - blockIdx.x, (int64_t)gridDim.x) : 0;
+    const int64_t nblk = my_tiles * KB;
+    float b0[kItems][8], b1[kItems][8], b2[kItems][8];
+    auto load = [&](int64_t g, float (&v)[kItems][8]) {
+      if (g >= nblk) return;
+      const int64_t tile = blockIdx.x + (g / KB) * (int64_t)gridDim.x;
+      const int kb = (int)(g % KB);
       const int64_t r0 = tile * kRows;
 #pragma unroll
       for (int i = 0; i < kItems; ++i) {
@@ -123,6 +131,7 @@ __global__ void __launch_bounds__(kThreadsP, 1) project_tc_kernel(ProjArgs pa) {
         const int r = item >> 3, kc = item & 7;
         const int64_t row = r0 + r;
         const int k0 = kb * kKB + 8 * kc;
+        if (item >= kRows * 8) break;
         if (row < pa.rows && k0 + 8 <= pa.l) {
           const float4 a = __ldg(reinterpret_cast<const float4*>(pa.C + row * pa.ldc + k0));
           const float4 b = __ldg(reinterpret_cast<const float4*>(pa.C + row * pa.ldc + k0 + 4));
@@ -135,34 +144,21 @@ __global__ void __launch_bounds__(kThreadsP, 1) project_tc_kernel(ProjArgs pa) {
         }
       }
     };
-    int64_t it = 0;
-    int64_t tile = blockIdx.x;
-    int kb = 0;
-    if (tile < ntiles) load(tile, kb, cur);
-    while (tile < ntiles && ok) {
-      // the block after (tile, kb)
-      int64_t ntile = tile;
-      int nkb = kb + 1;
-      if (nkb == KB) {
-        nkb = 0;
-        ntile += gridDim.x;
-      }
-      if (ntile < ntiles) load(ntile, nkb, nxt);
-      const int s = (int)(it % kAStages);
-      const uint32_t ph = (uint32_t)(it / kAStages) & 1u;
-      if (!tc::mbar_wait(&empty[s], ph ^ 1u)) {
-        ok = false;
-        break;
-      }
+    // convert block g from v into stage g mod kAStages; false on a timeout
+    auto convert = [&](int64_t g, const float (&v)[kItems][8]) -> bool {
+      const int s = (int)(g % kAStages);
+      const uint32_t ph = (uint32_t)(g / kAStages) & 1u;
+      if (!tc::mbar_wait(&empty[s], ph ^ 1u)) return false;
       uint8_t* hi = Atiles + (size_t)(2 * s) * kATile;
       uint8_t* lo = hi + kATile;
 #pragma unroll
       for (int i = 0; i < kItems; ++i) {
         const int item = cw * 32 + lane + i * kConv * 32;
         const int r = item >> 3, kc = item & 7;
+        if (item >= kRows * 8) break;
         uint32_t h[4], o[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) tc::split_bf16x2(cur[i][2 * j], cur[i][2 * j + 1], h[j], o[j]);
+        for (int j = 0; j < 4; ++j) tc::split_bf16x2(v[i][2 * j], v[i][2 * j + 1], h[j], o[j]);
         const uint32_t off = tc::sw128_chunk_offset(r, kc);
         *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
         *reinterpret_cast<uint4*>(lo + off) = make_uint4(o[0], o[1], o[2], o[3]);
@@ -170,15 +166,19 @@ __global__ void __launch_bounds__(kThreadsP, 1) project_tc_kernel(ProjArgs pa) {
       tc::fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&full[s]);
-#pragma unroll
-      for (int i = 0; i < kItems; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) cur[i][j] = nxt[i][j];
-      tile = ntile;
-      kb = nkb;
-      ++it;
+      return true;
+    };
+    load(0, b0);
+    load(1, b1);
+    for (int64_t g = 0; g < nblk && ok; g += 3) {
+      load(g + 2, b2);
+      if (!(ok = convert(g, b0)) || g + 1 >= nblk) break;
+      load(g + 3, b0);
+      if (!(ok = convert(g + 1, b1)) || g + 2 >= nblk) break;
+      load(g + 4, b1);
+      ok = convert(g + 2, b2);
     }
-  } else if (warp == 4 + kConv) {
+  } else if (warp == kEpi + kConv) {
     // ---- MMA issuer
     if (lane == 0) {
       const uint32_t idesc = tc::idesc_bf16_f32(kRows, Nc);
@@ -221,8 +221,12 @@ __global__ void __launch_bounds__(kThreadsP, 1) project_tc_kernel(ProjArgs pa) {
       }
     }
   } else {
-    // ---- epilogue warps 0..3: TMEM lanes 32w .. 32w+31 are rows of the tile
+    // ---- epilogue warps 0..3: TMEM lanes 32 w .. 32 w + 31 are rows of the tile
     const bool want_f32 = pa.outF && (!pa.f32_only_when_zero || *pa.f32_only_when_zero == 0);
+    const int nch = Nc / 16;
+    // 16-byte stores need 16-byte aligned rows
+    const bool vecF = want_f32 && (pa.ldf & 3) == 0 && (reinterpret_cast<uintptr_t>(pa.outF) & 15) == 0;
+    const bool vecB = pa.outB && (pa.ldb & 7) == 0 && (reinterpret_cast<uintptr_t>(pa.outB) & 15) == 0;
     int t = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++t) {
       const int b = t & 1;
@@ -232,28 +236,49 @@ __global__ void __launch_bounds__(kThreadsP, 1) project_tc_kernel(ProjArgs pa) {
         break;
       }
       tc::tc_fence_after();
-      // TMEM gives one row per thread; the 32 x 16 block goes through shared
-      // memory so that stores run along rows (two 64-byte row pieces per store)
-      float* ws = stg + warp * 32 * kStgLd;
-      const int64_t rbase = tile * kRows + 32 * warp;
-      for (int n0 = 0; n0 < Nc; n0 += 16) {
-        float v[16];
-        tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(b * Nc + n0), v);
+      const int64_t row = tile * kRows + 32 * warp + lane;  // TMEM gives one row per thread
+      const uint32_t tbase = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(b * Nc);
+      uint32_t cur[16], nxt[16];
+      tc::tmem_ld16_issue(tbase, cur);
+      tc::tmem_ld_wait(cur);
+      for (int ch = 0; ch < nch; ++ch) {
+        const bool more = ch + 1 < nch;
+        if (more) tc::tmem_ld16_issue(tbase + (uint32_t)(16 * (ch + 1)), nxt);
+        const int cbase = c0 + 16 * ch;
+        float x[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) ws[lane * kStgLd + i] = c0 + n0 + i < pa.cols ? v[i] : 0.f;
-        __syncwarp();
-        const int cl = lane & 15, c = c0 + n0 + cl;
-#pragma unroll 4
-        for (int rr = 0; rr < 16; ++rr) {
-          const int rl = 2 * rr + (lane >> 4);
-          const int64_t row = rbase + rl;
-          const float x = ws[rl * kStgLd + cl];
-          if (row < pa.rows) {
-            if (want_f32 && c < pa.ldf) pa.outF[row * pa.ldf + c] = x;
-            if (pa.outB && c < pa.ldb) pa.outB[row * pa.ldb + c] = __float2bfloat16_rn(x);
+        for (int i = 0; i < 16; ++i) x[i] = cbase + i < pa.cols ? __uint_as_float(cur[i]) : 0.f;
+        if (row < pa.rows) {
+          if (vecF && cbase + 16 <= pa.ldf) {
+            float4* dst = reinterpret_cast<float4*>(pa.outF + row * pa.ldf + cbase);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) dst[u] = make_float4(x[4 * u], x[4 * u + 1], x[4 * u + 2], x[4 * u + 3]);
+          } else if (want_f32) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+              if (cbase + i < pa.ldf) pa.outF[row * pa.ldf + cbase + i] = x[i];
+          }
+          if (vecB && cbase + 16 <= pa.ldb) {
+            uint32_t pk[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const __nv_bfloat162 h2 = __floats2bfloat162_rn(x[2 * u], x[2 * u + 1]);
+              pk[u] = *reinterpret_cast<const uint32_t*>(&h2);
+            }
+            uint4* dst = reinterpret_cast<uint4*>(pa.outB + row * pa.ldb + cbase);
+            dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+          } else if (pa.outB) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+              if (cbase + i < pa.ldb) pa.outB[row * pa.ldb + cbase + i] = __float2bfloat16_rn(x[i]);
           }
         }
-        __syncwarp();
+        if (more) {
+          tc::tmem_ld_wait(nxt);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) cur[i] = nxt[i];
+        }
       }
       tc::tc_fence_before();
       __syncwarp();
@@ -263,7 +288,7 @@ __global__ void __launch_bounds__(kThreadsP, 1) project_tc_kernel(ProjArgs pa) {
   if (!ok && lane == 0) atomicExch(pa.err, 1);
   tc::tc_fence_before();
   __syncthreads();
-  if (warp == 4 + kConv) {
+  if (warp == kEpi + kConv) {
     tc::tc_fence_after();
     tc::tmem_dealloc(tmem, ncols);
   }
