@@ -337,10 +337,35 @@ int dashsvd_project_bf16x3(dashsvd_handle h, const float* C, int64_t rows, int l
  * U: rows x ldu (first l columns), S: l values descending, V: l x l
  * (leading dimension l). Columns are ordered by descending S (ties by lower
  * index) and signed so that each V column's largest-|.| entry is positive; a
- * column whose eigenvalue is <= 16 * eps * largest eigenvalue (eps: unit
- * roundoff of the eig precision) gives a zero U column. `form` picks FP32 Jacobi (plain) or FP64 eig (precision). */
+ * column whose eigenvalue d_i is <= 16 * eps * sum_j V_ji^2 G_jj (the diagonal
+ * entries of G = C^T C it is made of; eps: unit roundoff of the Gram's
+ * precision) gives a zero U column. `form` picks the plain form (FP32 Gram and
+ * Jacobi) or the precision form (BF16x3 tensor-core Gram and projection, FP32
+ * Jacobi refined in FP64). */
 int dashsvd_eigsvd(dashsvd_handle h, const float* C, int64_t rows, int l, int64_t ldc, float* U,
                    int64_t ldu, float* S, float* V, int form);
+
+/* Accuracy metrics of Sec. 4 for a computed rank-k SVD A ~= U diag(S) V^T
+ * (the evaluation of the paper's experiments; not part of dashsvd_run):
+ *   out[0] eps_PVE   = max_{i<=k} |sigma_i^2 - ||A^T u_i||^2| / sigma_{k+1}^2
+ *   out[1] eps_res   = max_{i<=k} ||A^T u_i - s_i v_i||_2 / sigma_i
+ *   out[2] eps_sigma = max_{i<=k} |sigma_i - s_i| / sigma_i
+ *   out[3] eps_spec  = (||A - U S V^T||_2 - sigma_{k+1}) / sigma_{k+1}
+ *   out[4] the estimate of ||A - U S V^T||_2 used for out[3]
+ * A: m x n CSR (device). U: m x ldu (ldu >= k, ldu % 4 == 0, 16-byte aligned),
+ * S: k values, V: n x ldv (ldv >= k), all device FP32. sigma_ref: HOST array of
+ * the k + 1 reference singular values sigma_1 .. sigma_{k+1} of A (all > 0).
+ * out: HOST array of 5 doubles. 1 <= k < min(m, n), k <= DASHSVD_MAX_L.
+ * ||A - U S V^T||_2 is estimated by `spec_iters` steps of the block power
+ * method on (A - U S V^T)^T (A - U S V^T) with `spec_block` (1..16) columns
+ * started from a seeded Gaussian block; the estimate approaches the norm from
+ * below. spec_iters = 0 skips it (out[3], out[4] = NaN). A^T U and the power
+ * method run on the device (CSR of A^T built into the handle's own metrics
+ * workspace; the run's cached setup is not touched); the call waits for its
+ * work. DASHSVD_EINVAL on bad shapes, strides or reference values. */
+int dashsvd_metrics(dashsvd_handle h, const dashsvd_csr* A, int k, const float* U, int64_t ldu, const float* S,
+                    const float* V, int64_t ldv, const double* sigma_ref, int spec_block, int spec_iters,
+                    uint64_t seed, double* out);
 
 #ifdef __cplusplus
 }

@@ -6,7 +6,10 @@ TEST INFRASTRUCTURE: used by the tests and the benchmark's accuracy check only.
                / sigma_{k+1}(A)^2; for exact singular vectors u_i^T A A^T u_i = sigma_i^2,
                so only ||A^T uh_i||^2 is needed.
 * eps_sigma -- max_{i<=k} |sigma_i - sigmah_i| / sigma_i (Sec. 4).
-* eps_res   -- max_{i<=k} ||A^T uh_i - sigmah_i vh_i|| / sigma_i (Sec. 4, from Eq. 9).
+* eps_res   -- max_{i<=k} ||A^T uh_i - sigmah_i vh_i|| / sigma_i (Sec. 4, from Eq. 8).
+* eps_spec  -- (||A - Uh Sh Vh^T||_2 - ||A - A_k||_2) / ||A - A_k||_2 with
+               ||A - A_k||_2 = sigma_{k+1} (Sec. 4, from Eq. 17); the spectral norm
+               of the dense residual by LAPACK's SVD (small matrices).
 * theorem1_rhs / lemma6_rhs -- right-hand sides of Theorem 1 (shifted power
   iteration) and Lemma 6 (unshifted), and phi, the failure probability bound
   shared by both (Theorem 1 / Lemma 7).
@@ -31,6 +34,12 @@ def eps_sigma(S_hat, sigma_true, k):
 def eps_res(A, U_hat, S_hat, V_hat, sigma_true, k):
     R = A.T @ U_hat[:, :k] - V_hat[:, :k] * S_hat[None, :k]
     return float(np.max(np.linalg.norm(R, axis=0) / sigma_true[:k]))
+
+
+def eps_spec(A, U_hat, S_hat, V_hat, sigma_true, k):
+    A = A.toarray() if hasattr(A, "toarray") else np.asarray(A, dtype=np.float64)
+    R = A - (U_hat[:, :k] * S_hat[None, :k]) @ V_hat[:, :k].T
+    return float((np.linalg.norm(R, 2) - sigma_true[k]) / sigma_true[k])
 
 
 def principal_angles(X, Y):

@@ -40,7 +40,7 @@ EXPORTS = (
     "dashsvd_gram_bf16x3",
     "dashsvd_project", "dashsvd_project_bf16x3", "dashsvd_eigsvd", "dashsvd_gram_noalloc",
     "dashsvd_mlp_features", "dashsvd_mlp_forward", "dashsvd_mlp_loss_grad", "dashsvd_mlp_adam",
-    "dashsvd_get_tuning", "dashsvd_spmm_fused",
+    "dashsvd_get_tuning", "dashsvd_spmm_fused", "dashsvd_metrics",
 )
 MLP_PARAMS = 1218
 MLP_IN = 16
@@ -101,6 +101,7 @@ def _load():
         "dashsvd_mlp_features": (I, [P, P, I64, I, I, I, D, P]),
         "dashsvd_get_tuning": (I, [P, P, I64]),
         "dashsvd_spmm_fused": (I, [P, P, P, I64, I, P, P, I64]),
+        "dashsvd_metrics": (I, [P, P, I, P, I64, P, P, I64, P, I, I, U64, P]),
         "dashsvd_mlp_forward": (I, [P, P, P, I64, P]),
         "dashsvd_mlp_loss_grad": (I, [P, P, P, P, P, I64, P, P]),
         "dashsvd_mlp_adam": (I, [P, P, P, P, P, I, C.c_float, C.c_float, C.c_float, C.c_float]),
@@ -143,6 +144,7 @@ dashsvd_gram_noalloc = _export("dashsvd_gram_noalloc")
 dashsvd_mlp_features = _export("dashsvd_mlp_features")
 dashsvd_get_tuning = _export("dashsvd_get_tuning")
 dashsvd_spmm_fused = _export("dashsvd_spmm_fused")
+dashsvd_metrics = _export("dashsvd_metrics")
 dashsvd_mlp_forward = _export("dashsvd_mlp_forward")
 dashsvd_mlp_loss_grad = _export("dashsvd_mlp_loss_grad")
 dashsvd_mlp_adam = _export("dashsvd_mlp_adam")
@@ -404,6 +406,28 @@ class Handle:
     def mlp_adam(self, W, grad, m, v, step: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8):
         check(dashsvd_mlp_adam(self.h, W.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(), step, lr, beta1,
                                beta2, eps), "dashsvd_mlp_adam")
+
+    def metrics(self, A: CsrDevice, U, S, V, sigma_ref, spec_block: int = 16, spec_iters: int = 30,
+                seed: int = 0x5EED) -> dict:
+        """Accuracy metrics of Sec. 4 of a computed SVD (U, S, V device FP32 tensors)
+        against reference singular values sigma_ref (k + 1 host values)."""
+        import numpy as np
+
+        import torch
+
+        k = S.shape[0]
+        if U.stride(0) % 4 or U.stride(1) != 1 or U.data_ptr() % 16:  # the SpMM wants 16-byte rows
+            Up = torch.zeros((U.shape[0], (k + 3) // 4 * 4), dtype=torch.float32, device=U.device)
+            Up[:, :k] = U[:, :k]
+            U = Up
+        sig = np.ascontiguousarray(np.asarray(sigma_ref, dtype=np.float64)[: k + 1])
+        if sig.shape[0] != k + 1:
+            raise ValueError("sigma_ref needs k + 1 values")
+        out = (C.c_double * 5)()
+        check(dashsvd_metrics(self.h, C.byref(A.struct()), k, U.data_ptr(), U.stride(0), S.data_ptr(),
+                              V.data_ptr(), V.stride(0), sig.ctypes.data, spec_block, spec_iters, seed, out),
+              "dashsvd_metrics")
+        return {"eps_pve": out[0], "eps_res": out[1], "eps_sigma": out[2], "eps_spec": out[3], "spec_norm": out[4]}
 
     def eigsvd(self, Cm, l: int, form: int = DASHSVD_FORM_PLAIN):
         import torch

@@ -91,6 +91,9 @@ struct dashsvd_handle_s {
   DevBuf Qb, G64;           // precision form: BF16 basis, FP64 Gram
   DevBuf mlpw, mlp_part;    // learned form: network parameters, gradient partials
   DevBuf fpw;               // fingerprint of the last run's matrix
+  // accuracy metrics (dashsvd_metrics): CSR of A^T, partitions, blocks, sums
+  DevBuf mt_rowptr, mt_col, mt_val, mt_cursor, mt_scan, mt_seg_a, mt_seg_t, mt_T, mt_X, mt_Y, mt_Z, mt_C, mt_part,
+      mt_sig, mt_out, mt_S, mt_V;
   // setup kept across runs: the CSR of A^T and both merge-path partitions are
   // reused while the matrix (its arrays, sizes and fingerprint) is unchanged
   struct SetupKey {
@@ -563,7 +566,9 @@ int dashsvd_destroy(dashsvd_handle h) {
   DevBuf* bufs[] = {&h->rowptr_b, &h->col_b, &h->val_b, &h->cursor, &h->scan_tmp, &h->Y,       &h->Z,
                     &h->Q,        &h->G,     &h->W,     &h->W2,     &h->partial,  &h->carry, &h->carry_row,
                     &h->ctl,      &h->trace, &h->eigw,   &h->seg_fwd, &h->seg_bwd, &h->errw, &h->Qb, &h->G64,
-                    &h->mlpw, &h->mlp_part, &h->fpw};
+                    &h->mlpw, &h->mlp_part, &h->fpw, &h->mt_rowptr, &h->mt_col, &h->mt_val, &h->mt_cursor,
+                    &h->mt_scan, &h->mt_seg_a, &h->mt_seg_t, &h->mt_T, &h->mt_X, &h->mt_Y, &h->mt_Z, &h->mt_C,
+                    &h->mt_part, &h->mt_sig, &h->mt_out, &h->mt_S, &h->mt_V};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (h->side) cudaStreamDestroy(h->side);
@@ -815,7 +820,9 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
     DevBuf* bufs[] = {&h->rowptr_b, &h->col_b, &h->val_b, &h->cursor, &h->scan_tmp, &h->Y,       &h->Z,
                       &h->Q,        &h->G,     &h->W,     &h->W2,     &h->partial,  &h->carry, &h->carry_row,
                       &h->ctl,      &h->trace, &h->eigw,   &h->seg_fwd, &h->seg_bwd, &h->errw, &h->Qb, &h->G64,
-                    &h->mlpw, &h->mlp_part, &h->fpw};
+                    &h->mlpw, &h->mlp_part, &h->fpw, &h->mt_rowptr, &h->mt_col, &h->mt_val, &h->mt_cursor,
+                    &h->mt_scan, &h->mt_seg_a, &h->mt_seg_t, &h->mt_T, &h->mt_X, &h->mt_Y, &h->mt_Z, &h->mt_C,
+                    &h->mt_part, &h->mt_sig, &h->mt_out, &h->mt_S, &h->mt_V};
     for (DevBuf* b : bufs) ws += (int64_t)b->bytes;
     info->workspace_bytes = ws;
     info->eig_sweeps = hc.sweeps;
@@ -1031,6 +1038,142 @@ int dashsvd_eigsvd(dashsvd_handle h, const float* C, int64_t rows, int l, int64_
   }
   DS_CUDA(launch_eig_f32(as<float>(h->G), ld, a, eig_work_view(h->eigw.p), st));
   DS_CUDA(launch_project(C, rows, l, ldc, as<float>(h->W), ld, l, U, ldu, h->num_sms, st));
+  return DASHSVD_OK;
+}
+
+// ------------------------------------------------------------------ metrics
+
+int dashsvd_metrics(dashsvd_handle h, const dashsvd_csr* A, int k, const float* U, int64_t ldu, const float* S,
+                    const float* V, int64_t ldv, const double* sigma_ref, int spec_block, int spec_iters,
+                    uint64_t seed, double* out) {
+  if (!h || !csr_ok(A) || !U || !S || !V || !sigma_ref || !out) return DASHSVD_EINVAL;
+  const int64_t m = A->m, n = A->n, mn = std::min(m, n);
+  if (k < 1 || k >= mn || k > DASHSVD_MAX_L || ldu < k || ldv < k || ldu % 4 || !aligned16(U)) return DASHSVD_EINVAL;
+  if (spec_iters < 0 || (spec_iters > 0 && (spec_block < 1 || spec_block > 16 || spec_block > mn)))
+    return DASHSVD_EINVAL;
+  for (int i = 0; i <= k; ++i)
+    if (!(sigma_ref[i] > 0.0) || !std::isfinite(sigma_ref[i])) return DASHSVD_EINVAL;
+  for (int i = 0; i < 5; ++i) out[i] = std::nan("");
+  cudaStream_t st = h->stream;
+  const int nsm = h->num_sms;
+  const int bw = spec_iters > 0 ? spec_block : 0;
+  const int64_t ldk = round_up(k, 4), ldb = round_up(bw > 0 ? bw : 1, 8);
+  dashsvd_csr At{n, m, A->nnz, nullptr, nullptr, nullptr};
+  SpmmPart pa, pt;
+  pa.segments = spmm_segments(*A, nsm);
+  pt.segments = spmm_segments(At, nsm);
+  const int64_t segs = std::max(pa.segments, pt.segments);
+  const int64_t ldc = std::max(ldk, ldb);
+  bool moved = false;
+  int rc;
+  if ((rc = ensure(h->mt_rowptr, sizeof(int32_t) * (size_t)(n + 1), &moved)) ||
+      (rc = ensure(h->mt_col, sizeof(int32_t) * (size_t)A->nnz, &moved)) ||
+      (rc = ensure(h->mt_val, sizeof(float) * (size_t)A->nnz, &moved)) ||
+      (rc = ensure(h->mt_cursor, sizeof(int32_t) * (size_t)n, &moved)) ||
+      (rc = ensure(h->mt_scan, sizeof(int32_t) * scan_tmp_ints(n), &moved)) ||
+      (rc = ensure(h->mt_seg_a, sizeof(int32_t) * (size_t)(2 * (pa.segments + 1)), &moved)) ||
+      (rc = ensure(h->mt_seg_t, sizeof(int32_t) * (size_t)(2 * (pt.segments + 1)), &moved)) ||
+      (rc = ensure(h->carry, sizeof(float) * (size_t)(2 * segs * ldc), &moved)) ||
+      (rc = ensure(h->carry_row, sizeof(int32_t) * (size_t)(2 * segs), &moved)) ||
+      (rc = ensure(h->mt_T, sizeof(float) * (size_t)(n * ldk), &moved)) ||
+      (rc = ensure(h->mt_part, sizeof(double) * metrics_partial_doubles(std::max(m, n), k, bw, nsm), &moved)) ||
+      (rc = ensure(h->mt_sig, sizeof(double) * (size_t)(k + 1), &moved)) ||
+      (rc = ensure(h->mt_out, sizeof(double) * 4, &moved)))
+    return rc;
+  if (bw > 0 &&
+      ((rc = ensure(h->mt_X, sizeof(float) * (size_t)(n * ldb), &moved)) ||
+       (rc = ensure(h->mt_Z, sizeof(float) * (size_t)(n * ldb), &moved)) ||
+       (rc = ensure(h->mt_Y, sizeof(float) * (size_t)(m * ldb), &moved)) ||
+       (rc = ensure(h->mt_C, sizeof(float) * (size_t)(k * bw), &moved)) ||
+       (rc = ensure(h->mt_S, sizeof(float) * 16, &moved)) || (rc = ensure(h->mt_V, sizeof(float) * 256, &moved)) ||
+       (rc = ensure(h->G, sizeof(float) * (size_t)(ldb * ldb), &moved)) ||
+       (rc = ensure(h->W, sizeof(float) * (size_t)(ldb * ldb), &moved)) ||
+       (rc = ensure(h->eigw, eig_work_bytes(), &moved)) ||
+       (rc = ensure(h->partial, sizeof(float) * gram_partial_floats(std::max(m, n), bw, nsm), &moved))))
+    return rc;
+  if (moved) h->have_graph = false;
+  At.rowptr = as<int32_t>(h->mt_rowptr);
+  At.colidx = as<int32_t>(h->mt_col);
+  At.val = as<float>(h->mt_val);
+  DS_CUDA(launch_csr_transpose(*A, as<int32_t>(h->mt_rowptr), as<int32_t>(h->mt_col), as<float>(h->mt_val),
+                               as<int32_t>(h->mt_cursor), as<int32_t>(h->mt_scan), st));
+  pa.seg_row = as<int32_t>(h->mt_seg_a);
+  pa.seg_nnz = pa.seg_row + pa.segments + 1;
+  pt.seg_row = as<int32_t>(h->mt_seg_t);
+  pt.seg_nnz = pt.seg_row + pt.segments + 1;
+  DS_CUDA(launch_spmm_partition(*A, pa, st));
+  DS_CUDA(launch_spmm_partition(At, pt, st));
+  SpmmScratch scr;
+  scr.carry = as<float>(h->carry);
+  scr.carry_row = as<int32_t>(h->carry_row);
+  scr.max_segments = segs;
+  scr.ldc = (int)ldc;
+
+  // eps_PVE, eps_res, eps_sigma from T = A^T U
+  double* part = as<double>(h->mt_part);
+  DS_CUDA(cudaMemcpyAsync(h->mt_sig.p, sigma_ref, sizeof(double) * (size_t)(k + 1), cudaMemcpyHostToDevice, st));
+  DS_CUDA(launch_spmm(At, pt, U, ldu, k, as<float>(h->mt_T), ldk, nullptr, nullptr, 0, 1, scr, nsm, st));
+  DS_CUDA(launch_column_metrics(as<float>(h->mt_T), ldk, V, ldv, S, n, k, as<double>(h->mt_sig), part,
+                                as<double>(h->mt_out), nsm, st));
+  double cm[3];
+  DS_CUDA(cudaMemcpyAsync(cm, h->mt_out.p, sizeof(cm), cudaMemcpyDeviceToHost, st));
+
+  // eps_spec: block power method on R = A - U S V^T (R X = A X - U S (V^T X),
+  // R^T Y = A^T Y - V S (U^T Y)); X is kept orthonormal by eigSVD, and the
+  // largest singular value of R X after the last step is the estimate of
+  // ||R||_2 (from below); ||A - A_k||_2 = sigma_{k+1}
+  float smax = std::nanf("");
+  if (bw > 0) {
+    float* X = as<float>(h->mt_X);
+    float* Z = as<float>(h->mt_Z);
+    float* Y = as<float>(h->mt_Y);
+    float* C = as<float>(h->mt_C);
+    DS_CUDA(cudaMemsetAsync(X, 0, sizeof(float) * (size_t)(n * ldb), st));
+    DS_CUDA(cudaMemsetAsync(Z, 0, sizeof(float) * (size_t)(n * ldb), st));
+    DS_CUDA(cudaMemsetAsync(Y, 0, sizeof(float) * (size_t)(m * ldb), st));
+    EigArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.l = bw;
+    a.k = bw;
+    a.ldw = (int)ldb;
+    a.mode = kModeEigsvd;
+    a.W = as<float>(h->W);
+    a.W2 = as<float>(h->mt_V);
+    a.S_out = as<float>(h->mt_S);
+    const EigWork wk = eig_work_view(h->eigw.p);
+    // singular values of B (rows x bw) into mt_S and W = V S^-1
+    auto svd_of = [&](const float* B, int64_t rows) -> cudaError_t {
+      cudaError_t e = launch_gram(B, rows, bw, ldb, as<float>(h->G), ldb, as<float>(h->partial), nsm, st);
+      if (e == cudaSuccess) e = launch_eig_f32(as<float>(h->G), ldb, a, wk, st);
+      return e;
+    };
+    DS_CUDA(launch_gaussian(seed, n, bw, 0, Z, ldb, st));
+    DS_CUDA(svd_of(Z, n));
+    DS_CUDA(launch_project(Z, n, bw, ldb, as<float>(h->W), ldb, bw, X, ldb, nsm, st));
+    for (int t = 0; t < spec_iters; ++t) {
+      DS_CUDA(launch_spmm(*A, pa, X, ldb, bw, Y, ldb, nullptr, nullptr, 0, 1, scr, nsm, st));
+      DS_CUDA(launch_tall_tn(V, ldv, X, ldb, n, k, bw, C, part, nsm, st));
+      DS_CUDA(launch_sub_low_rank(Y, ldb, m, bw, U, ldu, k, S, C, nsm, st));
+      if (t == spec_iters - 1) {
+        DS_CUDA(svd_of(Y, m));
+        break;
+      }
+      DS_CUDA(launch_spmm(At, pt, Y, ldb, bw, Z, ldb, nullptr, nullptr, 0, 1, scr, nsm, st));
+      DS_CUDA(launch_tall_tn(U, ldu, Y, ldb, m, k, bw, C, part, nsm, st));
+      DS_CUDA(launch_sub_low_rank(Z, ldb, n, bw, V, ldv, k, S, C, nsm, st));
+      DS_CUDA(svd_of(Z, n));
+      DS_CUDA(launch_project(Z, n, bw, ldb, as<float>(h->W), ldb, bw, X, ldb, nsm, st));
+    }
+    DS_CUDA(cudaMemcpyAsync(&smax, h->mt_S.p, sizeof(float), cudaMemcpyDeviceToHost, st));
+  }
+  DS_CUDA(cudaStreamSynchronize(st));
+  out[0] = cm[0];
+  out[1] = cm[1];
+  out[2] = cm[2];
+  if (bw > 0) {
+    out[4] = (double)smax;
+    out[3] = ((double)smax - sigma_ref[k]) / sigma_ref[k];
+  }
   return DASHSVD_OK;
 }
 

@@ -161,6 +161,21 @@ cudaError_t launch_project(const float* C, int64_t rows, int l, int64_t ldc, con
                            int64_t ldw, int cols, float* Out, int64_t ldo, int num_sms,
                            cudaStream_t st);
 
+// Accuracy metrics (evaluation, Sec. 4): column sums of T = A^T U against V, S
+// and the reference singular values sigma (k + 1 FP64 values on the device)
+// into out[0..2] = eps_PVE, eps_res, eps_sigma; the tall products of the
+// block power method on A - U S V^T (k <= 256, b <= 16 columns).
+size_t metrics_partial_doubles(int64_t rows, int k, int b, int num_sms);
+cudaError_t launch_column_metrics(const float* T, int64_t ldt, const float* V, int64_t ldv, const float* S,
+                                  int64_t rows, int k, const double* sigma, double* partial, double* out, int num_sms,
+                                  cudaStream_t st);
+// C (k x b, FP32) = P^T Q over `rows` rows
+cudaError_t launch_tall_tn(const float* P, int64_t ldp, const float* Q, int64_t ldq, int64_t rows, int k, int b,
+                           float* C, double* partial, int num_sms, cudaStream_t st);
+// Y <- Y - P diag(S) C
+cudaError_t launch_sub_low_rank(float* Y, int64_t ldy, int64_t rows, int b, const float* P, int64_t ldp, int k,
+                                const float* S, const float* C, int num_sms, cudaStream_t st);
+
 // One-time per-process opt-ins (dynamic shared memory above 48 KB); must run
 // before any launch is captured into a graph.
 cudaError_t prepare_project();
