@@ -319,3 +319,67 @@ def test_direct_pve_control_argument_checks(ds):
         with pytest.raises(ds.DashSvdError) as ei:
             _run(ds, A, 8, 4, 2, 1e-2, **opts)
         assert ei.value.status == ds.DASHSVD_EINVAL, opts
+
+
+# ------------------------------------------ full size: the 1M x 1M social graph
+
+
+@pytest.fixture(scope="module")
+def social_1m():
+    import os
+
+    A, prm = datagen.make_config(2)
+    path = os.path.join(os.path.dirname(__file__), "golden", "social_graph_1m_sigma.txt")
+    return A, prm, np.loadtxt(path, comments="#")
+
+
+@pytest.mark.parametrize("form", ["plain", "precision_learned"])
+def test_full_size_social_graph(ds, social_1m, form):
+    """The benchmark's workload (1M x 1M, nnz 15M, k = 100, s = 50, p_max = 20,
+    tol = 1e-2) in the launch configuration it times (CUDA graph, autotuned
+    SpMM; the chosen form with the trained network): properties that hold at
+    any size against the FP64 oracle's stored singular values, and output rows
+    the host computes one by one."""
+    from paper_2404_09276_gb300 import learn
+
+    A, prm, sigma = social_1m
+    k, s = prm["k"], prm["s"]
+    learned = form == "precision_learned"
+    opts = {"form": ds.DASHSVD_FORM_PRECISION, "learned": 1} if learned else {"form": ds.DASHSVD_FORM_PLAIN}
+    Ad = ds.CsrDevice.from_host(A)
+    with ds.Handle(**opts) as h:
+        if learned:
+            w, _ = learn.load_weights()
+            h.load_mlp(w)
+        U, S, V, info = h.run(Ad, k, s, prm["p_max"], prm["tol"])
+        met = h.metrics(Ad, U, S, V, sigma[: k + 1], spec_iters=0)
+    assert info.status == ds.DASHSVD_OK and 2 <= info.passes <= prm["p_max"]
+    # true per-vector error within the tolerance (Sec. 4), singular values close
+    # and never above the true ones (Prop. 2) beyond rounding: FP32 in the plain
+    # form; in the precision form the BF16x3 Gram's error of about 2^-16 sigma_1^2
+    # moves sigma_i by up to about 2^-17 (sigma_1 / sigma_i)^2 of itself
+    assert met["eps_pve"] <= prm["tol"], met
+    assert met["eps_sigma"] <= 1e-2, met
+    Sh = S.cpu().numpy().astype(np.float64)
+    slack = 1e-4 + (0.0 if form == "plain" else 3e-5 * (sigma[0] / sigma[:k]) ** 2)
+    assert np.all(np.diff(Sh) <= 0) and np.all(Sh <= sigma[:k] * (1 + slack))
+    # Alg. 5 steps 9-11 give U S = B V_B = A Q V_B = A V exactly: check sampled
+    # rows of U against A V computed row by row in FP64 on the host
+    rng = np.random.default_rng(7)
+    rows = rng.choice(A.m, 2000, replace=False)
+    As = A.to_scipy()[rows].astype(np.float64)
+    Vh = V.cpu().numpy().astype(np.float64)
+    AV = As @ Vh
+    bound = abs(As) @ np.abs(Vh)
+    US = U.cpu().numpy()[rows].astype(np.float64) * Sh[None, :]
+    assert np.all(np.abs(US - AV) <= 1e-3 * bound + 1e-6 * Sh[0])
+
+
+def test_full_size_gaussian_block_sampled(ds):
+    """Omega of the 1M-row workload (l = 150) at three row offsets, against the
+    oracle's Philox4x32-10 + Box-Muller for those rows."""
+    with ds.Handle() as h:
+        for row0 in (0, 499_937, 1_000_000 - 128):
+            Y = h.gaussian(0x5EED, 128, 150, row0).cpu().numpy()
+            ref = oracle.gaussian_block(0x5EED, 128, 150, row0)
+            np.testing.assert_allclose(Y[:, :150], ref, rtol=1e-5, atol=2e-6)
