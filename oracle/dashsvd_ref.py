@@ -123,6 +123,14 @@ def pve_ratio(S_prev, alpha_prev, S, alpha, k):
     return float(np.max(np.abs(S_prev[:k] + alpha_prev - S[:k] - alpha)) / denom)
 
 
+def next_shift(S_l, alpha, f=1.0):
+    """Alg. 5 step 6: alpha <- (Shat_l + alpha) / 2 if Shat_l > alpha (the safe
+    bound of Prop. 1); the learned form takes the fraction f of it, clamped to
+    [0, bound], and the bound itself for a non-finite f."""
+    bound = 0.5 * (S_l + alpha) if S_l > alpha else alpha
+    return min(max(f * bound, 0.0), bound) if np.isfinite(f) else bound
+
+
 def direct_pve_ratio(Sd_prev, Sd, k):
     """max_{i<=k} |s'_i^2 - s_i^2| / max(s_{k+1}^2, floor): Eq. 19 of
     Sec. 3.2 on singular values s of B = A Q (this pass) and s' (the pass
@@ -214,8 +222,7 @@ def dashsvd(
             if j == 1:
                 alpha = 0.5 * S[l - 1]
         elif shift:  # step 6 (learned form: a fraction of the same bound)
-            bound = 0.5 * (S[l - 1] + alpha) if S[l - 1] > alpha else alpha
-            alpha = min(max(f * bound, 0.0), bound) if np.isfinite(f) else bound
+            alpha = next_shift(S[l - 1], alpha, f)
         S_prev = S  # step 7
         alpha_prev = alpha_used if alpha_prev_mode == 0 else alpha
         if direct:  # sigma^(j) of B = A Q against sigma^(j-1)

@@ -133,6 +133,25 @@ def test_per_pass_invariants_prop1_prop3():
     assert r.trace[0].alpha_used == 0.0 and r.trace[1].alpha_used > 0.0
 
 
+def _gap_case():
+    """sigma_1..12 in [5, 10], then a gap to sigma_13..100 in [1, 2]: with l = 12
+    the l-th Ritz value converges fast."""
+    sv = np.r_[np.linspace(10, 5, 12), np.linspace(2.0, 1.0, 88)]
+    return datagen.dense_with_spectrum(150, 100, sv, 3), sv
+
+
+def test_shift_converges_to_half_sigma_l_squared():
+    """Step 6's fixed point: once sqrt(Shat_l + alpha) has converged to sigma_l
+    (Prop. 3's surrogate), alpha = (Shat_l + alpha) / 2 has the fixed point
+    sigma_l^2 / 2, the top of Prop. 1's safe range; alpha approaches it from
+    below without overshooting."""
+    A, sv = _gap_case()
+    r = dashsvd(A, 8, 4, p_max=20, tol=0.0, seed=2)
+    target = sv[11] ** 2 / 2
+    assert r.alpha <= target * (1 + 1e-12)
+    assert abs(r.alpha - target) <= 1e-7 * target
+
+
 def test_pve_stop_closed_form_full_width():
     """With l = n every surrogate is exact (Shat_i + alpha = sigma_i^2), so under
     reading R1 the test sees a zero change at j = 2 and stops there; taking
@@ -389,3 +408,19 @@ def test_direct_pin_catches_planted_mistakes(monkeypatch, mutant):
     for tol in (0.5, 1e-1, 1e-2, 1e-3, 1e-4):
         want.append(_eq19_stop_pass(A, 10, 5, tol, 12, 3))
     assert got != want
+
+
+@pytest.mark.parametrize("mutant", ["no_alpha_term", "no_half"])
+def test_shift_pin_catches_planted_mistakes(monkeypatch, mutant):
+    """Plant a mistake in the oracle's step 6 (the new shift without the old
+    alpha term, or without the halving) and check that a pin fails."""
+    import oracle.dashsvd_ref as ref
+
+    if mutant == "no_alpha_term":
+        monkeypatch.setattr(ref, "next_shift", lambda S_l, alpha, f=1.0: 0.5 * S_l if S_l > alpha else alpha)
+    else:
+        monkeypatch.setattr(ref, "next_shift", lambda S_l, alpha, f=1.0: S_l + alpha if S_l > alpha else alpha)
+    A, sv = _gap_case()
+    r = ref.dashsvd(A, 8, 4, p_max=20, tol=0.0, seed=2)
+    target = sv[11] ** 2 / 2
+    assert abs(r.alpha - target) > 1e-3 * target
