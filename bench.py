@@ -155,24 +155,42 @@ def reference_arm(args):
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle samples while the timed region runs."""
+    """nvidia-smi clock / throttle samples (every 50 ms) around the timed
+    region: started before the warm-up runs, and summarized over the samples
+    whose timestamps fall between mark() and stop() (all samples if none do)."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-         "clocks_event_reasons.sw_power_cap")
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, interval_ms: int = 50):
         self.path = tempfile.mktemp(suffix=".csv")
         self.proc = None
+        self.t0 = None
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(interval_ms)],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+        # give nvidia-smi (bounded) time to start producing samples
+        t_end = time.time() + 3.0
+        while self.proc is not None and self.proc.poll() is None and time.time() < t_end:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
+
+    def mark(self):
+        """Start of the timed window."""
+        import datetime
+
+        self.t0 = datetime.datetime.now()
 
     def stop(self):
+        import datetime
+
+        t1 = datetime.datetime.now()
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -181,26 +199,30 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         with open(self.path) as f:
             for line in f:
                 p = [x.strip() for x in line.split(",")]
-                if len(p) < 9:
+                if len(p) < 10:
                     continue
                 try:
-                    sm.append(float(p[1]))
-                    mx.append(float(p[2]))
+                    sm, mx = float(p[2]), float(p[3])
                 except ValueError:
                     continue
-                for nm, v in zip(names, p[5:9]):
-                    if v.lower() == "active":
-                        reasons.add(nm)
+                try:
+                    ts = datetime.datetime.strptime(p[0], "%Y/%m/%d %H:%M:%S.%f")
+                except ValueError:
+                    ts = None  # unknown format: the sample still counts, outside the window test
+                rows.append((ts, sm, mx, [nm for nm, v in zip(names, p[6:10]) if v.lower() == "active"]))
         os.unlink(self.path)
-        if not sm:
+        inside = [r for r in rows if self.t0 is not None and r[0] is not None and self.t0 <= r[0] <= t1]
+        use = inside or rows
+        if not use:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return {"sm_mhz": statistics.median(r[1] for r in use), "sm_max_mhz": max(r[2] for r in use),
+                "reasons": sorted({nm for r in use for nm in r[3]}), "samples": len(use),
+                "window": "timed region" if inside else "warm-up and timed runs"}
 
 
 def _time_kernel(fn, reps, stream):
@@ -294,10 +316,11 @@ def _measure_form(form, args, ds, torch, A, Ad, prm, stream, flush, barrier, wor
     tuning = [[round(float(x), 3) for x in row] for row in tn[: (4 if gb else 2)]] + [[round(float(tn[4][0]), 3)]]
 
     def timed(tol_run):
+        clocks = ClockSampler(local)
         for _ in range(args.warmup):
             h.run(Ad, k, s, p_max, tol_run, U, S, V)
         barrier()
-        clocks = ClockSampler(local)
+        clocks.mark()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         infos = []
         for i in range(args.steps):
