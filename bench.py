@@ -250,13 +250,15 @@ FORMS = {
 }
 
 
-def _launches_per_run(form, passes, var_fwd, var_bwd):
+def _launches_per_run(form, passes, var_fwd, var_bwd, setup_reused=True, fused=False):
     kpv = lambda v: 2 if (v & 1) else 1  # noqa: E731  kernels per SpMM launch (merge path adds its fix-up)
     eig = 3 if form == "plain" else 3 + 1 + 2 * 6  # Jacobi, replay, finish (+ FP64 refinement)
     # (the BF16-gather form tunes BF16 variants for the loop; its prologue and final product stay FP32)
-    setup = 5 + 2  # CSR transpose, merge-path partitions
+    # the matrix fingerprint, plus the CSR transpose and merge-path partitions unless kept from the last run
+    setup = 1 + (0 if setup_reused else 5 + 2)
     prologue = 1 + kpv(var_bwd) + 2 + eig + 1
-    per_pass = kpv(var_fwd) + kpv(var_bwd) + 2 + eig + 1
+    # a pass: both products (or the fused one: -alpha Q, then the scatter), Gram + reduce, eig, projection
+    per_pass = (2 if fused else kpv(var_fwd) + kpv(var_bwd)) + 2 + eig + 1
     final = kpv(var_fwd) + 2 + eig + 2
     return setup + prologue + passes * per_pass + final
 
@@ -442,7 +444,8 @@ def _measure_form(form, args, ds, torch, A, Ad, prm, stream, flush, barrier, wor
             "accuracy": {"eps_pve": attempts[-1]["eps_pve"], "tol_used": tol_run, "attempts": attempts},
             "pve_surrogate": info.pve_ratio, "trace": trace, "e2e": e2e, "kernels_s": kt,
             "kernel_s_per_run": per_run, "spmm": dict(spmm, tuning_ms=tuning), "clocks": clk,
-            "gpu_launches": _launches_per_run(form, passes, var_fwd, var_bwd) * args.steps,
+            "gpu_launches": _launches_per_run(form, passes, var_fwd, var_bwd, bool(info.setup_reused),
+                                              bool(fused)) * args.steps,
             "bytes": {"spmm_fwd": bytes_fwd, "spmm_bwd": bytes_bwd}}
 
 

@@ -84,3 +84,13 @@ def test_traffic_needs_the_same_sources(monkeypatch):
     monkeypatch.setattr(bench, "_git_blob_sha1", lambda p: "0" * 40)
     assert bench._traffic("spmm_bwd", 7) is None
     assert bench._traffic("spmm_bwd", 3) is None
+
+
+def test_launch_count_matches_the_committed_launch_list():
+    """One steady-state run of the chosen form on the 1M graph (5 passes, A Q
+    by variant 5 and A^T Y - alpha Q by variant 7, setup kept) launched 160 of
+    the library's kernels in the committed ncu launch list."""
+    assert bench._launches_per_run("precision_learned", 5, 5, 7, setup_reused=True) == 160
+    assert bench._launches_per_run("precision_learned", 5, 5, 7, setup_reused=False) == 167
+    # the fused pass product replaces the two products (2 + 2 launches) by 2
+    assert bench._launches_per_run("precision", 5, 5, 7, fused=True) == 160 - 5 * 2
