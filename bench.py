@@ -37,6 +37,7 @@ sys.path.insert(0, ROOT)
 METRIC = "s to PVE<=1e-2, k=100: chosen vs plain GPU form; SpMM GB/s vs HBM peak"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
 NUM_SMS_GB300 = 152
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal (the measured copy bandwidth is the roofline's peak)
 FP32_LANES_PER_SM = 128
 
 
@@ -490,6 +491,7 @@ def _roofline(r, A, l, pk):
         traffic = _traffic(dom, var)
         return {"kernel": dom, "variant": var, "bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": gbs / pk["hbm_gbs"], "traffic": traffic,
+                "frac_of_nominal": gbs / NOMINAL_HBM_GBS,
                 "dram_gbs": traffic / kt[dom] / 1e9 if traffic else None,
                 "gathered_gbs": A.nnz * l * 4 / kt[dom] / 1e9,
                 "peak_source": pk["source"] + " HBM copy bandwidth (burst: the kernel is timed alone)",

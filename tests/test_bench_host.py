@@ -71,6 +71,7 @@ def test_roofline_of_the_dominant_spmm():
     assert r["kernel"] == "spmm_bwd" and r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert abs(r["achieved"] - 1.932e9 / 0.0029 / 1e9) < 1e-9
     assert abs(r["frac"] - r["achieved"] / 6790.0) < 1e-12
+    assert abs(r["frac_of_nominal"] - r["achieved"] / 7900.0) < 1e-12
     assert abs(r["gathered_gbs"] - 15e6 * 150 * 4 / 0.0029 / 1e9) < 1e-9
     if r["traffic"] is not None:  # the committed summary matches the current SpMM sources
         assert abs(r["dram_gbs"] - r["traffic"] / 0.0029 / 1e9) < 1e-9
