@@ -367,6 +367,19 @@ int dashsvd_metrics(dashsvd_handle h, const dashsvd_csr* A, int k, const float* 
                     const float* V, int64_t ldv, const double* sigma_ref, int spec_block, int spec_iters,
                     uint64_t seed, double* out);
 
+/* Self-tests of the failure paths (for tests; they fault, trap and hang nothing).
+ *
+ * dashsvd_selftest_bounded_wait: one kernel waits on a device barrier that
+ * nothing completes, giving up after `polls` polls (1 .. 2^20) the way every
+ * bounded wait of the library does; returns DASHSVD_ETIMEOUT when the bound
+ * ran out (the expected result) and leaves the handle usable.
+ *
+ * dashsvd_selftest_fail_alloc: the nth device workspace allocation from now
+ * on (any handle in the process; nth >= 1) fails with DASHSVD_ENOMEM before
+ * any buffer is released; 0 disarms. A failed call leaves the handle usable. */
+int dashsvd_selftest_bounded_wait(dashsvd_handle h, uint32_t polls);
+int dashsvd_selftest_fail_alloc(int nth);
+
 #ifdef __cplusplus
 }
 #endif

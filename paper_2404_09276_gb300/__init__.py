@@ -40,7 +40,8 @@ EXPORTS = (
     "dashsvd_gram_bf16x3",
     "dashsvd_project", "dashsvd_project_bf16x3", "dashsvd_eigsvd", "dashsvd_gram_noalloc",
     "dashsvd_mlp_features", "dashsvd_mlp_forward", "dashsvd_mlp_loss_grad", "dashsvd_mlp_adam",
-    "dashsvd_get_tuning", "dashsvd_spmm_fused", "dashsvd_metrics",
+    "dashsvd_get_tuning", "dashsvd_spmm_fused", "dashsvd_metrics", "dashsvd_selftest_bounded_wait",
+    "dashsvd_selftest_fail_alloc",
 )
 MLP_PARAMS = 1218
 MLP_IN = 16
@@ -102,6 +103,8 @@ def _load():
         "dashsvd_get_tuning": (I, [P, P, I64]),
         "dashsvd_spmm_fused": (I, [P, P, P, I64, I, P, P, I64]),
         "dashsvd_metrics": (I, [P, P, I, P, I64, P, P, I64, P, I, I, U64, P]),
+        "dashsvd_selftest_bounded_wait": (I, [P, C.c_uint32]),
+        "dashsvd_selftest_fail_alloc": (I, [I]),
         "dashsvd_mlp_forward": (I, [P, P, P, I64, P]),
         "dashsvd_mlp_loss_grad": (I, [P, P, P, P, P, I64, P, P]),
         "dashsvd_mlp_adam": (I, [P, P, P, P, P, I, C.c_float, C.c_float, C.c_float, C.c_float]),
@@ -145,6 +148,8 @@ dashsvd_mlp_features = _export("dashsvd_mlp_features")
 dashsvd_get_tuning = _export("dashsvd_get_tuning")
 dashsvd_spmm_fused = _export("dashsvd_spmm_fused")
 dashsvd_metrics = _export("dashsvd_metrics")
+dashsvd_selftest_bounded_wait = _export("dashsvd_selftest_bounded_wait")
+dashsvd_selftest_fail_alloc = _export("dashsvd_selftest_fail_alloc")
 dashsvd_mlp_forward = _export("dashsvd_mlp_forward")
 dashsvd_mlp_loss_grad = _export("dashsvd_mlp_loss_grad")
 dashsvd_mlp_adam = _export("dashsvd_mlp_adam")

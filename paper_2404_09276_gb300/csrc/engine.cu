@@ -13,6 +13,7 @@
 // on any pass. The graph is cached per handle and rebuilt when an argument
 // that is baked into it changes.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -39,10 +40,15 @@ struct DevBuf {
 
 int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
+// Allocation fault injection (dashsvd_selftest_fail_alloc): when > 0, the
+// allocation that brings it to 0 fails before anything is freed.
+std::atomic<int> g_fail_alloc_in{0};
+
 // Grow-only device buffer; returns a status code.
 int ensure(DevBuf& b, size_t bytes, bool* moved) {
   if (bytes == 0) bytes = 16;
   if (b.bytes >= bytes) return DASHSVD_OK;
+  if (g_fail_alloc_in.load() > 0 && g_fail_alloc_in.fetch_sub(1) == 1) return DASHSVD_ENOMEM;
   if (b.p) cudaFree(b.p);
   b.p = nullptr;
   b.bytes = 0;
@@ -1174,6 +1180,31 @@ int dashsvd_metrics(dashsvd_handle h, const dashsvd_csr* A, int k, const float* 
     out[4] = (double)smax;
     out[3] = ((double)smax - sigma_ref[k]) / sigma_ref[k];
   }
+  return DASHSVD_OK;
+}
+
+// ------------------------------------------------------------------ self-tests
+
+int dashsvd_selftest_bounded_wait(dashsvd_handle h, uint32_t polls) {
+  if (!h || polls == 0 || polls > (1u << 20)) return DASHSVD_EINVAL;
+  bool moved = false;
+  int rc;
+  if ((rc = ensure(h->errw, 16, &moved))) return rc;
+  if (moved) h->have_graph = false;
+  cudaStream_t st = h->stream;
+  DS_CUDA(cudaMemsetAsync(h->errw.p, 0, sizeof(int), st));
+  DS_CUDA(launch_bounded_wait_selftest(polls, as<int>(h->errw), st));
+  int err = 0;
+  DS_CUDA(cudaMemcpyAsync(&err, h->errw.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DS_CUDA(cudaStreamSynchronize(st));
+  DS_CUDA(cudaMemsetAsync(h->errw.p, 0, sizeof(int), st));
+  DS_CUDA(cudaStreamSynchronize(st));
+  return err ? DASHSVD_ETIMEOUT : DASHSVD_OK;
+}
+
+int dashsvd_selftest_fail_alloc(int nth) {
+  if (nth < 0) return DASHSVD_EINVAL;
+  g_fail_alloc_in.store(nth);
   return DASHSVD_OK;
 }
 

@@ -176,6 +176,10 @@ cudaError_t launch_tall_tn(const float* P, int64_t ldp, const float* Q, int64_t 
 cudaError_t launch_sub_low_rank(float* Y, int64_t ldy, int64_t rows, int b, const float* P, int64_t ldp, int k,
                                 const float* S, const float* C, int num_sms, cudaStream_t st);
 
+// Self-test of the bounded waits: a wait that nothing completes gives up after
+// `polls` polls and sets *err to 1.
+cudaError_t launch_bounded_wait_selftest(uint32_t polls, int* err, cudaStream_t st);
+
 // One-time per-process opt-ins (dynamic shared memory above 48 KB); must run
 // before any launch is captured into a graph.
 cudaError_t prepare_project();
