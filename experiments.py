@@ -26,9 +26,9 @@ FP64-accumulated run of the library itself with a wide sketch):
   eps_res   = max_i ||A^T u_i - s_i v_i|| / sigma_i
 
 Usage (GPU):
-    python -m paper_2404_09276_gb300.experiments fig1 --seeds 5
-    python -m paper_2404_09276_gb300.experiments variance --runs 100
-    python -m paper_2404_09276_gb300.experiments table4 --configs 2 3
+    python experiments.py fig1 --seeds 5
+    python experiments.py variance --runs 100
+    python experiments.py table4 --configs 2 3
 """
 from __future__ import annotations
 
@@ -39,7 +39,7 @@ import sys
 
 import numpy as np
 
-HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.abspath(__file__))
 ALGS = (("Alg. 1", 0), ("Alg. 2*", 2), ("Alg. 2", 1))
 
 
@@ -85,7 +85,7 @@ def fig1(ds, seeds, ps, k=100, s=50):
 def _reference_sigma(ds, Ad, cfg, k):
     """sigma_1..sigma_{k+1}: the stored FP64 values for the 1M social graph,
     else a long run of the library with a wide sketch."""
-    p = os.path.join(os.path.dirname(HERE), "tests", "golden", "social_graph_1m_sigma.txt")
+    p = os.path.join(ROOT, "tests", "golden", "social_graph_1m_sigma.txt")
     if cfg == 2 and os.path.exists(p):
         return np.loadtxt(p, comments="#"), "FP64 oracle, stored"
     with ds.Handle() as h:
@@ -153,7 +153,7 @@ def main(argv=None):
     ap.add_argument("--runs", type=int, default=100)
     ap.add_argument("--configs", type=int, nargs="+", default=[2, 3])
     a = ap.parse_args(argv)
-    sys.path.insert(0, os.path.dirname(HERE))
+    sys.path.insert(0, ROOT)
     import paper_2404_09276_gb300 as ds
 
     if a.which == "fig1":

@@ -45,6 +45,9 @@ extern "C" {
 typedef enum {
   DASHSVD_OK = 0,
   DASHSVD_MAX_PASSES = 1,  /* p_max passes ran without meeting tol; results are valid */
+  DASHSVD_LEARNED_STOP = 2, /* learned form: the network stopped the run while the PVE
+                               surrogate ratio was above tol but within 3 tol (results are
+                               valid; the surrogate test itself did not pass) */
   DASHSVD_EINVAL = -1,     /* bad argument (sizes, null pointer, k/s/l out of range) */
   DASHSVD_ENOMEM = -2,     /* device workspace allocation failed */
   DASHSVD_ECUDA = -3,      /* a CUDA call failed (message: dashsvd_last_error) */
@@ -115,7 +118,22 @@ typedef struct {
                               of the pass before (p = 0 for the first pass). EINVAL with
                               learned or gather_bf16; the fused pass product is not
                               used (B must be stored). */
-  int32_t reserved[5];
+  int32_t trust_csr;       /* 0 (default): every step-level entry point that takes a CSR
+                              (dashsvd_csr_transpose, dashsvd_spmm*, dashsvd_metrics)
+                              first checks its structure on the device, as dashsvd_csr_check
+                              does, and returns DASHSVD_EINVAL without touching the dense
+                              operands if it is malformed (this adds one kernel and a wait);
+                              1: the caller vouches for the CSR (for timing single kernels).
+                              dashsvd_run always checks. */
+  int32_t deterministic;   /* 1: bitwise-reproducible runs: the CSR of A^T is built by a
+                              stable counting sort (entries of each row of A^T in increasing
+                              row order of A), so every sum has a fixed order; the fused pass
+                              product (atomic scatter, spmm_variant 10) is refused. 0: the
+                              transpose orders the entries of a row of A^T by atomics, so two
+                              runs agree to rounding, not bit for bit. */
+  int32_t profile;         /* 1: the run uses the host-driven loop and records the device time
+                              of each group of launches (dashsvd_get_profile); 0: off */
+  int32_t reserved[2];
 } dashsvd_options;
 
 typedef struct {
@@ -151,7 +169,9 @@ int dashsvd_destroy(dashsvd_handle h);
  *   test, which gives the fixed-p dashSVD of Alg. 4.
  * Outputs (device, caller-owned): U m x k row-major, S k values (descending),
  * V n x k row-major. Returns DASHSVD_OK when the PVE test stopped the loop,
- * DASHSVD_MAX_PASSES when p_max passes ran (or pve_tol <= 0), else an error.
+ * DASHSVD_MAX_PASSES when p_max passes ran (or pve_tol <= 0),
+ * DASHSVD_LEARNED_STOP when the learned network stopped it first (learned
+ * form only), else an error.
  * `info` (host pointer, may be NULL) receives run statistics.
  * Setup: the CSR of the transpose and the merge-path partitions are built on
  * the first run and kept while later runs pass the same arrays with the same
@@ -160,6 +180,23 @@ int dashsvd_destroy(dashsvd_handle h);
  * Step-level SpMM calls on the handle also drop them. */
 int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_passes,
                 double pve_tol, float* U, float* S, float* V, dashsvd_info* info);
+
+/* Check the structure of a CSR matrix on the device (the precondition of every
+ * sparse product): rowptr[0] == 0, rowptr non-decreasing, rowptr[m] == nnz, and
+ * every column id in [0, n). The check reads only the m + 1 row pointers and
+ * nnz column ids that A declares (values are not inspected; non-finite values
+ * are reported by dashsvd_run as DASHSVD_ENONFINITE). Returns DASHSVD_OK or
+ * DASHSVD_EINVAL; `flags` (HOST, may be NULL) receives the failed conditions:
+ * bit 0 rowptr[0] != 0, bit 1 rowptr decreases, bit 2 rowptr[m] != nnz,
+ * bit 3 a column id outside [0, n). Waits for its kernel. dashsvd_run runs the
+ * same check (in the same read as its setup fingerprint) and returns
+ * DASHSVD_EINVAL before any product when it fails. The paper states the input
+ * as a sparse matrix A (Sec. 2.1); this is the library's guard on its CSR form. */
+#define DASHSVD_CSR_BAD_FIRST 1u
+#define DASHSVD_CSR_BAD_ORDER 2u
+#define DASHSVD_CSR_BAD_LAST 4u
+#define DASHSVD_CSR_BAD_COL 8u
+int dashsvd_csr_check(dashsvd_handle h, const dashsvd_csr* A, uint32_t* flags);
 
 /* Copy the per-pass history of the last run (record_trace = 1) to HOST memory.
  * Record j (0-based) holds 5 + l doubles: pass index, shift used in the pass,
@@ -176,6 +213,17 @@ int dashsvd_get_trace(dashsvd_handle h, double* out, int64_t cap, int64_t* count
  * A Q plus the best A^T Y - alpha Q (dashsvd_info.spmm_variant bit 16). */
 int dashsvd_get_tuning(dashsvd_handle h, float* ms, int64_t cap);
 
+/* Device time per step of the last run made with options.profile = 1 (HOST
+ * buffer of at least 14 doubles): ms[c] = total milliseconds and ms[7 + c] =
+ * number of timed launch groups of category c, where c is 0 the Gaussian block
+ * (Alg. 5 step 1), 1 the products A Q (steps 4 and 9), 2 the products
+ * A^T Y - alpha Q (and A^T Omega of step 2), 3 the Gram matrices, 4 the l x l
+ * eigensolves with their control tail (Jacobi, eigenvector replay, FP64
+ * refinement, conventions, steps 5-7), 5 the projections C W (steps 2, 4, 11),
+ * 6 the host's waits between passes of the host-driven loop. The time of the
+ * setup fingerprint is not included. */
+int dashsvd_get_profile(dashsvd_handle h, double* ms, int64_t cap);
+
 /* ---- learned form --------------------------------------------------------
  * The paper has no learned component; this is an addition. A network
  * 16 -> 64 (tanh) -> 2 reads features of each power-iteration pass (Shat_i +
@@ -187,7 +235,8 @@ int dashsvd_get_tuning(dashsvd_handle h, float* ms, int64_t cap);
  *     plain rule;
  *   - an early stop (o_1 > 0), honoured from pass 2 on and only while the
  *     surrogate ratio of step 5 is at most 3 pve_tol; the surrogate test
- *     itself still stops the run at pve_tol.
+ *     itself still stops the run at pve_tol. A run the network stopped before
+ *     the surrogate test passed returns DASHSVD_LEARNED_STOP, not DASHSVD_OK.
  * Parameters (1218 floats): W1 (64 x 16, row-major), b1 (64), W2 (2 x 64), b2 (2).
  * Features are computed on the device, in FP64, from the same quantities the
  * trace records (dashsvd_get_trace), and rounded to FP32; the network runs in
@@ -344,6 +393,19 @@ int dashsvd_project_bf16x3(dashsvd_handle h, const float* C, int64_t rows, int l
  * Jacobi refined in FP64). */
 int dashsvd_eigsvd(dashsvd_handle h, const float* C, int64_t rows, int l, int64_t ldc, float* U,
                    int64_t ldu, float* S, float* V, int form);
+
+/* The precision form's l x l symmetric eigensolver on its own (Alg. 3 step 1,
+ * [V, D] = eig(G), in FP64): G (l x l, leading dimension ldg, symmetric, FP64,
+ * DEVICE) is rounded to FP32 for cyclic Jacobi sweeps run to FP32 rounding,
+ * then `iters` (0..8) refinement steps against the FP64 G follow (Ogita and
+ * Aishima's iteration: Newton corrections for eigenvector pairs whose
+ * eigenvalue gap exceeds the current residual, re-orthogonalization within
+ * closer groups); eigSVD and dashsvd_run use 3. iters = 0 returns the FP32
+ * Jacobi result widened to FP64. Outputs (DEVICE, FP64): D (l eigenvalues,
+ * descending, ties by lower index) and V (l x l row-major; column r is the
+ * eigenvector of D[r], signed so that its largest-|.| entry is positive).
+ * Waits for its work; DASHSVD_ENOCONV if the Jacobi sweeps hit their limit. */
+int dashsvd_eig_fp64(dashsvd_handle h, const double* G, int64_t ldg, int l, int iters, double* D, double* V);
 
 /* Accuracy metrics of Sec. 4 for a computed rank-k SVD A ~= U diag(S) V^T
  * (the evaluation of the paper's experiments; not part of dashsvd_run):

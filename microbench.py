@@ -9,7 +9,7 @@ GB/s). Under a profiler, the warm-up launches come first, so ``ncu -s <warmup>
 -c <reps>`` selects the timed ones.
 
 Usage:
-    python -m paper_2404_09276_gb300.microbench --config 2 --product bwd --variant 7
+    python microbench.py --config 2 --product bwd --variant 7
 """
 from __future__ import annotations
 
@@ -20,7 +20,7 @@ import sys
 
 import numpy as np
 
-HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.abspath(__file__))
 
 
 def main(argv=None):
@@ -36,7 +36,7 @@ def main(argv=None):
     ap.add_argument("--flush", action="store_true", help="write 256 MB before each timed launch (cold L2)")
     a = ap.parse_args(argv)
 
-    sys.path.insert(0, os.path.dirname(HERE))
+    sys.path.insert(0, ROOT)
     import torch
 
     import datagen

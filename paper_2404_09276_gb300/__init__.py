@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libdashsvd.so")
 # ---- status codes (dashsvd_status) -------------------------------------------
 DASHSVD_OK = 0
 DASHSVD_MAX_PASSES = 1
+DASHSVD_LEARNED_STOP = 2
 DASHSVD_EINVAL = -1
 DASHSVD_ENOMEM = -2
 DASHSVD_ECUDA = -3
@@ -41,7 +42,7 @@ EXPORTS = (
     "dashsvd_project", "dashsvd_project_bf16x3", "dashsvd_eigsvd", "dashsvd_gram_noalloc",
     "dashsvd_mlp_features", "dashsvd_mlp_forward", "dashsvd_mlp_loss_grad", "dashsvd_mlp_adam",
     "dashsvd_get_tuning", "dashsvd_spmm_fused", "dashsvd_metrics", "dashsvd_selftest_bounded_wait",
-    "dashsvd_selftest_fail_alloc",
+    "dashsvd_selftest_fail_alloc", "dashsvd_csr_check", "dashsvd_eig_fp64", "dashsvd_get_profile",
 )
 MLP_PARAMS = 1218
 MLP_IN = 16
@@ -59,7 +60,8 @@ class dashsvd_options(C.Structure):
         ("form", C.c_int32), ("learned", C.c_int32), ("seed", C.c_uint64),
         ("alpha_prev_mode", C.c_int32), ("use_graph", C.c_int32), ("spmm_variant", C.c_int32),
         ("record_trace", C.c_int32), ("shift", C.c_int32), ("gather_bf16", C.c_int32),
-        ("pve_mode", C.c_int32), ("reserved", C.c_int32 * 5),
+        ("pve_mode", C.c_int32), ("trust_csr", C.c_int32), ("deterministic", C.c_int32),
+        ("profile", C.c_int32), ("reserved", C.c_int32 * 2),
     ]
 
 
@@ -105,6 +107,9 @@ def _load():
         "dashsvd_metrics": (I, [P, P, I, P, I64, P, P, I64, P, I, I, U64, P]),
         "dashsvd_selftest_bounded_wait": (I, [P, C.c_uint32]),
         "dashsvd_selftest_fail_alloc": (I, [I]),
+        "dashsvd_csr_check": (I, [P, P, P]),
+        "dashsvd_eig_fp64": (I, [P, P, I64, I, I, P, P]),
+        "dashsvd_get_profile": (I, [P, P, I64]),
         "dashsvd_mlp_forward": (I, [P, P, P, I64, P]),
         "dashsvd_mlp_loss_grad": (I, [P, P, P, P, P, I64, P, P]),
         "dashsvd_mlp_adam": (I, [P, P, P, P, P, I, C.c_float, C.c_float, C.c_float, C.c_float]),
@@ -150,6 +155,11 @@ dashsvd_spmm_fused = _export("dashsvd_spmm_fused")
 dashsvd_metrics = _export("dashsvd_metrics")
 dashsvd_selftest_bounded_wait = _export("dashsvd_selftest_bounded_wait")
 dashsvd_selftest_fail_alloc = _export("dashsvd_selftest_fail_alloc")
+dashsvd_csr_check = _export("dashsvd_csr_check")
+dashsvd_eig_fp64 = _export("dashsvd_eig_fp64")
+dashsvd_get_profile = _export("dashsvd_get_profile")
+PROFILE_CATEGORIES = ("gaussian", "spmm_fwd", "spmm_bwd", "gram", "eig", "project", "host_gap")
+DASHSVD_CSR_BAD_FIRST, DASHSVD_CSR_BAD_ORDER, DASHSVD_CSR_BAD_LAST, DASHSVD_CSR_BAD_COL = 1, 2, 4, 8
 dashsvd_mlp_forward = _export("dashsvd_mlp_forward")
 dashsvd_mlp_loss_grad = _export("dashsvd_mlp_loss_grad")
 dashsvd_mlp_adam = _export("dashsvd_mlp_adam")
@@ -258,8 +268,24 @@ class Handle:
         info = dashsvd_info()
         st = dashsvd_run(self.h, C.byref(A.struct()), k, s, max_passes, float(pve_tol), U.data_ptr(),
                          S.data_ptr(), V.data_ptr(), C.byref(info))
-        check(st, "dashsvd_run", ok=(DASHSVD_OK, DASHSVD_MAX_PASSES))
+        check(st, "dashsvd_run", ok=(DASHSVD_OK, DASHSVD_MAX_PASSES, DASHSVD_LEARNED_STOP))
         return U, S, V, info
+
+    def csr_check(self, A: CsrDevice) -> tuple[int, int]:
+        """Device check of A's structure: (status, failed-condition bits)."""
+        flags = C.c_uint32()
+        st = dashsvd_csr_check(self.h, C.byref(A.struct()), C.byref(flags))
+        return st, flags.value
+
+    def eig_fp64(self, G, l: int, iters: int = 3):
+        """FP64 eigenpairs (D descending, V columns) of an l x l FP64 device matrix."""
+        import torch
+
+        D = torch.empty((l,), dtype=torch.float64, device=G.device)
+        V = torch.empty((l, l), dtype=torch.float64, device=G.device)
+        check(dashsvd_eig_fp64(self.h, G.data_ptr(), G.stride(0), l, iters, D.data_ptr(), V.data_ptr()),
+              "dashsvd_eig_fp64")
+        return D, V
 
     def trace(self):
         """Per-pass records of the last run: list of (j, alpha_used, ratio, alpha_next, sweeps, Shat[l])."""
@@ -355,6 +381,15 @@ class Handle:
         check(dashsvd_project_bf16x3(self.h, Cm.data_ptr(), Cm.shape[0], l, Cm.stride(0), W.data_ptr(), W.stride(0),
                                      cols, out.data_ptr(), out.stride(0)), "dashsvd_project_bf16x3")
         return out
+
+    def profile(self) -> dict:
+        """Per-step device milliseconds (and launch-group counts) of the last
+        run made with profile=1."""
+        import numpy as np
+
+        buf = np.zeros(14, dtype=np.float64)
+        check(dashsvd_get_profile(self.h, buf.ctypes.data, buf.size), "dashsvd_get_profile")
+        return {c: (float(buf[i]), int(buf[7 + i])) for i, c in enumerate(PROFILE_CATEGORIES)}
 
     def tuning(self):
         """The autotuner's last measurements: (5 products x 10 variants) ms, 0 = not timed."""

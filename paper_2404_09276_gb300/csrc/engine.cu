@@ -67,6 +67,9 @@ T* as(DevBuf& b) {
   return reinterpret_cast<T*>(b.p);
 }
 
+// categories of dashsvd_get_profile (the order of include/dashsvd.h)
+enum ProfCat : int { kPfGauss = 0, kPfFwd, kPfBwd, kPfGram, kPfEig, kPfProject, kPfGap, kProfCats };
+
 struct GraphKey {
   dashsvd_csr A;
   int k, s, pmax;
@@ -97,6 +100,7 @@ struct dashsvd_handle_s {
   DevBuf Qb, G64;           // precision form: BF16 basis, FP64 Gram
   DevBuf mlpw, mlp_part;    // learned form: network parameters, gradient partials
   DevBuf fpw;               // fingerprint of the last run's matrix
+  DevBuf det_work;          // stable transposition (options.deterministic): radix-sort buffers
   // accuracy metrics (dashsvd_metrics): CSR of A^T, partitions, blocks, sums
   DevBuf mt_rowptr, mt_col, mt_val, mt_cursor, mt_scan, mt_seg_a, mt_seg_t, mt_T, mt_X, mt_Y, mt_Z, mt_C, mt_part,
       mt_sig, mt_out, mt_S, mt_V;
@@ -128,6 +132,14 @@ struct dashsvd_handle_s {
   std::vector<Tune> tuned;
   float tune_ms[5][10] = {};  // last autotuning: best time per (product, variant), ms; 0 = not timed
                              // (product 4, variant 0: the fused pass product)
+  // per-step device times of a host-driven run (options.profile): an event
+  // after each group of launches, tagged with the group's category
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_ev;
+  std::vector<int> prof_cat;
+  size_t prof_n = 0;
+  double prof_ms[kProfCats] = {};
+  int prof_cnt[kProfCats] = {};
 };
 
 namespace {
@@ -140,6 +152,21 @@ void drop_graph(dashsvd_handle h) {
   h->have_graph = false;
 }
 
+// Record a profiling event on `st`: the device work since the previous event
+// belongs to category `cat`. No-op unless a profiled host-driven run is on.
+cudaError_t tmark(dashsvd_handle h, int cat, cudaStream_t st) {
+  if (!h->prof_on) return cudaSuccess;
+  if (h->prof_n == h->prof_ev.size()) {
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreate(&ev);
+    if (e != cudaSuccess) return e;
+    h->prof_ev.push_back(ev);
+    h->prof_cat.push_back(0);
+  }
+  h->prof_cat[h->prof_n] = cat;
+  return cudaEventRecord(h->prof_ev[h->prof_n++], st);
+}
+
 bool csr_ok(const dashsvd_csr* A) {
   if (!A || A->m < 1 || A->n < 1 || A->nnz < 0 || A->nnz >= (int64_t)1 << 31) return false;
   if (A->m >= (int64_t)1 << 31 || A->n >= (int64_t)1 << 31) return false;
@@ -149,6 +176,11 @@ bool csr_ok(const dashsvd_csr* A) {
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// The device check of a CSR's structure (the fingerprint kernel's flags):
+// DASHSVD_OK, DASHSVD_EINVAL with *flags set, or an allocation / CUDA error.
+// Waits for the check. `fp` (may be null) receives the content fingerprint.
+int csr_device_check(dashsvd_handle h, const dashsvd_csr& A, unsigned* flags, unsigned long long* fp);
 
 // Everything one run launches, in order; `cond` is the loop's conditional
 // handle (0 when the host drives the loop).
@@ -196,7 +228,7 @@ bool direct_pve(dashsvd_handle h) { return h->opt.pve_mode == 1; }
 
 // Refinement iterations of the precision form's FP64 eigensolve, and the
 // rounding level of its BF16x3 Gram, which scales the null-column test of eigSVD.
-constexpr int kRefineIters = 2;
+constexpr int kRefineIters = 3;
 constexpr double kEpsBf16x3 = 1.52587890625e-05;  // 2^-16
 
 // eigSVD of C (rows x l): Gram, eigensolve with the control tail (the
@@ -206,21 +238,33 @@ cudaError_t eigsvd_step(dashsvd_handle h, const RunPlan& p, const float* C, int6
   cudaError_t e;
   if (precision(h)) {
     if ((e = launch_gram_tc(C, rows, p.l, p.ld, as<double>(h->G64), p.ld, as<float>(h->G), p.ld,
-                            as<float>(h->partial), as<int>(h->errw), h->num_sms, st)) != cudaSuccess)
+                            as<float>(h->partial), as<int>(h->errw), h->num_sms, st)) != cudaSuccess ||
+        (e = tmark(h, kPfGram, st)) != cudaSuccess)
       return e;
-    return launch_eig_refined(as<float>(h->G), p.ld, as<double>(h->G64), p.ld, kEpsBf16x3, kRefineIters,
-                              eig_args(h, p, mode, cond), eig_work_view(h->eigw.p), st);
+    if ((e = launch_eig_refined(as<float>(h->G), p.ld, as<double>(h->G64), p.ld, kEpsBf16x3, kRefineIters,
+                                eig_args(h, p, mode, cond), eig_work_view(h->eigw.p), st)) != cudaSuccess)
+      return e;
+    return tmark(h, kPfEig, st);
   }
   if ((e = launch_gram(C, rows, p.l, p.ld, as<float>(h->G), p.ld, as<float>(h->partial), h->num_sms, st)) !=
+          cudaSuccess ||
+      (e = tmark(h, kPfGram, st)) != cudaSuccess)
+    return e;
+  if ((e = launch_eig_f32(as<float>(h->G), p.ld, eig_args(h, p, mode, cond), eig_work_view(h->eigw.p), st)) !=
       cudaSuccess)
     return e;
-  return launch_eig_f32(as<float>(h->G), p.ld, eig_args(h, p, mode, cond), eig_work_view(h->eigw.p), st);
+  return tmark(h, kPfEig, st);
 }
 
 // Q <- Z W (the new basis): FP32 (SIMT in the plain form, BF16x3 tensor cores
 // in the precision form); with BF16 gathers, BF16 for the next gathers plus
 // FP32 once the loop is about to end (the final B = A Q uses the FP32 copy)
+cudaError_t project_basis_launch(dashsvd_handle h, const RunPlan& p, cudaStream_t st);
 cudaError_t project_basis(dashsvd_handle h, const RunPlan& p, cudaStream_t st) {
+  const cudaError_t e = project_basis_launch(h, p, st);
+  return e != cudaSuccess ? e : tmark(h, kPfProject, st);
+}
+cudaError_t project_basis_launch(dashsvd_handle h, const RunPlan& p, cudaStream_t st) {
   if (bf16_gathers(h)) {
     const Control* ctl = as<Control>(h->ctl);
     return launch_project_tc(as<float>(h->Z), p.nw, p.l, p.ld, as<float>(h->W), p.ld, p.l, as<float>(h->Q), p.ld,
@@ -236,10 +280,13 @@ cudaError_t project_basis(dashsvd_handle h, const RunPlan& p, cudaStream_t st) {
 cudaError_t launch_prologue(dashsvd_handle h, const RunPlan& p, unsigned long long cond, cudaStream_t st) {
   cudaError_t e;
   // Alg. 5 step 1: Omega (mw x l) into Y
-  if ((e = launch_gaussian(h->opt.seed, p.mw, p.l, 0, as<float>(h->Y), p.ld, st)) != cudaSuccess) return e;
+  if ((e = launch_gaussian(h->opt.seed, p.mw, p.l, 0, as<float>(h->Y), p.ld, st)) != cudaSuccess ||
+      (e = tmark(h, kPfGauss, st)) != cudaSuccess)
+    return e;
   // step 2: Z = A^T Omega, Q = eigSVD(Z)
   if ((e = launch_spmm(p.AwT, p.part_bwd, as<float>(h->Y), p.ld, p.l, as<float>(h->Z), p.ld, nullptr, nullptr, 0,
-                       p.var_bwd32, p.scr, h->num_sms, st, as<int>(h->errw))) != cudaSuccess)
+                       p.var_bwd32, p.scr, h->num_sms, st, as<int>(h->errw))) != cudaSuccess ||
+      (e = tmark(h, kPfBwd, st)) != cudaSuccess)
     return e;
   if ((e = eigsvd_step(h, p, as<float>(h->Z), p.nw, kModeInit, cond, st)) != cudaSuccess) return e;
   if ((e = project_basis(h, p, st)) != cudaSuccess) return e;
@@ -247,7 +294,8 @@ cudaError_t launch_prologue(dashsvd_handle h, const RunPlan& p, unsigned long lo
   // PVE control without the surrogate: B = A Q_0 (kept in Y for the first
   // pass) and its singular values, the p = 0 values of the criterion
   if ((e = launch_spmm(p.Aw, p.part_fwd, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld, nullptr, nullptr, 0,
-                       p.var_fwd, p.scr, h->num_sms, st, as<int>(h->errw))) != cudaSuccess)
+                       p.var_fwd, p.scr, h->num_sms, st, as<int>(h->errw))) != cudaSuccess ||
+      (e = tmark(h, kPfFwd, st)) != cudaSuccess)
     return e;
   return eigsvd_step(h, p, as<float>(h->Y), p.mw, kModeDirect, cond, st);
 }
@@ -259,33 +307,40 @@ cudaError_t launch_pass(dashsvd_handle h, const RunPlan& p, unsigned long long c
   if (direct_pve(h)) {
     // Y = A Q is already there (the end of the previous pass or the prologue)
     if ((e = launch_spmm(p.AwT, p.part_bwd, as<float>(h->Y), p.ld, p.l, as<float>(h->Z), p.ld, &ctl->alpha,
-                         as<float>(h->Q), p.ld, p.var_bwd, p.scr, h->num_sms, st, as<int>(h->errw))) != cudaSuccess)
+                         as<float>(h->Q), p.ld, p.var_bwd, p.scr, h->num_sms, st, as<int>(h->errw))) != cudaSuccess ||
+        (e = tmark(h, kPfBwd, st)) != cudaSuccess)
       return e;
     if ((e = eigsvd_step(h, p, as<float>(h->Z), p.nw, kModePass, cond, st)) != cudaSuccess) return e;
     if ((e = project_basis(h, p, st)) != cudaSuccess) return e;
     // B = A Q of the new basis, its singular values and the stop test
     if ((e = launch_spmm(p.Aw, p.part_fwd, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld, nullptr, nullptr, 0,
-                         p.var_fwd, p.scr, h->num_sms, st, as<int>(h->errw))) != cudaSuccess)
+                         p.var_fwd, p.scr, h->num_sms, st, as<int>(h->errw))) != cudaSuccess ||
+        (e = tmark(h, kPfFwd, st)) != cudaSuccess)
       return e;
     return eigsvd_step(h, p, as<float>(h->Y), p.mw, kModeDirect, cond, st);
   }
   if (bf16_gathers(h)) {
     if ((e = launch_spmm_bf16(p.Aw, p.part_fwd, h->Qb.p, p.ld, p.l, h->Y.p, true, p.ld, nullptr, nullptr, 0,
-                              p.var_fwd, p.scr, h->num_sms, st)) != cudaSuccess)
+                              p.var_fwd, p.scr, h->num_sms, st)) != cudaSuccess ||
+        (e = tmark(h, kPfFwd, st)) != cudaSuccess)
       return e;
     if ((e = launch_spmm_bf16(p.AwT, p.part_bwd, h->Y.p, p.ld, p.l, h->Z.p, false, p.ld, &ctl->alpha, h->Qb.p, p.ld,
-                              p.var_bwd, p.scr, h->num_sms, st)) != cudaSuccess)
+                              p.var_bwd, p.scr, h->num_sms, st)) != cudaSuccess ||
+        (e = tmark(h, kPfBwd, st)) != cudaSuccess)
       return e;
   } else if (p.fused) {  // one read of A: Z = A^T (A Q) - alpha Q, Y never stored
     if ((e = launch_spmm_fused(p.Aw, as<float>(h->Q), p.ld, p.l, &ctl->alpha, as<float>(h->Z), p.ld, h->num_sms,
-                               st)) != cudaSuccess)
+                               st)) != cudaSuccess ||
+        (e = tmark(h, kPfBwd, st)) != cudaSuccess)
       return e;
   } else {
     if ((e = launch_spmm(p.Aw, p.part_fwd, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld, nullptr, nullptr, 0,
-                         p.var_fwd, p.scr, h->num_sms, st, as<int>(h->errw))) != cudaSuccess)
+                         p.var_fwd, p.scr, h->num_sms, st, as<int>(h->errw))) != cudaSuccess ||
+        (e = tmark(h, kPfFwd, st)) != cudaSuccess)
       return e;
     if ((e = launch_spmm(p.AwT, p.part_bwd, as<float>(h->Y), p.ld, p.l, as<float>(h->Z), p.ld, &ctl->alpha,
-                         as<float>(h->Q), p.ld, p.var_bwd, p.scr, h->num_sms, st, as<int>(h->errw))) != cudaSuccess)
+                         as<float>(h->Q), p.ld, p.var_bwd, p.scr, h->num_sms, st, as<int>(h->errw))) != cudaSuccess ||
+        (e = tmark(h, kPfBwd, st)) != cudaSuccess)
       return e;
   }
   // steps 5-7 run inside the eig kernels' control tail
@@ -297,23 +352,27 @@ cudaError_t launch_final(dashsvd_handle h, const RunPlan& p, cudaStream_t st) {
   cudaError_t e;
   // step 9: B = A Q (into Y), from the FP32 basis in both forms (already
   // there when the PVE control works on B directly)
-  if (!direct_pve(h) && (e = launch_spmm(p.Aw, p.part_fwd, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld,
-                                         nullptr, nullptr, 0, p.var_fwd32, p.scr, h->num_sms, st,
-                                         as<int>(h->errw))) != cudaSuccess)
+  if (!direct_pve(h) && ((e = launch_spmm(p.Aw, p.part_fwd, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld,
+                                          nullptr, nullptr, 0, p.var_fwd32, p.scr, h->num_sms, st,
+                                          as<int>(h->errw))) != cudaSuccess ||
+                         (e = tmark(h, kPfFwd, st)) != cudaSuccess))
     return e;
   // steps 10-11: eigSVD(B); U = B V_k S_k^-1; V = Q V_k
   if ((e = eigsvd_step(h, p, as<float>(h->Y), p.mw, kModeFinal, 0, st)) != cudaSuccess) return e;
   if (precision(h)) {
     if ((e = launch_project_tc(as<float>(h->Y), p.mw, p.l, p.ld, as<float>(h->W), p.ld, p.k, p.Uw, p.k, nullptr, 0,
+                               nullptr, as<int>(h->errw), h->num_sms, st)) != cudaSuccess ||
+        (e = launch_project_tc(as<float>(h->Q), p.nw, p.l, p.ld, as<float>(h->W2), p.ld, p.k, p.Vw, p.k, nullptr, 0,
                                nullptr, as<int>(h->errw), h->num_sms, st)) != cudaSuccess)
       return e;
-    return launch_project_tc(as<float>(h->Q), p.nw, p.l, p.ld, as<float>(h->W2), p.ld, p.k, p.Vw, p.k, nullptr, 0,
-                             nullptr, as<int>(h->errw), h->num_sms, st);
+    return tmark(h, kPfProject, st);
   }
   if ((e = launch_project(as<float>(h->Y), p.mw, p.l, p.ld, as<float>(h->W), p.ld, p.k, p.Uw, p.k, h->num_sms, st)) !=
-      cudaSuccess)
+          cudaSuccess ||
+      (e = launch_project(as<float>(h->Q), p.nw, p.l, p.ld, as<float>(h->W2), p.ld, p.k, p.Vw, p.k, h->num_sms, st)) !=
+          cudaSuccess)
     return e;
-  return launch_project(as<float>(h->Q), p.nw, p.l, p.ld, as<float>(h->W2), p.ld, p.k, p.Vw, p.k, h->num_sms, st);
+  return tmark(h, kPfProject, st);
 }
 
 int build_graph(dashsvd_handle h, const RunPlan& p) {
@@ -487,9 +546,48 @@ int autotune_spmm(dashsvd_handle h, RunPlan& p, const dashsvd_csr& A) {
   return DASHSVD_OK;
 }
 
+int csr_device_check(dashsvd_handle h, const dashsvd_csr& A, unsigned* flags, unsigned long long* fp) {
+  bool moved = false;
+  int rc;
+  if ((rc = ensure(h->fpw, 16, &moved))) return rc;
+  if (moved) h->have_graph = false;
+  unsigned long long w[2] = {0, 0};
+  DS_CUDA(launch_fingerprint(A, as<unsigned long long>(h->fpw), h->num_sms, h->stream));
+  DS_CUDA(cudaMemcpyAsync(w, h->fpw.p, sizeof(w), cudaMemcpyDeviceToHost, h->stream));
+  DS_CUDA(cudaStreamSynchronize(h->stream));
+  if (flags) *flags = (unsigned)w[1];
+  if (fp) *fp = w[0];
+  return w[1] ? DASHSVD_EINVAL : DASHSVD_OK;
+}
+
+// The CSR of A^T into (rowptr_t, colidx_t, val_t): a stable counting sort with
+// options.deterministic (rows of A^T in increasing row order of A), else the
+// atomic scatter (entries of a row of A^T in arrival order).
+int transpose_into(dashsvd_handle h, const dashsvd_csr& A, int32_t* rowptr_t, int32_t* colidx_t, float* val_t,
+                   int32_t* cursor, int32_t* scan, cudaStream_t st) {
+  if (h->opt.deterministic) {
+    bool moved = false;
+    if (const int rc = ensure(h->det_work, sizeof(int32_t) * stable_transpose_ints(A.nnz), &moved)) return rc;
+    if (moved) h->have_graph = false;
+    DS_CUDA(launch_csr_transpose_stable(A, rowptr_t, colidx_t, val_t, cursor, scan, as<int32_t>(h->det_work), st));
+    return DASHSVD_OK;
+  }
+  DS_CUDA(launch_csr_transpose(A, rowptr_t, colidx_t, val_t, cursor, scan, st));
+  return DASHSVD_OK;
+}
+
+// Step-level entry points check the structure of the CSR they are given
+// unless the handle was created with options.trust_csr = 1.
+int step_csr_ok(dashsvd_handle h, const dashsvd_csr* A) {
+  if (!csr_ok(A)) return DASHSVD_EINVAL;
+  if (h->opt.trust_csr) return DASHSVD_OK;
+  return csr_device_check(h, *A, nullptr, nullptr);
+}
+
 int status_from_control(const Control& c) {
   if (c.status & kStatusNonFinite) return DASHSVD_ENONFINITE;
   if (c.status & kStatusNoConv) return DASHSVD_ENOCONV;
+  if (c.stop == 2) return DASHSVD_LEARNED_STOP;
   return c.stop ? DASHSVD_OK : DASHSVD_MAX_PASSES;
 }
 
@@ -516,6 +614,7 @@ const char* dashsvd_status_string(int status) {
   switch (status) {
     case DASHSVD_OK: return "ok: PVE tolerance met";
     case DASHSVD_MAX_PASSES: return "max_passes reached (results valid)";
+    case DASHSVD_LEARNED_STOP: return "stopped by the learned network with the PVE surrogate within 3 tol (results valid)";
     case DASHSVD_EINVAL: return "invalid argument";
     case DASHSVD_ENOMEM: return "device memory allocation failed";
     case DASHSVD_ECUDA: return "CUDA error";
@@ -572,11 +671,12 @@ int dashsvd_destroy(dashsvd_handle h) {
   DevBuf* bufs[] = {&h->rowptr_b, &h->col_b, &h->val_b, &h->cursor, &h->scan_tmp, &h->Y,       &h->Z,
                     &h->Q,        &h->G,     &h->W,     &h->W2,     &h->partial,  &h->carry, &h->carry_row,
                     &h->ctl,      &h->trace, &h->eigw,   &h->seg_fwd, &h->seg_bwd, &h->errw, &h->Qb, &h->G64,
-                    &h->mlpw, &h->mlp_part, &h->fpw, &h->mt_rowptr, &h->mt_col, &h->mt_val, &h->mt_cursor,
+                    &h->mlpw, &h->mlp_part, &h->fpw, &h->det_work, &h->mt_rowptr, &h->mt_col, &h->mt_val, &h->mt_cursor,
                     &h->mt_scan, &h->mt_seg_a, &h->mt_seg_t, &h->mt_T, &h->mt_X, &h->mt_Y, &h->mt_Z, &h->mt_C,
                     &h->mt_part, &h->mt_sig, &h->mt_out, &h->mt_S, &h->mt_V};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
+  for (cudaEvent_t ev : h->prof_ev) cudaEventDestroy(ev);
   if (h->side) cudaStreamDestroy(h->side);
   if (h->cap) cudaStreamDestroy(h->cap);
   delete h;
@@ -637,10 +737,20 @@ int dashsvd_get_tuning(dashsvd_handle h, float* ms, int64_t cap) {
   return DASHSVD_OK;
 }
 
+int dashsvd_get_profile(dashsvd_handle h, double* ms, int64_t cap) {
+  if (!h || !ms || cap < 2 * kProfCats) return DASHSVD_EINVAL;
+  for (int c = 0; c < kProfCats; ++c) {
+    ms[c] = h->prof_ms[c];
+    ms[kProfCats + c] = h->prof_cnt[c];
+  }
+  return DASHSVD_OK;
+}
+
 int dashsvd_spmm_fused(dashsvd_handle h, const dashsvd_csr* A, const float* Q, int64_t ldq, int l,
                        const double* alpha, float* Z, int64_t ldz) {
   if (!h || !csr_ok(A) || !Q || !Z || l < 1 || l > DASHSVD_MAX_L) return DASHSVD_EINVAL;
   if (ldq < l || ldz < l || ldq % 4 || ldz % 4 || !aligned16(Q) || !aligned16(Z)) return DASHSVD_EINVAL;
+  if (const int rc0 = step_csr_ok(h, A)) return rc0;
   DS_CUDA(launch_spmm_fused(*A, Q, ldq, l, alpha, Z, ldz, h->num_sms, h->stream));
   return DASHSVD_OK;
 }
@@ -669,6 +779,7 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
   if (h->opt.gather_bf16 && h->opt.spmm_variant >= kSpmmVariantsBf16) return DASHSVD_EINVAL;
   if (h->opt.learned && (!h->mlp_loaded || h->opt.shift != 1)) return DASHSVD_EINVAL;
   if (h->opt.pve_mode < 0 || h->opt.pve_mode > 1) return DASHSVD_EINVAL;
+  if (h->opt.deterministic && h->opt.spmm_variant == kSpmmFused) return DASHSVD_EINVAL;
   if (direct_pve(h) && (h->opt.learned || h->opt.gather_bf16 || h->opt.spmm_variant == kSpmmFused))
     return DASHSVD_EINVAL;
   if ((h->opt.form != DASHSVD_FORM_PLAIN && h->opt.form != DASHSVD_FORM_PRECISION) || h->opt.learned < 0 ||
@@ -742,35 +853,40 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
   p.part_bwd.seg_nnz = p.part_bwd.seg_row + p.part_bwd.segments + 1;
   const int forced = h->opt.spmm_variant;
   // a forced variant 10 means the fused pass product (the other products use variant 1)
-  p.var_fwd = p.var_fwd32 = forced >= 0 && forced < kSpmmVariants ? forced : 1;
-  p.var_bwd = p.var_bwd32 = forced >= 0 && forced < kSpmmVariants ? forced : 1;
+  // unforced: autotuned below, or with options.deterministic the fixed
+  // variant 5 (the tuner's timing-dependent choice would change the
+  // summation order from run to run)
+  const int dflt = h->opt.deterministic ? 5 : 1;
+  p.var_fwd = p.var_fwd32 = forced >= 0 && forced < kSpmmVariants ? forced : dflt;
+  p.var_bwd = p.var_bwd32 = forced >= 0 && forced < kSpmmVariants ? forced : dflt;
   p.fused = forced == kSpmmFused;
 
   cudaStream_t st = h->stream;
   // setup (Sec. 8(d) reports it apart from the iteration): the CSR of the
   // transpose and the merge-path partitions, rebuilt only when the matrix changed
-  if ((rc = ensure(h->fpw, 16, &moved))) return rc;
+  // the structure check (row pointers from 0 to nnz, non-decreasing; column ids
+  // in [0, n)) rides on the fingerprint's read: nothing gathers before it passed
   unsigned long long fp = 0;
-  DS_CUDA(launch_fingerprint(*A, as<unsigned long long>(h->fpw), h->num_sms, st));
-  DS_CUDA(cudaMemcpyAsync(&fp, h->fpw.p, sizeof(fp), cudaMemcpyDeviceToHost, st));
-  DS_CUDA(cudaStreamSynchronize(st));
+  unsigned bad = 0;
+  if ((rc = csr_device_check(h, *A, &bad, &fp)) != DASHSVD_OK) return rc;
   const dashsvd_handle_s::SetupKey skey{A->rowptr, A->colidx, A->val, A->m, A->n, A->nnz, fp,
                                         p.part_fwd.segments, p.part_bwd.segments};
   const bool reuse = h->setup_valid && !moved && std::memcmp(&skey, &h->setup, sizeof(skey)) == 0;
   if (!reuse) {
     h->setup_valid = false;
-    DS_CUDA(launch_csr_transpose(*A, as<int32_t>(h->rowptr_b), as<int32_t>(h->col_b), as<float>(h->val_b),
-                                 as<int32_t>(h->cursor), as<int32_t>(h->scan_tmp), st));
+    if ((rc = transpose_into(h, *A, as<int32_t>(h->rowptr_b), as<int32_t>(h->col_b), as<float>(h->val_b),
+                             as<int32_t>(h->cursor), as<int32_t>(h->scan_tmp), st)) != DASHSVD_OK)
+      return rc;
     DS_CUDA(launch_spmm_partition(p.Aw, p.part_fwd, st));
     DS_CUDA(launch_spmm_partition(p.AwT, p.part_bwd, st));
     h->setup = skey;
     h->setup_valid = true;
   }
-  if (forced < 0 && (rc = autotune_spmm(h, p, *A)) != DASHSVD_OK) return rc;
+  if (forced < 0 && !h->opt.deterministic && (rc = autotune_spmm(h, p, *A)) != DASHSVD_OK) return rc;
   if (direct_pve(h)) p.fused = false;  // B = A Q is stored every pass
   DS_CUDA(cudaMemsetAsync(h->errw.p, 0, sizeof(int), st));
 
-  if (h->opt.use_graph) {
+  if (h->opt.use_graph && !h->opt.profile) {
     GraphKey key;
     std::memset(&key, 0, sizeof(key));
     key.A = *A;
@@ -797,15 +913,35 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
     }
     DS_CUDA(cudaGraphLaunch(h->exec, st));
   } else {
-    DS_CUDA(launch_prologue(h, p, 0, st));
-    Control hc;
-    for (int j = 0; j < max_passes; ++j) {
-      DS_CUDA(cudaMemcpyAsync(&hc, h->ctl.p, sizeof(Control), cudaMemcpyDeviceToHost, st));
+    h->prof_on = h->opt.profile != 0;
+    h->prof_n = 0;
+    std::memset(h->prof_ms, 0, sizeof(h->prof_ms));
+    std::memset(h->prof_cnt, 0, sizeof(h->prof_cnt));
+    const int rc_loop = [&]() -> int {
+      DS_CUDA(tmark(h, kPfGap, st));
+      DS_CUDA(launch_prologue(h, p, 0, st));
+      Control hc;
+      for (int j = 0; j < max_passes; ++j) {
+        DS_CUDA(cudaMemcpyAsync(&hc, h->ctl.p, sizeof(Control), cudaMemcpyDeviceToHost, st));
+        DS_CUDA(cudaStreamSynchronize(st));
+        if (!hc.cont) break;
+        DS_CUDA(tmark(h, kPfGap, st));  // the host's wait between passes
+        DS_CUDA(launch_pass(h, p, 0, st));
+      }
+      DS_CUDA(launch_final(h, p, st));
+      return DASHSVD_OK;
+    }();
+    if (h->prof_on && rc_loop == DASHSVD_OK) {
       DS_CUDA(cudaStreamSynchronize(st));
-      if (!hc.cont) break;
-      DS_CUDA(launch_pass(h, p, 0, st));
+      for (size_t i = 1; i < h->prof_n; ++i) {
+        float ms = 0.f;
+        DS_CUDA(cudaEventElapsedTime(&ms, h->prof_ev[i - 1], h->prof_ev[i]));
+        h->prof_ms[h->prof_cat[i]] += ms;
+        h->prof_cnt[h->prof_cat[i]] += 1;
+      }
     }
-    DS_CUDA(launch_final(h, p, st));
+    h->prof_on = false;
+    if (rc_loop != DASHSVD_OK) return rc_loop;
   }
   Control hc;
   int werr = 0;
@@ -826,7 +962,7 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
     DevBuf* bufs[] = {&h->rowptr_b, &h->col_b, &h->val_b, &h->cursor, &h->scan_tmp, &h->Y,       &h->Z,
                       &h->Q,        &h->G,     &h->W,     &h->W2,     &h->partial,  &h->carry, &h->carry_row,
                       &h->ctl,      &h->trace, &h->eigw,   &h->seg_fwd, &h->seg_bwd, &h->errw, &h->Qb, &h->G64,
-                    &h->mlpw, &h->mlp_part, &h->fpw, &h->mt_rowptr, &h->mt_col, &h->mt_val, &h->mt_cursor,
+                    &h->mlpw, &h->mlp_part, &h->fpw, &h->det_work, &h->mt_rowptr, &h->mt_col, &h->mt_val, &h->mt_cursor,
                     &h->mt_scan, &h->mt_seg_a, &h->mt_seg_t, &h->mt_T, &h->mt_X, &h->mt_Y, &h->mt_Z, &h->mt_C,
                     &h->mt_part, &h->mt_sig, &h->mt_out, &h->mt_S, &h->mt_V};
     for (DevBuf* b : bufs) ws += (int64_t)b->bytes;
@@ -849,14 +985,14 @@ int dashsvd_csr_transpose(dashsvd_handle h, const dashsvd_csr* A, int32_t* rowpt
                           float* val_t) {
   if (!h || !csr_ok(A) || !rowptr_t || (A->nnz > 0 && (!colidx_t || !val_t))) return DASHSVD_EINVAL;
   int rc;
+  if ((rc = step_csr_ok(h, A)) != DASHSVD_OK) return rc;
   bool moved = false;
   if ((rc = ensure(h->cursor, sizeof(int32_t) * (size_t)A->n, &moved)) ||
       (rc = ensure(h->scan_tmp, sizeof(int32_t) * scan_tmp_ints(A->n), &moved)))
     return rc;
   if (moved) h->have_graph = false;
-  DS_CUDA(launch_csr_transpose(*A, rowptr_t, colidx_t, val_t, as<int32_t>(h->cursor), as<int32_t>(h->scan_tmp),
-                               h->stream));
-  return DASHSVD_OK;
+  return transpose_into(h, *A, rowptr_t, colidx_t, val_t, as<int32_t>(h->cursor), as<int32_t>(h->scan_tmp),
+                        h->stream);
 }
 
 static int spmm_common(dashsvd_handle h, const dashsvd_csr* A, const float* X, int64_t ldx, int l, float* Y,
@@ -865,6 +1001,7 @@ static int spmm_common(dashsvd_handle h, const dashsvd_csr* A, const float* X, i
   if (ldx < l || ldy < l || ldx % 4 || ldy % 4 || !aligned16(X) || !aligned16(Y)) return DASHSVD_EINVAL;
   if (alpha && (!Q || ldq < l || ldq % 4 || !aligned16(Q))) return DASHSVD_EINVAL;
   if (variant < -1 || variant >= kSpmmVariants) return DASHSVD_EINVAL;
+  if (const int rc0 = step_csr_ok(h, A)) return rc0;
   SpmmPart part;
   part.segments = spmm_segments(*A, h->num_sms);
   const int64_t ldc = ((l + 3) / 4) * 4;
@@ -914,6 +1051,7 @@ int dashsvd_spmm_bf16(dashsvd_handle h, const dashsvd_csr* A, const void* X, int
     return DASHSVD_EINVAL;
   if (alpha && (!Q || ldq < l || ldq % 4 || ((uintptr_t)Q & 7u))) return DASHSVD_EINVAL;
   if (variant < -1 || variant >= kSpmmVariantsBf16) return DASHSVD_EINVAL;
+  if (const int rc0 = step_csr_ok(h, A)) return rc0;
   SpmmPart part;
   part.segments = spmm_segments(*A, h->num_sms);
   const int64_t ldc = ((l + 3) / 4) * 4;
@@ -1047,6 +1185,34 @@ int dashsvd_eigsvd(dashsvd_handle h, const float* C, int64_t rows, int l, int64_
   return DASHSVD_OK;
 }
 
+int dashsvd_csr_check(dashsvd_handle h, const dashsvd_csr* A, uint32_t* flags) {
+  if (flags) *flags = 0;
+  if (!h || !csr_ok(A)) return DASHSVD_EINVAL;
+  unsigned bad = 0;
+  const int rc = csr_device_check(h, *A, &bad, nullptr);
+  if (flags) *flags = bad;
+  return rc;
+}
+
+int dashsvd_eig_fp64(dashsvd_handle h, const double* G, int64_t ldg, int l, int iters, double* D, double* V) {
+  if (!h || !G || !D || !V || l < 1 || l > DASHSVD_MAX_L || ldg < l || iters < 0 || iters > 8)
+    return DASHSVD_EINVAL;
+  const int64_t ld = round_up(l, 8);
+  int rc;
+  bool moved = false;
+  if ((rc = ensure(h->G, sizeof(float) * (size_t)(ld * ld), &moved)) ||
+      (rc = ensure(h->eigw, eig_work_bytes(), &moved)))
+    return rc;
+  if (moved) h->have_graph = false;
+  cudaStream_t st = h->stream;
+  const EigWork wk = eig_work_view(h->eigw.p);
+  DS_CUDA(launch_eig_fp64(G, ldg, l, iters, as<float>(h->G), ld, D, V, wk, st));
+  int hdr[2] = {0, 0};
+  DS_CUDA(cudaMemcpyAsync(hdr, wk.hdr, sizeof(hdr), cudaMemcpyDeviceToHost, st));
+  DS_CUDA(cudaStreamSynchronize(st));
+  return (hdr[1] & kStatusNoConv) ? DASHSVD_ENOCONV : DASHSVD_OK;
+}
+
 // ------------------------------------------------------------------ metrics
 
 int dashsvd_metrics(dashsvd_handle h, const dashsvd_csr* A, int k, const float* U, int64_t ldu, const float* S,
@@ -1059,6 +1225,7 @@ int dashsvd_metrics(dashsvd_handle h, const dashsvd_csr* A, int k, const float* 
     return DASHSVD_EINVAL;
   for (int i = 0; i <= k; ++i)
     if (!(sigma_ref[i] > 0.0) || !std::isfinite(sigma_ref[i])) return DASHSVD_EINVAL;
+  if (const int rc0 = step_csr_ok(h, A)) return rc0;
   for (int i = 0; i < 5; ++i) out[i] = std::nan("");
   cudaStream_t st = h->stream;
   const int nsm = h->num_sms;
@@ -1101,8 +1268,9 @@ int dashsvd_metrics(dashsvd_handle h, const dashsvd_csr* A, int k, const float* 
   At.rowptr = as<int32_t>(h->mt_rowptr);
   At.colidx = as<int32_t>(h->mt_col);
   At.val = as<float>(h->mt_val);
-  DS_CUDA(launch_csr_transpose(*A, as<int32_t>(h->mt_rowptr), as<int32_t>(h->mt_col), as<float>(h->mt_val),
-                               as<int32_t>(h->mt_cursor), as<int32_t>(h->mt_scan), st));
+  if ((rc = transpose_into(h, *A, as<int32_t>(h->mt_rowptr), as<int32_t>(h->mt_col), as<float>(h->mt_val),
+                           as<int32_t>(h->mt_cursor), as<int32_t>(h->mt_scan), st)) != DASHSVD_OK)
+    return rc;
   pa.seg_row = as<int32_t>(h->mt_seg_a);
   pa.seg_nnz = pa.seg_row + pa.segments + 1;
   pt.seg_row = as<int32_t>(h->mt_seg_t);

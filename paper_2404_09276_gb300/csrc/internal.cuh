@@ -18,7 +18,7 @@ struct Control {
   double ratio;       // last surrogate PVE ratio
   double ratio_prev;  // the ratio of the pass before (learned-form feature)
   int32_t pass;       // power iterations done
-  int32_t stop;       // 1 once the PVE test has passed
+  int32_t stop;       // 1 once the PVE test has passed; 2 once the learned network stopped the run
   int32_t status;     // kStatus* bit flags
   int32_t cont;       // 1 while another pass should run
   int32_t sweeps;     // Jacobi sweeps of the last eigensolve
@@ -70,8 +70,15 @@ cudaError_t launch_csr_transpose(const dashsvd_csr& A, int32_t* rowptr_t, int32_
                                  float* val_t, int32_t* cursor, int32_t* scan_tmp,
                                  cudaStream_t st);
 size_t scan_tmp_ints(int64_t n);
+// Stable CSR transpose (rows of A^T list their entries in increasing row order
+// of A): `work` holds stable_transpose_ints(nnz) int32.
+size_t stable_transpose_ints(int64_t nnz);
+cudaError_t launch_csr_transpose_stable(const dashsvd_csr& A, int32_t* rowptr_t, int32_t* colidx_t, float* val_t,
+                                        int32_t* cursor, int32_t* scan_tmp, int32_t* work, cudaStream_t st);
 // 64-bit order-independent fingerprint of the three CSR arrays (m, n, nnz are
-// compared separately), to recognize a matrix that has not changed.
+// compared separately), to recognize a matrix that has not changed, into
+// out[0]; the structure check's kCsrBad* bits into out[1] (two words).
+enum : unsigned { kCsrBadFirst = 1, kCsrBadOrder = 2, kCsrBadLast = 4, kCsrBadCol = 8 };
 cudaError_t launch_fingerprint(const dashsvd_csr& A, unsigned long long* out, int num_sms, cudaStream_t st);
 
 // SpMM Y = A X (alpha == nullptr) or Y = A X - alpha Q.
@@ -140,6 +147,10 @@ EigWork eig_work_view(void* base);
 cudaError_t launch_eig_f32(const float* G, int64_t ldg, const EigArgs& a, const EigWork& wk, cudaStream_t st);
 cudaError_t launch_eig_refined(const float* G32, int64_t ldg32, const double* G64, int64_t ldg64, double eps_null,
                                int iters, const EigArgs& a, const EigWork& wk, cudaStream_t st);
+// The precision form's eigensolver alone: FP64 eigenpairs of an FP64 Gram
+// (descending, signed), after `iters` refinement steps (0: FP32 Jacobi only).
+cudaError_t launch_eig_fp64(const double* G, int64_t ldg, int l, int iters, float* G32, int64_t ld32, double* D,
+                            double* V, const EigWork& wk, cudaStream_t st);
 // FP64 iterative refinement of an approximate eigenbasis V32 of G64 (Ogita and
 // Aishima); *X receives the refined basis (inside wk), wk.lam64 the eigenvalues.
 cudaError_t launch_refine_fp64(const double* G64, int64_t ldg, const float* V32, int l, int iters, const EigWork& wk,

@@ -35,10 +35,6 @@ namespace {
 constexpr int kJacThreads = 1024;
 constexpr int kMaxN = kMaxL;  // N <= 256
 constexpr float kEps32 = 1.1920929e-07f;
-// Jacobi skip threshold (relative, |G_pq| <= tol sqrt(G_pp G_qq)) when the
-// result is refined in FP64 afterwards: two quadratically convergent
-// refinement steps take an off-diagonal residue of 1e-4 to FP64 rounding
-constexpr float kRefinedJacobiTol = 1e-4f;
 
 
 // Packed upper triangle: element (a, b), a <= b, of an N x N matrix at
@@ -494,7 +490,9 @@ __global__ void __launch_bounds__(kVecWarps * 32) finish_kernel(const T* __restr
     if (a.mlp) {
       const float o0 = fs.out[0], o1 = fs.out[1];
       if (isfinite(o0)) f = 1.0 / (1.0 + exp(-(double)o0));
-      if (!stop && a.tol > 0.0 && j >= 2 && ratio <= kMlpSoftTol * a.tol && o1 > 0.f && !nonfinite) stop = 1;
+      // a stop the network makes before the surrogate test passes is marked 2
+      // (reported as DASHSVD_LEARNED_STOP, not as a met tolerance)
+      if (!stop && a.tol > 0.0 && j >= 2 && ratio <= kMlpSoftTol * a.tol && o1 > 0.f && !nonfinite) stop = 2;
     }
     double alpha_next = alpha;
     if (!stop && a.shift == 1) {
@@ -531,6 +529,49 @@ __global__ void __launch_bounds__(kVecWarps * 32) finish_kernel(const T* __restr
     if (!stop) ctl->S_prev[r] = fs.S[r];
     ctl->S[r] = fs.S[r];
     if (a.trace) a.trace[(int64_t)(j - 1) * (5 + l) + 5 + r] = fs.S[r];
+  }
+}
+
+// G (FP64) rounded to FP32 for the Jacobi sweeps that start the FP64 eigensolver
+__global__ void g64_to_g32_kernel(const double* __restrict__ G, int64_t ldg, int l, float* __restrict__ G32,
+                                  int64_t ld32) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)l * l;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(i / l), c = (int)(i - (int64_t)r * l);
+    G32[(int64_t)r * ld32 + c] = (float)G[(int64_t)r * ldg + c];
+  }
+}
+
+// Eigenpairs (d, columns of the row-major V) in descending order of d (ties by
+// lower index), each vector signed so that its largest-|.| entry (lowest index
+// on ties) is positive, written as FP64: D[r], Vout[j * l + r]. One CTA.
+template <typename T>
+__global__ void __launch_bounds__(256) eig_export_kernel(const T* __restrict__ d, const T* __restrict__ V, int l,
+                                                         double* __restrict__ D, double* __restrict__ Vout) {
+  __shared__ int rank[kMaxL];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < l; i += nt) {
+    const double di = (double)d[i];
+    int r = 0;
+    for (int j = 0; j < l; ++j) {
+      const double dj = (double)d[j];
+      r += (dj > di) || (dj == di && j < i);
+    }
+    rank[i] = r < l ? r : l - 1;
+    D[rank[i]] = di;
+  }
+  __syncthreads();
+  for (int c = tid; c < l; c += nt) {
+    double best = -1.0, sg = 1.0;
+    for (int j = 0; j < l; ++j) {
+      const double v = (double)V[(int64_t)j * l + c];
+      if (fabs(v) > best) {
+        best = fabs(v);
+        sg = v < 0.0 ? -1.0 : 1.0;
+      }
+    }
+    const int r = rank[c];
+    for (int j = 0; j < l; ++j) Vout[(int64_t)j * l + r] = sg * (double)V[(int64_t)j * l + c];
   }
 }
 
@@ -589,9 +630,13 @@ cudaError_t launch_eig_f32(const float* G, int64_t ldg, const EigArgs& a, const 
 cudaError_t launch_eig_refined(const float* G32, int64_t ldg32, const double* G64, int64_t ldg64, double eps_null,
                                int iters, const EigArgs& a, const EigWork& wk, cudaStream_t st) {
   if (a.l < 1 || a.l > kMaxL) return cudaErrorInvalidValue;
-  // the FP64 refinement converges quadratically from the Jacobi basis, so the
-  // sweeps stop at a looser threshold (pairs below kRefinedJacobiTol are left)
-  jacobi_f32_kernel<<<1, kJacThreads, jacobi_smem(a.l), st>>>(G32, ldg32, a.l, wk, kRefinedJacobiTol);
+  // the Jacobi sweeps run to FP32 rounding, as in the plain form: the
+  // refinement's first-order corrections are only taken for pairs whose
+  // eigenvalue gap exceeds its threshold delta, which is of the size of the
+  // starting basis's off-diagonal residue summed over all pairs; a looser
+  // start (1e-4) leaves close pairs uncorrected (about 1e-6 relative error on
+  // Wishart-like Grams) however many steps follow
+  jacobi_f32_kernel<<<1, kJacThreads, jacobi_smem(a.l), st>>>(G32, ldg32, a.l, wk, kEps32);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   eigvec_replay_kernel<<<(unsigned)ds_ceil_div(a.l, kReplayWarps), kReplayWarps * 32, 0, st>>>(wk, a.l);
@@ -600,6 +645,30 @@ cudaError_t launch_eig_refined(const float* G32, int64_t ldg32, const double* G6
   const double* X = nullptr;
   if ((e = launch_refine_fp64(G64, ldg64, wk.V32, a.l, iters, wk, &X, st)) != cudaSuccess) return e;
   finish_kernel<double><<<blocks, kVecWarps * 32, 0, st>>>(wk.lam64, X, wk.d0_64, eps_null, wk.hdr, a);
+  return cudaGetLastError();
+}
+
+// The precision form's eigensolver on its own (FP64 Gram in, FP64 eigenpairs
+// out): FP32 Jacobi on the rounded Gram, then `iters` FP64 refinement steps
+// against the FP64 Gram (none: the FP32 result, widened). G32 is an ld32 x l
+// FP32 scratch matrix.
+cudaError_t launch_eig_fp64(const double* G, int64_t ldg, int l, int iters, float* G32, int64_t ld32, double* D,
+                            double* V, const EigWork& wk, cudaStream_t st) {
+  if (l < 1 || l > kMaxL || iters < 0) return cudaErrorInvalidValue;
+  g64_to_g32_kernel<<<(unsigned)ds_ceil_div((int64_t)l * l, 256), 256, 0, st>>>(G, ldg, l, G32, ld32);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  jacobi_f32_kernel<<<1, kJacThreads, jacobi_smem(l), st>>>(G32, ld32, l, wk, kEps32);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  eigvec_replay_kernel<<<(unsigned)ds_ceil_div(l, kReplayWarps), kReplayWarps * 32, 0, st>>>(wk, l);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (iters == 0) {
+    eig_export_kernel<float><<<1, 256, 0, st>>>(wk.d, wk.V32, l, D, V);
+    return cudaGetLastError();
+  }
+  const double* X = nullptr;
+  if ((e = launch_refine_fp64(G, ldg, wk.V32, l, iters, wk, &X, st)) != cudaSuccess) return e;
+  eig_export_kernel<double><<<1, 256, 0, st>>>(wk.lam64, X, l, D, V);
   return cudaGetLastError();
 }
 

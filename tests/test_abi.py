@@ -46,6 +46,7 @@ def test_struct_layout_matches_header(ds, tmp_path):
         'printf("%zu %zu %zu\\n", sizeof(dashsvd_csr), sizeof(dashsvd_options), sizeof(dashsvd_info));\n'
         'printf("%zu %zu %zu\\n", offsetof(dashsvd_csr, val), offsetof(dashsvd_options, shift), '
         "offsetof(dashsvd_info, eig_sweeps));\n"
+        'printf("%zu %zu\\n", offsetof(dashsvd_options, trust_csr), offsetof(dashsvd_options, deterministic));\n'
         'printf("%d %d\\n", DASHSVD_MAX_L, (int)DASHSVD_ENOCONV);\n'
         "return 0;}\n"
     )
@@ -56,7 +57,8 @@ def test_struct_layout_matches_header(ds, tmp_path):
     offs = [int(x) for x in out[3:6]]
     assert sizes == [C.sizeof(ds.dashsvd_csr), C.sizeof(ds.dashsvd_options), C.sizeof(ds.dashsvd_info)]
     assert offs == [ds.dashsvd_csr.val.offset, ds.dashsvd_options.shift.offset, ds.dashsvd_info.eig_sweeps.offset]
-    assert int(out[6]) == ds.DASHSVD_MAX_L and int(out[7]) == ds.DASHSVD_ENOCONV
+    assert [int(x) for x in out[6:8]] == [ds.dashsvd_options.trust_csr.offset, ds.dashsvd_options.deterministic.offset]
+    assert int(out[8]) == ds.DASHSVD_MAX_L and int(out[9]) == ds.DASHSVD_ENOCONV
 
 
 def test_options_defaults(ds):
@@ -82,6 +84,8 @@ def test_argument_checks_before_cuda(ds):
     assert ds.dashsvd_gram(None, None, 10, 4, 4, None, 4) == E
     assert ds.dashsvd_spmm(None, None, None, 4, 4, None, 4, -1) == E
     assert ds.dashsvd_get_trace(None, None, 0, None, None) == E
+    assert ds.dashsvd_csr_check(None, None, None) == E
+    assert ds.dashsvd_eig_fp64(None, None, 4, 4, 3, None, None) == E
 
 
 def test_create_without_gpu_reports_cuda_error(ds):

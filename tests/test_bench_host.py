@@ -57,22 +57,30 @@ def test_clock_sampler_without_nvidia_smi(monkeypatch, tmp_path):
 
 
 def _record(bwd_s=0.0029, var=7):
+    per_run = {"gaussian": 0.0004, "spmm_fwd": 6 * 0.0013, "spmm_bwd": 6 * bwd_s, "gram": 0.0025, "eig": 0.01,
+               "project": 0.003, "host_gap": 0.0003}
+    groups = {"gaussian": 1, "spmm_fwd": 6, "spmm_bwd": 6, "gram": 7, "eig": 7, "project": 7, "host_gap": 6}
     return {"kernels_s": {"spmm_fwd": 0.0013, "spmm_bwd": bwd_s, "gram": 0.00035, "project": 0.00038, "eig": 0.003},
-            "kernel_s_per_run": {"spmm_fwd": 0.0078, "spmm_bwd": 6 * bwd_s, "gram": 0.0025, "project": 0.003,
-                                 "eig": 0.02},
+            "kernel_s_per_run": per_run, "kernel_launch_groups_per_run": groups,
+            "profiled_run": {"variants": [5, var], "passes": 5},
             "bytes": {"spmm_fwd": 1.332e9, "spmm_bwd": 1.932e9}, "spmm": {"variants": [5, var]},
             "form": "precision"}
 
 
 def test_roofline_of_the_dominant_spmm():
+    """The dominant step is A^T Y - alpha Q (6 launch groups: 5 passes and the
+    prologue's A^T Omega, which reads no Q): achieved = the compulsory bytes of
+    those launches over their in-loop device time."""
     A = types.SimpleNamespace(m=1_000_000, n=1_000_000, nnz=15_000_000)
     pk = {"hbm_gbs": 6790.0, "source": "measured", "sm_max_mhz": 2070.0}
     r = bench._roofline(_record(), A, 150, pk)
     assert r["kernel"] == "spmm_bwd" and r["bound"] == "hbm" and r["unit"] == "GB/s"
-    assert abs(r["achieved"] - 1.932e9 / 0.0029 / 1e9) < 1e-9
+    total = 6 * 1.932e9 - 4 * 1_000_000 * 150
+    assert abs(r["achieved"] - total / (6 * 0.0029) / 1e9) < 1e-9
     assert abs(r["frac"] - r["achieved"] / 6790.0) < 1e-12
     assert abs(r["frac_of_nominal"] - r["achieved"] / 7900.0) < 1e-12
     assert abs(r["gathered_gbs"] - 15e6 * 150 * 4 / 0.0029 / 1e9) < 1e-9
+    assert abs(r["achieved_isolated"] - 1.932e9 / 0.0029 / 1e9) < 1e-9
     if r["traffic"] is not None:  # the committed summary matches the current SpMM sources
         assert abs(r["dram_gbs"] - r["traffic"] / 0.0029 / 1e9) < 1e-9
 
@@ -89,9 +97,10 @@ def test_traffic_needs_the_same_sources(monkeypatch):
 
 def test_launch_count_matches_the_committed_launch_list():
     """One steady-state run of the chosen form on the 1M graph (5 passes, A Q
-    by variant 5 and A^T Y - alpha Q by variant 7, setup kept) launched 160 of
-    the library's kernels in the committed ncu launch list."""
-    assert bench._launches_per_run("precision_learned", 5, 5, 7, setup_reused=True) == 160
-    assert bench._launches_per_run("precision_learned", 5, 5, 7, setup_reused=False) == 167
+    by variant 5 and A^T Y - alpha Q by variant 7, setup kept): the committed
+    ncu launch list counts 202 of the library's kernels (7 eigensolves, each
+    with three FP64 refinement steps of 6 launches)."""
+    assert bench._launches_per_run("precision_learned", 5, 5, 7, setup_reused=True) == 202
+    assert bench._launches_per_run("precision_learned", 5, 5, 7, setup_reused=False) == 209
     # the fused pass product replaces the two products (2 + 2 launches) by 2
-    assert bench._launches_per_run("precision", 5, 5, 7, fused=True) == 160 - 5 * 2
+    assert bench._launches_per_run("precision", 5, 5, 7, fused=True) == 202 - 5 * 2

@@ -113,7 +113,7 @@ def _spmm_check(A, X, Y, l):
 
 
 @pytest.mark.parametrize("name", list(MATRICES))
-@pytest.mark.parametrize("l", [1, 7, 30, 150, 160, 220])
+@pytest.mark.parametrize("l", [1, 7, 30, 150, 160, 220, 256])
 @pytest.mark.parametrize("variant", range(10))
 def test_spmm_matches_fp64(ds, h, name, l, variant):
     A = MATRICES[name]()

@@ -200,13 +200,15 @@ def test_learned_stop_gate(ds):
     expect = next(j for j, r in enumerate(ratios, start=1) if j >= 2 and r <= 3 * tol)
     _, _, _, i1, _ = _run(ds, A, k, s, 12, tol, weights=_const_net(40.0, 40.0))
     assert i1.passes == expect
-    assert i1.status == ds.DASHSVD_OK
+    # the surrogate test passed by itself at that pass (OK), or only the network stopped it
+    assert i1.status == (ds.DASHSVD_OK if ratios[expect - 1] <= tol else ds.DASHSVD_LEARNED_STOP)
 
 
 def test_trained_network_gain(ds):
     """What the committed network gains over the plain rule on held-out
     matrices of the training family (seeds the training script never saw):
-    fewer passes on average, and no run over the tolerance where the plain
+    at least 0.2 fewer passes on average (a network that never stops early
+    gains nothing and fails), and no run over the tolerance where the plain
     rule's run meets it."""
     from paper_2404_09276_gb300 import learn
 
@@ -216,4 +218,4 @@ def test_trained_network_gain(ds):
     s = learn.summarize(rows)
     print("learned-form gain on 12 held-out matrices:", s)
     assert s["failures"] == 0, s["fail_seeds"]
-    assert s["learned_passes"] <= s["plain_passes"]
+    assert s["learned_passes"] <= s["plain_passes"] - 0.2, s

@@ -353,7 +353,13 @@ def test_full_size_social_graph(ds, social_1m, form):
             h.load_mlp(w)
         U, S, V, info = h.run(Ad, k, s, prm["p_max"], prm["tol"])
         met = h.metrics(Ad, U, S, V, sigma[: k + 1], spec_iters=0)
-    assert info.status == ds.DASHSVD_OK and 2 <= info.passes <= prm["p_max"]
+    # the learned form may stop before the surrogate test passes (its status then
+    # says so, and the surrogate ratio is within 3 tol); the plain rule may not
+    if learned and info.status == ds.DASHSVD_LEARNED_STOP:
+        assert prm["tol"] < info.pve_ratio <= 3 * prm["tol"]
+    else:
+        assert info.status == ds.DASHSVD_OK and info.pve_ratio <= prm["tol"]
+    assert 2 <= info.passes <= prm["p_max"]
     # true per-vector error within the tolerance (Sec. 4), singular values close
     # and never above the true ones (Prop. 2) beyond rounding: FP32 in the plain
     # form; in the precision form the BF16x3 Gram's error of about 2^-16 sigma_1^2
