@@ -19,8 +19,9 @@ variance  Spread of the error metrics over repeated runs with different Omega
           recipe at 100k x 100k).
 
 The metrics (Sec. 4) are computed on the host from the returned U, S, V and
-exact singular values (LAPACK on the dense matrices; for the graph, a long
-FP64-accumulated run of the library itself with a wide sketch):
+exact singular values (LAPACK on the dense matrices; for the sparse
+stand-ins, the FP64 oracle's values stored under tests/golden by
+tests/golden/make_reference_sigma.py):
   eps_PVE   = max_i |sigma_i^2 - ||A^T u_i||^2| / sigma_{k+1}^2
   eps_sigma = max_i |sigma_i - s_i| / sigma_i
   eps_res   = max_i ||A^T u_i - s_i v_i|| / sigma_i
@@ -82,12 +83,24 @@ def fig1(ds, seeds, ps, k=100, s=50):
     return out
 
 
+GOLDEN_SIGMA = {(2, 1.0): "social_graph_1m", (2, 0.1): "social_graph_100k", (3, 1.0): "term_document_500k",
+                (5, 1.0): "recommender_2m"}
+
+
+def _golden_sigma(cfg, scale=1.0):
+    """The stored FP64 oracle values (tests/golden/make_reference_sigma.py) of a
+    workload, or None."""
+    name = GOLDEN_SIGMA.get((cfg, scale))
+    p = os.path.join(ROOT, "tests", "golden", f"{name}_sigma.txt") if name else ""
+    return np.loadtxt(p, comments="#") if name and os.path.exists(p) else None
+
+
 def _reference_sigma(ds, Ad, cfg, k):
-    """sigma_1..sigma_{k+1}: the stored FP64 values for the 1M social graph,
+    """sigma_1..sigma_{k+1}: the stored FP64 oracle values of the workload,
     else a long run of the library with a wide sketch."""
-    p = os.path.join(ROOT, "tests", "golden", "social_graph_1m_sigma.txt")
-    if cfg == 2 and os.path.exists(p):
-        return np.loadtxt(p, comments="#"), "FP64 oracle, stored"
+    sig = _golden_sigma(cfg)
+    if sig is not None and sig.size > k:
+        return sig, "FP64 oracle, stored"
     with ds.Handle() as h:
         kk = k + 1
         s = min(100, 256 - kk)
@@ -135,15 +148,17 @@ def variance(ds, runs, ps, k=100, s=50):
     A, _ = datagen.make_config(2, scale=0.1)
     As = A.to_scipy()
     Ad = ds.CsrDevice.from_host(A)
-    with ds.Handle() as h:  # reference sigma: wide sketch, many passes
-        _, S, _, _ = h.run(Ad, k + 1, 100, 40, 0.0)
-        sigma = S.cpu().numpy().astype(np.float64)
+    sigma = _golden_sigma(2, 0.1)  # the FP64 oracle's values (tests/golden)
+    if sigma is None:
+        raise SystemExit("missing tests/golden/social_graph_100k_sigma.txt: "
+                         "python -m tests.golden.make_reference_sigma social_graph_100k")
     res = {}
     for p in ps:
         m = np.array([_metrics(As, *_run(ds, Ad, k, s, p, 1, 0x5EED + r), sigma, k) for r in range(runs)])
         res[p] = {name: {"mean": float(m[:, i].mean()), "std_over_mean": float(m[:, i].std() / m[:, i].mean())}
                   for i, name in enumerate(("eps_pve", "eps_sigma", "eps_res"))}
-    return {"matrix": f"social-graph recipe {A.m} x {A.n}, nnz {A.nnz}", "runs": runs, "k": k, "by_p": res}
+    return {"matrix": f"social-graph recipe {A.m} x {A.n}, nnz {A.nnz}", "runs": runs, "k": k,
+            "sigma_ref": "FP64 oracle (tests/golden/social_graph_100k_sigma.txt)", "by_p": res}
 
 
 def main(argv=None):

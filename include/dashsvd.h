@@ -96,7 +96,12 @@ typedef struct {
                               per team in flight (6-9: FP32 operands only, so not with
                               gather_bf16); 10 = the fused pass product of
                               dashsvd_spmm_fused for the power-iteration passes (the
-                              prologue and final products use variant 1) */
+                              prologue and final products use variant 1); v + 16 for
+                              v in 1, 3, 5, 6, 7 = variant v with L2 eviction-priority
+                              hints (the rows a product gathers most are kept in L2 with
+                              evict_last; the CSR, the -alpha Q operand and the outputs
+                              the next product does not gather stream with evict_first;
+                              see k_hot.cu); other v + 16 run without hints */
   int32_t record_trace;    /* 1: keep the per-pass Shat / shift history (get_trace) */
   int32_t shift;           /* 1: dynamic shifts (dashSVD, Alg. 5 step 6); 0: alpha = 0 (the
                               basic randomized SVD, Alg. 1 form); 2: the shift of the first
@@ -198,6 +203,17 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
 #define DASHSVD_CSR_BAD_COL 8u
 int dashsvd_csr_check(dashsvd_handle h, const dashsvd_csr* A, uint32_t* flags);
 
+/* dashsvd_run with A and the outputs in HOST memory: A's three arrays are
+ * copied into device buffers the handle owns, the run follows, and U (m x k),
+ * S (k) and V (n x k), row-major, are copied back before the call returns.
+ * Pinned host memory (cudaHostAlloc / cudaHostRegister) lets the copies run as
+ * DMA on the handle's stream; pageable memory works too, through the driver's
+ * staging. A matrix passed again with the same contents keeps its setup (the
+ * handle's device copy of A stays at the same address). Same arguments, status
+ * and *info as dashsvd_run otherwise. */
+int dashsvd_run_host(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_passes, double pve_tol, float* U,
+                     float* S, float* V, dashsvd_info* info);
+
 /* Copy the per-pass history of the last run (record_trace = 1) to HOST memory.
  * Record j (0-based) holds 5 + l doubles: pass index, shift used in the pass,
  * surrogate PVE ratio, shift after the update, Jacobi sweeps of the pass's
@@ -206,11 +222,13 @@ int dashsvd_csr_check(dashsvd_handle h, const dashsvd_csr* A, uint32_t* flags);
 int dashsvd_get_trace(dashsvd_handle h, double* out, int64_t cap, int64_t* count, int* l);
 
 /* The SpMM autotuner's measurements from the last run that tuned (HOST
- * buffer of at least 50 floats): ms[10 * product + variant] = best time of that
- * variant in ms (0 = not timed), products 0: A Q, 1: A^T Y - alpha Q (FP32),
- * 2, 3: the same with BF16 gathers, 4 (variant slot 0): the fused pass product
- * of dashsvd_spmm_fused. The run uses the fused product when it beats the best
- * A Q plus the best A^T Y - alpha Q (dashsvd_info.spmm_variant bit 16). */
+ * buffer of at least 100 floats): ms[20 * product + slot] = best time in ms
+ * (0 = not timed), products 0: A Q, 1: A^T Y - alpha Q (FP32), 2, 3: the same
+ * with BF16 gathers, 4 (slot 0): the fused pass product of dashsvd_spmm_fused;
+ * slot v < 10 is variant v, slot 10 + v is variant v with L2 hints (variant
+ * code v + 16, see options.spmm_variant). The run uses the fused product when it
+ * beats the best A Q plus the best A^T Y - alpha Q (dashsvd_info.spmm_variant
+ * bit 16). */
 int dashsvd_get_tuning(dashsvd_handle h, float* ms, int64_t cap);
 
 /* Device time per step of the last run made with options.profile = 1 (HOST

@@ -29,7 +29,9 @@ def main(argv=None):
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--product", default="bwd",
                     choices=["fwd", "bwd", "fused", "gram", "gram_bf16x3", "project", "project_bf16x3", "eigsvd"])
-    ap.add_argument("--variant", type=int, default=-1, help="SpMM variant (fwd / bwd)")
+    ap.add_argument("--variant", type=int, default=-1, help="SpMM variant (fwd / bwd); + 16: with L2 hints")
+    ap.add_argument("--variants", type=str, default="",
+                    help="comma-separated SpMM variants to time one after the other (overrides --variant)")
     ap.add_argument("--l", type=int, default=0, help="block width (default: the workload's k + s)")
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--reps", type=int, default=5)
@@ -45,8 +47,10 @@ def main(argv=None):
     A, prm = datagen.make_config(a.config, a.scale)
     l = a.l or prm["k"] + prm["s"]
     ld = ds.ld_for(l)
-    h = ds.Handle()
+    h = ds.Handle(trust_csr=1)  # the structure is checked once below, not on every timed call
     Ad = ds.CsrDevice.from_host(A)
+    st_chk, flags = h.csr_check(Ad)
+    assert st_chk == ds.DASHSVD_OK, flags
     At = h.csr_transpose(Ad) if a.product == "bwd" else None
     g = torch.Generator(device="cuda").manual_seed(0)
     rows = A.m if a.product in ("gram", "gram_bf16x3", "project", "project_bf16x3", "eigsvd") else A.n
@@ -61,10 +65,17 @@ def main(argv=None):
     Out = torch.empty((rows, ld), device="cuda")
     alpha = torch.tensor([0.5], dtype=torch.float64, device="cuda")
     csr_bytes = 4 * (A.m + 1) + 8 * A.nnz
+    variants = [int(v) for v in a.variants.split(",")] if a.variants else [a.variant]
+    for var in variants:
+        _time_one(a, h, ds, torch, A, Ad, At, l, ld, Q, Y, Z, C, W, Out, alpha, rows, csr_bytes, var)
+    h.close()
+
+
+def _time_one(a, h, ds, torch, A, Ad, At, l, ld, Q, Y, Z, C, W, Out, alpha, rows, csr_bytes, variant):
     if a.product == "fwd":
-        fn, nbytes = (lambda: h.spmm(Ad, Q, l, out=Y, variant=a.variant)), csr_bytes + 4 * A.n * l + 4 * A.m * ld
+        fn, nbytes = (lambda: h.spmm(Ad, Q, l, out=Y, variant=variant)), csr_bytes + 4 * A.n * l + 4 * A.m * ld
     elif a.product == "bwd":
-        fn = lambda: h.spmm_shift(At, Y, l, alpha, Q, out=Z, variant=a.variant)  # noqa: E731
+        fn = lambda: h.spmm_shift(At, Y, l, alpha, Q, out=Z, variant=variant)  # noqa: E731
         nbytes = csr_bytes + 4 * A.m * l + 4 * A.n * l + 4 * A.n * ld
     elif a.product == "fused":
         fn, nbytes = (lambda: h.spmm_fused(Ad, Q, l, alpha, out=Z)), csr_bytes + 8 * A.n * l + 4 * A.n * ld
@@ -92,9 +103,9 @@ def main(argv=None):
         e1.synchronize()
         ts.append(e0.elapsed_time(e1))
     ms = float(np.median(ts))
-    print(json.dumps({"config": a.config, "scale": a.scale, "product": a.product, "variant": a.variant, "l": l,
-                      "m": A.m, "n": A.n, "nnz": A.nnz, "ms": ms, "bytes": nbytes, "gbs": nbytes / ms / 1e6}))
-    h.close()
+    print(json.dumps({"config": a.config, "scale": a.scale, "product": a.product, "variant": variant, "l": l,
+                      "m": A.m, "n": A.n, "nnz": A.nnz, "ms": ms, "bytes": nbytes, "gbs": nbytes / ms / 1e6}),
+          flush=True)
 
 
 if __name__ == "__main__":

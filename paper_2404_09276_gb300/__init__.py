@@ -43,6 +43,7 @@ EXPORTS = (
     "dashsvd_mlp_features", "dashsvd_mlp_forward", "dashsvd_mlp_loss_grad", "dashsvd_mlp_adam",
     "dashsvd_get_tuning", "dashsvd_spmm_fused", "dashsvd_metrics", "dashsvd_selftest_bounded_wait",
     "dashsvd_selftest_fail_alloc", "dashsvd_csr_check", "dashsvd_eig_fp64", "dashsvd_get_profile",
+    "dashsvd_run_host",
 )
 MLP_PARAMS = 1218
 MLP_IN = 16
@@ -110,6 +111,7 @@ def _load():
         "dashsvd_csr_check": (I, [P, P, P]),
         "dashsvd_eig_fp64": (I, [P, P, I64, I, I, P, P]),
         "dashsvd_get_profile": (I, [P, P, I64]),
+        "dashsvd_run_host": (I, [P, P, I, I, I, D, P, P, P, P]),
         "dashsvd_mlp_forward": (I, [P, P, P, I64, P]),
         "dashsvd_mlp_loss_grad": (I, [P, P, P, P, P, I64, P, P]),
         "dashsvd_mlp_adam": (I, [P, P, P, P, P, I, C.c_float, C.c_float, C.c_float, C.c_float]),
@@ -158,6 +160,7 @@ dashsvd_selftest_fail_alloc = _export("dashsvd_selftest_fail_alloc")
 dashsvd_csr_check = _export("dashsvd_csr_check")
 dashsvd_eig_fp64 = _export("dashsvd_eig_fp64")
 dashsvd_get_profile = _export("dashsvd_get_profile")
+dashsvd_run_host = _export("dashsvd_run_host")
 PROFILE_CATEGORIES = ("gaussian", "spmm_fwd", "spmm_bwd", "gram", "eig", "project", "host_gap")
 DASHSVD_CSR_BAD_FIRST, DASHSVD_CSR_BAD_ORDER, DASHSVD_CSR_BAD_LAST, DASHSVD_CSR_BAD_COL = 1, 2, 4, 8
 dashsvd_mlp_forward = _export("dashsvd_mlp_forward")
@@ -287,6 +290,23 @@ class Handle:
               "dashsvd_eig_fp64")
         return D, V
 
+    def run_host(self, A, k: int, s: int, max_passes: int, pve_tol: float, U, S, V):
+        """dashSVD of a HOST CSR (object with m, n and numpy rowptr / colidx / val,
+        or torch CPU tensors) into HOST outputs U (m x k), S (k), V (n x k) (torch
+        CPU float32 tensors, pinned for DMA copies); returns info."""
+        import torch
+
+        def ptr(x):
+            return x.data_ptr() if isinstance(x, torch.Tensor) else x.ctypes.data
+
+        nnz = int(A.colidx.shape[0])
+        csr = dashsvd_csr(int(A.m), int(A.n), nnz, ptr(A.rowptr), ptr(A.colidx), ptr(A.val))
+        info = dashsvd_info()
+        st = dashsvd_run_host(self.h, C.byref(csr), k, s, max_passes, float(pve_tol), U.data_ptr(), S.data_ptr(),
+                              V.data_ptr(), C.byref(info))
+        check(st, "dashsvd_run_host", ok=(DASHSVD_OK, DASHSVD_MAX_PASSES, DASHSVD_LEARNED_STOP))
+        return info
+
     def trace(self):
         """Per-pass records of the last run: list of (j, alpha_used, ratio, alpha_next, sweeps, Shat[l])."""
         import numpy as np
@@ -392,12 +412,13 @@ class Handle:
         return {c: (float(buf[i]), int(buf[7 + i])) for i, c in enumerate(PROFILE_CATEGORIES)}
 
     def tuning(self):
-        """The autotuner's last measurements: (5 products x 10 variants) ms, 0 = not timed."""
+        """The autotuner's last measurements: (5 products x 20 variants) ms, 0 = not
+        timed; variants 10..19 are 0..9 with L2 hints."""
         import numpy as np
 
-        buf = np.zeros(50, dtype=np.float32)
+        buf = np.zeros(100, dtype=np.float32)
         check(dashsvd_get_tuning(self.h, buf.ctypes.data, buf.size), "dashsvd_get_tuning")
-        return buf.reshape(5, 10)
+        return buf.reshape(5, 20)
 
     def spmm_fused(self, A: CsrDevice, Q, l: int, alpha_dev=None, out=None):
         """Z = A^T (A Q) - alpha Q in one read of A (atomic scatter)."""

@@ -13,6 +13,7 @@
 // on any pass. The graph is cached per handle and rebuilt when an argument
 // that is baked into it changes.
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -101,6 +102,7 @@ struct dashsvd_handle_s {
   DevBuf mlpw, mlp_part;    // learned form: network parameters, gradient partials
   DevBuf fpw;               // fingerprint of the last run's matrix
   DevBuf det_work;          // stable transposition (options.deterministic): radix-sort buffers
+  DevBuf h_rowptr, h_col, h_val, h_U, h_S, h_V;  // dashsvd_run_host: device copies of A and the outputs
   // accuracy metrics (dashsvd_metrics): CSR of A^T, partitions, blocks, sums
   DevBuf mt_rowptr, mt_col, mt_val, mt_cursor, mt_scan, mt_seg_a, mt_seg_t, mt_T, mt_X, mt_Y, mt_Z, mt_C, mt_part,
       mt_sig, mt_out, mt_S, mt_V;
@@ -130,8 +132,22 @@ struct dashsvd_handle_s {
     bool fused;
   };
   std::vector<Tune> tuned;
-  float tune_ms[5][10] = {};  // last autotuning: best time per (product, variant), ms; 0 = not timed
-                             // (product 4, variant 0: the fused pass product)
+  float tune_ms[5][20] = {};  // last autotuning: best time per (product, variant), ms; 0 = not timed
+                             // (variants 10..19: 0..9 with L2 hints; product 4, variant 0: the fused
+                             // pass product)
+  // L2 hints (k_hot.cu): hot-row bitmaps of the run's products, from gather-count
+  // histograms taken with the setup (kept on the host), per gathered row size
+  DevBuf hot_fwd, hot_bwd, hot_hist, tag_fwd, tag_bwd;
+  std::vector<int32_t> hist_fwd, hist_bwd;
+  int64_t hot_rowbytes = 0;
+  bool hot_valid = false;
+  int64_t l2_bytes = 0;
+  // step-level hinted products: the bitmap of the last CSR's column-id counts
+  DevBuf st_counts, st_hot, st_tag;
+  struct StepHotKey {
+    const void* colidx;
+    int64_t nnz, n, rowbytes;
+  } st_key{};
   // per-step device times of a host-driven run (options.profile): an event
   // after each group of launches, tagged with the group's category
   bool prof_on = false;
@@ -195,6 +211,9 @@ struct RunPlan {
   bool fused = false;        // pass product as one fused A^T (A Q) - alpha Q (FP32 gathers only)
   SpmmPart part_fwd, part_bwd;
   SpmmScratch scr;
+  // L2 hints per product: A Q of a pass (gathers Q, stores Y that A^T Y gathers next),
+  // A^T Y (and A^T Omega), and the final B = A Q (stored for the Gram and projection)
+  SpmmHints hf, hb, hf_final;
 };
 
 EigArgs eig_args(dashsvd_handle h, const RunPlan& p, int mode, unsigned long long cond) {
@@ -285,7 +304,7 @@ cudaError_t launch_prologue(dashsvd_handle h, const RunPlan& p, unsigned long lo
     return e;
   // step 2: Z = A^T Omega, Q = eigSVD(Z)
   if ((e = launch_spmm(p.AwT, p.part_bwd, as<float>(h->Y), p.ld, p.l, as<float>(h->Z), p.ld, nullptr, nullptr, 0,
-                       p.var_bwd32, p.scr, h->num_sms, st, as<int>(h->errw))) != cudaSuccess ||
+                       p.var_bwd32, p.scr, h->num_sms, st, as<int>(h->errw), p.hb)) != cudaSuccess ||
       (e = tmark(h, kPfBwd, st)) != cudaSuccess)
     return e;
   if ((e = eigsvd_step(h, p, as<float>(h->Z), p.nw, kModeInit, cond, st)) != cudaSuccess) return e;
@@ -294,7 +313,7 @@ cudaError_t launch_prologue(dashsvd_handle h, const RunPlan& p, unsigned long lo
   // PVE control without the surrogate: B = A Q_0 (kept in Y for the first
   // pass) and its singular values, the p = 0 values of the criterion
   if ((e = launch_spmm(p.Aw, p.part_fwd, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld, nullptr, nullptr, 0,
-                       p.var_fwd, p.scr, h->num_sms, st, as<int>(h->errw))) != cudaSuccess ||
+                       p.var_fwd, p.scr, h->num_sms, st, as<int>(h->errw), p.hf)) != cudaSuccess ||
       (e = tmark(h, kPfFwd, st)) != cudaSuccess)
     return e;
   return eigsvd_step(h, p, as<float>(h->Y), p.mw, kModeDirect, cond, st);
@@ -307,25 +326,25 @@ cudaError_t launch_pass(dashsvd_handle h, const RunPlan& p, unsigned long long c
   if (direct_pve(h)) {
     // Y = A Q is already there (the end of the previous pass or the prologue)
     if ((e = launch_spmm(p.AwT, p.part_bwd, as<float>(h->Y), p.ld, p.l, as<float>(h->Z), p.ld, &ctl->alpha,
-                         as<float>(h->Q), p.ld, p.var_bwd, p.scr, h->num_sms, st, as<int>(h->errw))) != cudaSuccess ||
+                         as<float>(h->Q), p.ld, p.var_bwd, p.scr, h->num_sms, st, as<int>(h->errw), p.hb)) != cudaSuccess ||
         (e = tmark(h, kPfBwd, st)) != cudaSuccess)
       return e;
     if ((e = eigsvd_step(h, p, as<float>(h->Z), p.nw, kModePass, cond, st)) != cudaSuccess) return e;
     if ((e = project_basis(h, p, st)) != cudaSuccess) return e;
     // B = A Q of the new basis, its singular values and the stop test
     if ((e = launch_spmm(p.Aw, p.part_fwd, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld, nullptr, nullptr, 0,
-                         p.var_fwd, p.scr, h->num_sms, st, as<int>(h->errw))) != cudaSuccess ||
+                         p.var_fwd, p.scr, h->num_sms, st, as<int>(h->errw), p.hf)) != cudaSuccess ||
         (e = tmark(h, kPfFwd, st)) != cudaSuccess)
       return e;
     return eigsvd_step(h, p, as<float>(h->Y), p.mw, kModeDirect, cond, st);
   }
   if (bf16_gathers(h)) {
     if ((e = launch_spmm_bf16(p.Aw, p.part_fwd, h->Qb.p, p.ld, p.l, h->Y.p, true, p.ld, nullptr, nullptr, 0,
-                              p.var_fwd, p.scr, h->num_sms, st)) != cudaSuccess ||
+                              p.var_fwd, p.scr, h->num_sms, st, p.hf)) != cudaSuccess ||
         (e = tmark(h, kPfFwd, st)) != cudaSuccess)
       return e;
     if ((e = launch_spmm_bf16(p.AwT, p.part_bwd, h->Y.p, p.ld, p.l, h->Z.p, false, p.ld, &ctl->alpha, h->Qb.p, p.ld,
-                              p.var_bwd, p.scr, h->num_sms, st)) != cudaSuccess ||
+                              p.var_bwd, p.scr, h->num_sms, st, p.hb)) != cudaSuccess ||
         (e = tmark(h, kPfBwd, st)) != cudaSuccess)
       return e;
   } else if (p.fused) {  // one read of A: Z = A^T (A Q) - alpha Q, Y never stored
@@ -335,11 +354,11 @@ cudaError_t launch_pass(dashsvd_handle h, const RunPlan& p, unsigned long long c
       return e;
   } else {
     if ((e = launch_spmm(p.Aw, p.part_fwd, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld, nullptr, nullptr, 0,
-                         p.var_fwd, p.scr, h->num_sms, st, as<int>(h->errw))) != cudaSuccess ||
+                         p.var_fwd, p.scr, h->num_sms, st, as<int>(h->errw), p.hf)) != cudaSuccess ||
         (e = tmark(h, kPfFwd, st)) != cudaSuccess)
       return e;
     if ((e = launch_spmm(p.AwT, p.part_bwd, as<float>(h->Y), p.ld, p.l, as<float>(h->Z), p.ld, &ctl->alpha,
-                         as<float>(h->Q), p.ld, p.var_bwd, p.scr, h->num_sms, st, as<int>(h->errw))) != cudaSuccess ||
+                         as<float>(h->Q), p.ld, p.var_bwd, p.scr, h->num_sms, st, as<int>(h->errw), p.hb)) != cudaSuccess ||
         (e = tmark(h, kPfBwd, st)) != cudaSuccess)
       return e;
   }
@@ -354,7 +373,7 @@ cudaError_t launch_final(dashsvd_handle h, const RunPlan& p, cudaStream_t st) {
   // there when the PVE control works on B directly)
   if (!direct_pve(h) && ((e = launch_spmm(p.Aw, p.part_fwd, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld,
                                           nullptr, nullptr, 0, p.var_fwd32, p.scr, h->num_sms, st,
-                                          as<int>(h->errw))) != cudaSuccess ||
+                                          as<int>(h->errw), p.hf_final)) != cudaSuccess ||
                          (e = tmark(h, kPfFwd, st)) != cudaSuccess))
     return e;
   // steps 10-11: eigSVD(B); U = B V_k S_k^-1; V = Q V_k
@@ -466,16 +485,16 @@ int autotune_spmm(dashsvd_handle h, RunPlan& p, const dashsvd_csr& A) {
     switch (prod) {
       case 0:  // FP32 A Q
         return launch_spmm(p.Aw, p.part_fwd, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld, nullptr, nullptr, 0,
-                           v, p.scr, h->num_sms, st, as<int>(h->errw));
+                           v, p.scr, h->num_sms, st, as<int>(h->errw), p.hf);
       case 1:  // FP32 A^T Y - alpha Q
         return launch_spmm(p.AwT, p.part_bwd, as<float>(h->Y), p.ld, p.l, as<float>(h->Z), p.ld, &ctl->alpha,
-                           as<float>(h->Q), p.ld, v, p.scr, h->num_sms, st, as<int>(h->errw));
+                           as<float>(h->Q), p.ld, v, p.scr, h->num_sms, st, as<int>(h->errw), p.hb);
       case 2:  // BF16 A Q -> BF16
         return launch_spmm_bf16(p.Aw, p.part_fwd, h->Qb.p, p.ld, p.l, h->Y.p, true, p.ld, nullptr, nullptr, 0, v,
-                                p.scr, h->num_sms, st);
+                                p.scr, h->num_sms, st, p.hf);
       default:  // BF16 A^T Y - alpha Q -> FP32
         return launch_spmm_bf16(p.AwT, p.part_bwd, h->Y.p, p.ld, p.l, h->Z.p, false, p.ld, &ctl->alpha, h->Qb.p, p.ld,
-                                v, p.scr, h->num_sms, st);
+                                v, p.scr, h->num_sms, st, p.hb);
     }
   };
   // one timed launch of the variant, after a warm-up launch; A^T Y is preceded by
@@ -490,27 +509,38 @@ int autotune_spmm(dashsvd_handle h, RunPlan& p, const dashsvd_csr& A) {
     return e;
   };
   for (int prod = 0; prod < nprod && err == cudaSuccess; ++prod) {
+    // candidates: every variant, plus the merge-path ones again with L2 hints
+    // when this run has hot-row bitmaps
+    std::vector<int> cand;
     const int nv = prod < 2 ? kSpmmVariants : kSpmmVariantsBf16;
-    float t[kSpmmVariants];
-    for (int v = 0; v < nv && err == cudaSuccess; ++v) err = time1(prod, v, &t[v]);
+    for (int v = 0; v < nv; ++v) cand.push_back(v);
+    if (p.hf.gather_hot && p.hb.gather_hot) {
+      const int hv[] = {1, 3, 5, 6, 7};
+      for (int v : hv)
+        if (v < nv) cand.push_back(v | kSpmmHintFlag);
+    }
+    const int nc = (int)cand.size();
+    std::vector<float> t(nc);
+    for (int c = 0; c < nc && err == cudaSuccess; ++c) err = time1(prod, cand[c], &t[c]);
     if (err != cudaSuccess) break;
     // the close contenders (within 30 % of the fastest) are timed four more
     // times, interleaved; each is then judged by its median of five
-    const float lead = *std::min_element(t, t + nv);
-    float reps[kSpmmVariants][5];
-    for (int v = 0; v < nv; ++v) reps[v][0] = t[v];
+    const float lead = *std::min_element(t.begin(), t.end());
+    std::vector<std::array<float, 5>> reps(nc);
+    for (int c = 0; c < nc; ++c) reps[c][0] = t[c];
     for (int rep = 1; rep < 5 && err == cudaSuccess; ++rep)
-      for (int v = 0; v < nv && err == cudaSuccess; ++v)
-        if (t[v] <= 1.3f * lead) err = time1(prod, v, &reps[v][rep]);
-    for (int v = 0; v < nv && err == cudaSuccess; ++v)
-      if (t[v] <= 1.3f * lead) {
-        std::sort(reps[v], reps[v] + 5);
-        t[v] = reps[v][2];
+      for (int c = 0; c < nc && err == cudaSuccess; ++c)
+        if (t[c] <= 1.3f * lead) err = time1(prod, cand[c], &reps[c][rep]);
+    for (int c = 0; c < nc && err == cudaSuccess; ++c)
+      if (t[c] <= 1.3f * lead) {
+        std::sort(reps[c].begin(), reps[c].end());
+        t[c] = reps[c][2];
       }
-    for (int v = 0; v < nv; ++v) {
-      h->tune_ms[prod][v] = t[v];
-      if (t[v] < best[prod]) {
-        best[prod] = t[v];
+    for (int c = 0; c < nc; ++c) {
+      const int v = cand[c];
+      h->tune_ms[prod][(v & kSpmmHintFlag) ? 10 + (v & 15) : v] = t[c];
+      if (t[c] < best[prod]) {
+        best[prod] = t[c];
         arg[prod] = v;
       }
     }
@@ -639,13 +669,17 @@ int dashsvd_create(dashsvd_handle* out, const dashsvd_options* opt, void* cuda_s
     dashsvd_options_init(&h->opt);
   if ((h->opt.alpha_prev_mode != 0 && h->opt.alpha_prev_mode != 1) || h->opt.shift < 0 || h->opt.shift > 2 ||
       h->opt.spmm_variant < -1 ||
-      h->opt.spmm_variant > kSpmmFused) {
+      (h->opt.spmm_variant > kSpmmFused && !(h->opt.spmm_variant & kSpmmHintFlag)) ||
+      (h->opt.spmm_variant & kSpmmHintFlag && (h->opt.spmm_variant & ~kSpmmHintFlag) >= kSpmmVariants)) {
     delete h;
     return DASHSVD_EINVAL;
   }
   h->stream = (cudaStream_t)cuda_stream;
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+  int l2 = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, h->device);
+  h->l2_bytes = l2;
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = prepare_project();
@@ -671,7 +705,9 @@ int dashsvd_destroy(dashsvd_handle h) {
   DevBuf* bufs[] = {&h->rowptr_b, &h->col_b, &h->val_b, &h->cursor, &h->scan_tmp, &h->Y,       &h->Z,
                     &h->Q,        &h->G,     &h->W,     &h->W2,     &h->partial,  &h->carry, &h->carry_row,
                     &h->ctl,      &h->trace, &h->eigw,   &h->seg_fwd, &h->seg_bwd, &h->errw, &h->Qb, &h->G64,
-                    &h->mlpw, &h->mlp_part, &h->fpw, &h->det_work, &h->mt_rowptr, &h->mt_col, &h->mt_val, &h->mt_cursor,
+                    &h->mlpw, &h->mlp_part, &h->fpw, &h->det_work, &h->h_rowptr, &h->h_col, &h->h_val, &h->h_U,
+                    &h->h_S, &h->h_V, &h->hot_fwd, &h->hot_bwd, &h->hot_hist,
+                    &h->tag_fwd, &h->tag_bwd, &h->st_counts, &h->st_hot, &h->st_tag, &h->mt_rowptr, &h->mt_col, &h->mt_val, &h->mt_cursor,
                     &h->mt_scan, &h->mt_seg_a, &h->mt_seg_t, &h->mt_T, &h->mt_X, &h->mt_Y, &h->mt_Z, &h->mt_C,
                     &h->mt_part, &h->mt_sig, &h->mt_out, &h->mt_S, &h->mt_V};
   for (DevBuf* b : bufs)
@@ -731,9 +767,9 @@ int dashsvd_mlp_adam(dashsvd_handle h, float* W, const float* grad, float* m, fl
 }
 
 int dashsvd_get_tuning(dashsvd_handle h, float* ms, int64_t cap) {
-  if (!h || !ms || cap < 50) return DASHSVD_EINVAL;
+  if (!h || !ms || cap < 100) return DASHSVD_EINVAL;
   for (int p = 0; p < 5; ++p)
-    for (int v = 0; v < 10; ++v) ms[p * 10 + v] = h->tune_ms[p][v];
+    for (int v = 0; v < 20; ++v) ms[p * 20 + v] = h->tune_ms[p][v];
   return DASHSVD_OK;
 }
 
@@ -776,7 +812,9 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
   const int64_t mn = A->m < A->n ? A->m : A->n;
   if (l > mn || l > DASHSVD_MAX_L) return DASHSVD_EINVAL;
   if (h->opt.gather_bf16 && !precision(h)) return DASHSVD_EINVAL;
-  if (h->opt.gather_bf16 && h->opt.spmm_variant >= kSpmmVariantsBf16) return DASHSVD_EINVAL;
+  if (h->opt.gather_bf16 && h->opt.spmm_variant >= 0 &&
+      (h->opt.spmm_variant & ~kSpmmHintFlag) >= kSpmmVariantsBf16)
+    return DASHSVD_EINVAL;
   if (h->opt.learned && (!h->mlp_loaded || h->opt.shift != 1)) return DASHSVD_EINVAL;
   if (h->opt.pve_mode < 0 || h->opt.pve_mode > 1) return DASHSVD_EINVAL;
   if (h->opt.deterministic && h->opt.spmm_variant == kSpmmFused) return DASHSVD_EINVAL;
@@ -857,8 +895,9 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
   // variant 5 (the tuner's timing-dependent choice would change the
   // summation order from run to run)
   const int dflt = h->opt.deterministic ? 5 : 1;
-  p.var_fwd = p.var_fwd32 = forced >= 0 && forced < kSpmmVariants ? forced : dflt;
-  p.var_bwd = p.var_bwd32 = forced >= 0 && forced < kSpmmVariants ? forced : dflt;
+  const bool forced_var = forced >= 0 && forced != kSpmmFused;  // 0..9, or 16..25 (with L2 hints)
+  p.var_fwd = p.var_fwd32 = forced_var ? forced : dflt;
+  p.var_bwd = p.var_bwd32 = forced_var ? forced : dflt;
   p.fused = forced == kSpmmFused;
 
   cudaStream_t st = h->stream;
@@ -881,6 +920,54 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
     DS_CUDA(launch_spmm_partition(p.AwT, p.part_bwd, st));
     h->setup = skey;
     h->setup_valid = true;
+  }
+  // L2 hints: gather-count histograms with the setup (row lengths of A^T for the
+  // rows of Q that A Q gathers, of A for the rows of Y that A^T Y gathers), then
+  // the bitmaps for this gathered row size; each hot set may take 40 % of L2
+  if (!reuse || !h->hot_valid) {
+    h->hot_valid = false;
+    h->hist_fwd.assign(kHotBins, 0);
+    h->hist_bwd.assign(kHotBins, 0);
+    if ((rc = ensure(h->hot_hist, sizeof(int32_t) * 2 * kHotBins, &moved))) return rc;
+    int32_t* hh = as<int32_t>(h->hot_hist);
+    DS_CUDA(launch_hot_hist(p.AwT.rowptr, nullptr, p.nw, hh, st));
+    DS_CUDA(launch_hot_hist(p.Aw.rowptr, nullptr, p.mw, hh + kHotBins, st));
+    DS_CUDA(cudaMemcpyAsync(h->hist_fwd.data(), hh, sizeof(int32_t) * kHotBins, cudaMemcpyDeviceToHost, st));
+    DS_CUDA(cudaMemcpyAsync(h->hist_bwd.data(), hh + kHotBins, sizeof(int32_t) * kHotBins, cudaMemcpyDeviceToHost,
+                            st));
+    DS_CUDA(cudaStreamSynchronize(st));
+    h->hot_rowbytes = 0;
+    h->hot_valid = true;
+  }
+  {
+    const int64_t rowbytes = (int64_t)p.ld * (bf16_gathers(h) ? 2 : 4);
+    if ((rc = ensure(h->hot_fwd, sizeof(uint32_t) * (size_t)ds_ceil_div(p.nw, 32), &moved)) ||
+        (rc = ensure(h->hot_bwd, sizeof(uint32_t) * (size_t)ds_ceil_div(p.mw, 32), &moved)) ||
+        (rc = ensure(h->tag_fwd, sizeof(int32_t) * (size_t)A->nnz, &moved)) ||
+        (rc = ensure(h->tag_bwd, sizeof(int32_t) * (size_t)A->nnz, &moved)))
+      return rc;
+    if (rowbytes != h->hot_rowbytes || moved) {
+      const int64_t budget = (int64_t)(0.4 * (double)h->l2_bytes) / rowbytes;
+      DS_CUDA(launch_hot_bitmap(p.AwT.rowptr, nullptr, p.nw, hot_threshold(h->hist_fwd.data(), budget),
+                                as<uint32_t>(h->hot_fwd), st));
+      DS_CUDA(launch_hot_bitmap(p.Aw.rowptr, nullptr, p.mw, hot_threshold(h->hist_bwd.data(), budget),
+                                as<uint32_t>(h->hot_bwd), st));
+      // copies of the column ids with each gathered row's hot bit (bit 30)
+      if (p.nw < ((int64_t)1 << kHotColBit) && p.mw < ((int64_t)1 << kHotColBit)) {
+        DS_CUDA(launch_tag_cols(p.Aw.colidx, A->nnz, as<uint32_t>(h->hot_fwd), as<int32_t>(h->tag_fwd), st));
+        DS_CUDA(launch_tag_cols(p.AwT.colidx, A->nnz, as<uint32_t>(h->hot_bwd), as<int32_t>(h->tag_bwd), st));
+      }
+      h->hot_rowbytes = rowbytes;
+    }
+    if (p.nw < ((int64_t)1 << kHotColBit) && p.mw < ((int64_t)1 << kHotColBit)) {  // else no hints
+      p.hf.gather_hot = as<uint32_t>(h->hot_fwd);
+      p.hf.store_hot = as<uint32_t>(h->hot_bwd);
+      p.hf.tagged_col = as<int32_t>(h->tag_fwd);
+      p.hb.gather_hot = as<uint32_t>(h->hot_bwd);
+      p.hb.tagged_col = as<int32_t>(h->tag_bwd);
+      p.hf_final = p.hf;
+      p.hf_final.store_hot = nullptr;
+    }
   }
   if (forced < 0 && !h->opt.deterministic && (rc = autotune_spmm(h, p, *A)) != DASHSVD_OK) return rc;
   if (direct_pve(h)) p.fused = false;  // B = A Q is stored every pass
@@ -962,7 +1049,9 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
     DevBuf* bufs[] = {&h->rowptr_b, &h->col_b, &h->val_b, &h->cursor, &h->scan_tmp, &h->Y,       &h->Z,
                       &h->Q,        &h->G,     &h->W,     &h->W2,     &h->partial,  &h->carry, &h->carry_row,
                       &h->ctl,      &h->trace, &h->eigw,   &h->seg_fwd, &h->seg_bwd, &h->errw, &h->Qb, &h->G64,
-                    &h->mlpw, &h->mlp_part, &h->fpw, &h->det_work, &h->mt_rowptr, &h->mt_col, &h->mt_val, &h->mt_cursor,
+                    &h->mlpw, &h->mlp_part, &h->fpw, &h->det_work, &h->h_rowptr, &h->h_col, &h->h_val, &h->h_U,
+                    &h->h_S, &h->h_V, &h->hot_fwd, &h->hot_bwd, &h->hot_hist,
+                    &h->tag_fwd, &h->tag_bwd, &h->st_counts, &h->st_hot, &h->st_tag, &h->mt_rowptr, &h->mt_col, &h->mt_val, &h->mt_cursor,
                     &h->mt_scan, &h->mt_seg_a, &h->mt_seg_t, &h->mt_T, &h->mt_X, &h->mt_Y, &h->mt_Z, &h->mt_C,
                     &h->mt_part, &h->mt_sig, &h->mt_out, &h->mt_S, &h->mt_V};
     for (DevBuf* b : bufs) ws += (int64_t)b->bytes;
@@ -970,6 +1059,37 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
     info->eig_sweeps = hc.sweeps;
     info->setup_reused = reuse ? 1 : 0;
   }
+  return status;
+}
+
+int dashsvd_run_host(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_passes, double pve_tol, float* U,
+                     float* S, float* V, dashsvd_info* info) {
+  if (info) std::memset(info, 0, sizeof(*info));
+  if (!h || !csr_ok(A) || !U || !S || !V || k < 1) return DASHSVD_EINVAL;
+  int rc;
+  bool moved = false;
+  const size_t nnz = (size_t)A->nnz;
+  if ((rc = ensure(h->h_rowptr, sizeof(int32_t) * (size_t)(A->m + 1), &moved)) ||
+      (rc = ensure(h->h_col, sizeof(int32_t) * nnz, &moved)) || (rc = ensure(h->h_val, sizeof(float) * nnz, &moved)) ||
+      (rc = ensure(h->h_U, sizeof(float) * (size_t)(A->m * k), &moved)) ||
+      (rc = ensure(h->h_S, sizeof(float) * (size_t)k, &moved)) ||
+      (rc = ensure(h->h_V, sizeof(float) * (size_t)(A->n * k), &moved)))
+    return rc;
+  if (moved) h->have_graph = false;
+  cudaStream_t st = h->stream;
+  DS_CUDA(cudaMemcpyAsync(h->h_rowptr.p, A->rowptr, sizeof(int32_t) * (size_t)(A->m + 1), cudaMemcpyHostToDevice, st));
+  if (nnz > 0) {
+    DS_CUDA(cudaMemcpyAsync(h->h_col.p, A->colidx, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st));
+    DS_CUDA(cudaMemcpyAsync(h->h_val.p, A->val, sizeof(float) * nnz, cudaMemcpyHostToDevice, st));
+  }
+  const dashsvd_csr Ad{A->m, A->n, A->nnz, as<int32_t>(h->h_rowptr), as<int32_t>(h->h_col), as<float>(h->h_val)};
+  const int status = dashsvd_run(h, &Ad, k, s, max_passes, pve_tol, as<float>(h->h_U), as<float>(h->h_S),
+                                 as<float>(h->h_V), info);
+  if (status < 0) return status;
+  DS_CUDA(cudaMemcpyAsync(U, h->h_U.p, sizeof(float) * (size_t)(A->m * k), cudaMemcpyDeviceToHost, st));
+  DS_CUDA(cudaMemcpyAsync(S, h->h_S.p, sizeof(float) * (size_t)k, cudaMemcpyDeviceToHost, st));
+  DS_CUDA(cudaMemcpyAsync(V, h->h_V.p, sizeof(float) * (size_t)(A->n * k), cudaMemcpyDeviceToHost, st));
+  DS_CUDA(cudaStreamSynchronize(st));
   return status;
 }
 
@@ -995,13 +1115,51 @@ int dashsvd_csr_transpose(dashsvd_handle h, const dashsvd_csr* A, int32_t* rowpt
                         h->stream);
 }
 
+// The L2 hints of a step-level product: the bitmap of the rows of X that A's
+// column ids gather most (kept while the column array, sizes and row size stay).
+static int step_hints(dashsvd_handle h, const dashsvd_csr& A, int64_t rowbytes, SpmmHints* hs) {
+  const dashsvd_handle_s::StepHotKey key{A.colidx, A.nnz, A.n, rowbytes};
+  bool moved = false;
+  int rc;
+  if (A.n >= ((int64_t)1 << kHotColBit)) return DASHSVD_OK;  // column ids too large to carry the bit: no hints
+  if ((rc = ensure(h->st_counts, sizeof(int32_t) * (size_t)A.n, &moved)) ||
+      (rc = ensure(h->st_hot, sizeof(uint32_t) * (size_t)ds_ceil_div(A.n, 32), &moved)) ||
+      (rc = ensure(h->st_tag, sizeof(int32_t) * (size_t)A.nnz, &moved)) ||
+      (rc = ensure(h->hot_hist, sizeof(int32_t) * 2 * kHotBins, &moved)))
+    return rc;
+  if (moved) h->have_graph = false;
+  if (moved || std::memcmp(&key, &h->st_key, sizeof(key)) != 0) {
+    cudaStream_t st = h->stream;
+    std::vector<int32_t> hist(kHotBins);
+    DS_CUDA(launch_col_counts(A.colidx, A.nnz, A.n, as<int32_t>(h->st_counts), st));
+    DS_CUDA(launch_hot_hist(nullptr, as<int32_t>(h->st_counts), A.n, as<int32_t>(h->hot_hist), st));
+    DS_CUDA(cudaMemcpyAsync(hist.data(), h->hot_hist.p, sizeof(int32_t) * kHotBins, cudaMemcpyDeviceToHost, st));
+    DS_CUDA(cudaStreamSynchronize(st));
+    const int64_t budget = (int64_t)(0.4 * (double)h->l2_bytes) / rowbytes;
+    DS_CUDA(launch_hot_bitmap(nullptr, as<int32_t>(h->st_counts), A.n, hot_threshold(hist.data(), budget),
+                              as<uint32_t>(h->st_hot), st));
+    DS_CUDA(launch_tag_cols(A.colidx, A.nnz, as<uint32_t>(h->st_hot), as<int32_t>(h->st_tag), st));
+    h->st_key = key;
+  }
+  hs->gather_hot = as<uint32_t>(h->st_hot);
+  hs->tagged_col = as<int32_t>(h->st_tag);
+  return DASHSVD_OK;
+}
+
+static bool variant_ok(int v, int nv) {
+  return v == -1 || (v >= 0 && (v & ~kSpmmHintFlag) < nv && (v & ~kSpmmHintFlag) < 16);
+}
+
 static int spmm_common(dashsvd_handle h, const dashsvd_csr* A, const float* X, int64_t ldx, int l, float* Y,
                        int64_t ldy, const double* alpha, const float* Q, int64_t ldq, int variant) {
   if (!h || !csr_ok(A) || !X || !Y || l < 1 || l > DASHSVD_MAX_L) return DASHSVD_EINVAL;
   if (ldx < l || ldy < l || ldx % 4 || ldy % 4 || !aligned16(X) || !aligned16(Y)) return DASHSVD_EINVAL;
   if (alpha && (!Q || ldq < l || ldq % 4 || !aligned16(Q))) return DASHSVD_EINVAL;
-  if (variant < -1 || variant >= kSpmmVariants) return DASHSVD_EINVAL;
+  if (!variant_ok(variant, kSpmmVariants)) return DASHSVD_EINVAL;
   if (const int rc0 = step_csr_ok(h, A)) return rc0;
+  SpmmHints hints;
+  if (variant >= 0 && (variant & kSpmmHintFlag))
+    if (const int rc0 = step_hints(h, *A, (int64_t)ldx * 4, &hints)) return rc0;
   SpmmPart part;
   part.segments = spmm_segments(*A, h->num_sms);
   const int64_t ldc = ((l + 3) / 4) * 4;
@@ -1021,11 +1179,13 @@ static int spmm_common(dashsvd_handle h, const dashsvd_csr* A, const float* X, i
   part.seg_row = as<int32_t>(h->seg_fwd);
   part.seg_nnz = part.seg_row + part.segments + 1;
   const int var = variant < 0 ? 1 : variant;
+  const int base = var & ~kSpmmHintFlag;
   if ((rc = ensure(h->errw, 16, &moved))) return rc;
-  if (var >= 6) DS_CUDA(cudaMemsetAsync(h->errw.p, 0, sizeof(int), h->stream));
-  if ((var & 1) || var >= 6) DS_CUDA(launch_spmm_partition(*A, part, h->stream));  // merge-path variants
-  DS_CUDA(launch_spmm(*A, part, X, ldx, l, Y, ldy, alpha, Q, ldq, var, scr, h->num_sms, h->stream, as<int>(h->errw)));
-  if (var >= 6) {  // the bulk-copy variants wait on barriers with a bound: report a timeout
+  if (base >= 6) DS_CUDA(cudaMemsetAsync(h->errw.p, 0, sizeof(int), h->stream));
+  if ((base & 1) || base >= 6) DS_CUDA(launch_spmm_partition(*A, part, h->stream));  // merge-path variants
+  DS_CUDA(launch_spmm(*A, part, X, ldx, l, Y, ldy, alpha, Q, ldq, var, scr, h->num_sms, h->stream, as<int>(h->errw),
+                      hints));
+  if (base >= 6) {  // the bulk-copy variants wait on barriers with a bound: report a timeout
     int werr = 0;
     DS_CUDA(cudaMemcpyAsync(&werr, h->errw.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     DS_CUDA(cudaStreamSynchronize(h->stream));
@@ -1050,8 +1210,11 @@ int dashsvd_spmm_bf16(dashsvd_handle h, const dashsvd_csr* A, const void* X, int
   if (ldx < l || ldy < l || ldx % 4 || ldy % 4 || ((uintptr_t)X & 7u) || ((uintptr_t)Y & (y_bf16 ? 7u : 15u)))
     return DASHSVD_EINVAL;
   if (alpha && (!Q || ldq < l || ldq % 4 || ((uintptr_t)Q & 7u))) return DASHSVD_EINVAL;
-  if (variant < -1 || variant >= kSpmmVariantsBf16) return DASHSVD_EINVAL;
+  if (!variant_ok(variant, kSpmmVariantsBf16)) return DASHSVD_EINVAL;
   if (const int rc0 = step_csr_ok(h, A)) return rc0;
+  SpmmHints hints;
+  if (variant >= 0 && (variant & kSpmmHintFlag))
+    if (const int rc0 = step_hints(h, *A, (int64_t)ldx * 2, &hints)) return rc0;
   SpmmPart part;
   part.segments = spmm_segments(*A, h->num_sms);
   const int64_t ldc = ((l + 3) / 4) * 4;
@@ -1072,7 +1235,8 @@ int dashsvd_spmm_bf16(dashsvd_handle h, const dashsvd_csr* A, const void* X, int
   part.seg_nnz = part.seg_row + part.segments + 1;
   const int var = variant < 0 ? 1 : variant;
   if (var & 1) DS_CUDA(launch_spmm_partition(*A, part, h->stream));
-  DS_CUDA(launch_spmm_bf16(*A, part, X, ldx, l, Y, y_bf16 != 0, ldy, alpha, Q, ldq, var, scr, h->num_sms, h->stream));
+  DS_CUDA(launch_spmm_bf16(*A, part, X, ldx, l, Y, y_bf16 != 0, ldy, alpha, Q, ldq, var, scr, h->num_sms, h->stream,
+                           hints));
   return DASHSVD_OK;
 }
 

@@ -94,18 +94,53 @@ struct SpmmScratch {
   int64_t max_segments = 0;
   int ldc = 0;                   // carry row stride (floats, >= l rounded up to 4)
 };
+// L2 hints of a product (variant | kSpmmHintFlag): bitmaps over the gathered
+// rows (kept: evict_last) and over the output rows (stored evict_last).
+struct SpmmHints {
+  const uint32_t* gather_hot = nullptr;  // bitmap over the gathered rows
+  const uint32_t* store_hot = nullptr;   // bitmap over the output rows (may be null)
+  const int32_t* tagged_col = nullptr;   // the CSR's column ids with the gather bit in bit kHotColBit
+};
+constexpr int kSpmmHintFlag = 16;
+constexpr int kHotColBit = 30;
+// out[e] = colidx[e] | (hot bit of row colidx[e]) << kHotColBit
+cudaError_t launch_tag_cols(const int32_t* colidx, int64_t nnz, const uint32_t* hot, int32_t* out, cudaStream_t st);
+// Hot-row bitmaps (k_hot.cu): histogram of row lengths (rowptr) or of
+// counts[i] into kHotBins bins (the last one takes everything above), the
+// threshold that keeps at most max_rows rows (host), and the bitmap.
+constexpr int kHotBins = 32768;
+cudaError_t launch_hot_hist(const int32_t* rowptr, const int32_t* counts, int64_t rows, int32_t* hist,
+                            cudaStream_t st);
+int32_t hot_threshold(const int32_t* hist, int64_t max_rows);
+// counts[c] = occurrences of column id c in colidx (n counters)
+cudaError_t launch_col_counts(const int32_t* colidx, int64_t nnz, int64_t n, int32_t* counts, cudaStream_t st);
+cudaError_t launch_hot_bitmap(const int32_t* rowptr, const int32_t* counts, int64_t rows, int32_t thr, uint32_t* bits,
+                              cudaStream_t st);
 int64_t spmm_segments(const dashsvd_csr& A, int num_sms);
 cudaError_t launch_spmm_partition(const dashsvd_csr& A, SpmmPart& part, cudaStream_t st);
 cudaError_t launch_spmm(const dashsvd_csr& A, const SpmmPart& part, const float* X, int64_t ldx, int l, float* Y,
                         int64_t ldy, const double* alpha, const float* Q, int64_t ldq, int variant,
-                        const SpmmScratch& scr, int num_sms, cudaStream_t st, int* err = nullptr);
+                        const SpmmScratch& scr, int num_sms, cudaStream_t st, int* err = nullptr,
+                        const SpmmHints& hints = SpmmHints());
+// The hinted instantiations (k_spmm_hint.cu), called by launch_spmm /
+// launch_spmm_bf16 when a variant asks for hints and they apply.
+cudaError_t launch_spmm_hinted(const dashsvd_csr& A, const SpmmPart& part, const float* X, int64_t ldx, int l,
+                               float* Y, int64_t ldy, const double* alpha, const float* Q, int64_t ldq, int variant,
+                               const SpmmScratch& scr, int num_sms, cudaStream_t st, int* err,
+                               const SpmmHints& hints);
+cudaError_t launch_spmm_bf16_hinted(const dashsvd_csr& A, const SpmmPart& part, const void* X, int64_t ldx, int l,
+                                    void* Y, bool y_bf16, int64_t ldy, const double* alpha, const void* Q,
+                                    int64_t ldq, int variant, const SpmmScratch& scr, int num_sms, cudaStream_t st,
+                                    const SpmmHints& hints);
+cudaError_t prepare_spmm_hinted();
 // BF16 dense operand (and BF16 Q): Y in BF16 (y_bf16) or FP32
 // Fused pass product Z = A^T (A Q) - alpha Q (one read of A, atomic scatter into Z).
 cudaError_t launch_spmm_fused(const dashsvd_csr& A, const float* Q, int64_t ldq, int l, const double* alpha, float* Z,
                               int64_t ldz, int num_sms, cudaStream_t st);
 cudaError_t launch_spmm_bf16(const dashsvd_csr& A, const SpmmPart& part, const void* X, int64_t ldx, int l, void* Y,
                              bool y_bf16, int64_t ldy, const double* alpha, const void* Q, int64_t ldq, int variant,
-                             const SpmmScratch& scr, int num_sms, cudaStream_t st);
+                             const SpmmScratch& scr, int num_sms, cudaStream_t st,
+                             const SpmmHints& hints = SpmmHints());
 
 // Gram G = C^T C.
 size_t gram_partial_floats(int64_t rows, int l, int num_sms);
@@ -139,8 +174,10 @@ struct EigWork {
   double* X64;    // 6 l x l FP64 matrices for the refinement
   double* lam64;  // kMaxL refined eigenvalues
   double* d0_64;  // kMaxL diagonal of the FP64 Gram
+  double* part64; // 3 x kRefineParts partial sums of the refinement's residual norms
   float2* log;    // (c, s) per sweep x step x pair
 };
+constexpr int kRefineParts = 256;  // (256 / 16)^2 tiles of an l x l product at l = 256
 int eig_max_l_f32();
 size_t eig_work_bytes();
 EigWork eig_work_view(void* base);

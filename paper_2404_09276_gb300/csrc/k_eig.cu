@@ -582,7 +582,7 @@ int eig_max_l_f32() { return kMaxL; }
 size_t eig_work_bytes() {
   const size_t L = kMaxL;
   return 256 + 2 * sizeof(float) * L + sizeof(float) * L * L + 6 * sizeof(double) * L * L + 2 * sizeof(double) * L +
-         sizeof(float2) * (size_t)kMaxSweeps * (kMaxN - 1) * (kMaxN / 2);
+         3 * sizeof(double) * kRefineParts + sizeof(float2) * (size_t)kMaxSweeps * (kMaxN - 1) * (kMaxN / 2);
 }
 
 EigWork eig_work_view(void* base) {
@@ -598,6 +598,8 @@ EigWork eig_work_view(void* base) {
   p += sizeof(double) * L;
   w.d0_64 = reinterpret_cast<double*>(p);
   p += sizeof(double) * L;
+  w.part64 = reinterpret_cast<double*>(p);
+  p += 3 * sizeof(double) * kRefineParts;
   w.d = reinterpret_cast<float*>(p);
   p += sizeof(float) * L;
   w.d0 = reinterpret_cast<float*>(p);

@@ -6,7 +6,7 @@
 // Refinement step (Ogita and Aishima, "Iterative refinement for symmetric
 // eigenvalue decomposition", Japan J. Indust. Appl. Math. 35, 2018): for G
 // and an approximate eigenvector basis X, with R = I - X^T X and S = X^T G X,
-//   lambda_i = s_ii / (1 - r_ii),
+//   lambda_i = s_ii / (1 - r_ii)  (= s_ii / t_ii with T = X^T X),
 //   delta    = 2 (||S - diag(lambda)|| + ||G|| ||R||)     (Frobenius norms here),
 //   e_ij     = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i)  if |lambda_i - lambda_j| > delta,
 //              r_ij / 2                                       otherwise (and on the diagonal),
@@ -23,12 +23,19 @@ namespace {
 
 constexpr int kT = 16;
 
-// C = op(A) B (+ D), l x l, row-major; op(A) = A^T when TRANSA
-template <bool TRANSA, bool ADD>
+__device__ double block_sum(double v, double* red);
+
+// C = op(A) B (+ D), l x l, row-major; op(A) = A^T when TRANSA. NORM = 1 also
+// writes this tile's sum of squared off-diagonal entries of C, NORM = 2 its sum
+// of squared entries of I - C, to part[tile] (tile = blockIdx.y * gridDim.x +
+// blockIdx.x), for the refinement's residual norms.
+template <bool TRANSA, bool ADD, int NORM>
 __global__ void __launch_bounds__(kT* kT) gemm64_kernel(const double* __restrict__ A, int64_t lda,
                                                         const double* __restrict__ B, int64_t ldb,
-                                                        const double* __restrict__ D, double* __restrict__ C, int l) {
+                                                        const double* __restrict__ D, double* __restrict__ C, int l,
+                                                        double* __restrict__ part) {
   __shared__ double As[kT][kT + 1], Bs[kT][kT + 1];
+  __shared__ double red[32];
   const int tx = threadIdx.x % kT, ty = threadIdx.x / kT;
   const int row = blockIdx.y * kT + ty, col = blockIdx.x * kT + tx;
   double acc = 0.0;
@@ -43,15 +50,36 @@ __global__ void __launch_bounds__(kT* kT) gemm64_kernel(const double* __restrict
     __syncthreads();
   }
   if (row < l && col < l) C[(int64_t)row * l + col] = ADD ? D[(int64_t)row * l + col] + acc : acc;
+  if constexpr (NORM != 0) {
+    double q = 0.0;
+    if (row < l && col < l) {
+      if (NORM == 1 && row != col) q = acc * acc;
+      if (NORM == 2) {
+        const double r = (row == col ? 1.0 : 0.0) - acc;
+        q = r * r;
+      }
+    }
+    q = block_sum(q, red);
+    if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = q;
+  }
 }
 
+// X = V32 in FP64, the diagonal of G, and ||G||_F^2 (CTA partials into gpart,
+// summed by each refine_e CTA).
 __global__ void refine_init_kernel(const float* __restrict__ V32, const double* __restrict__ G64, int64_t ldg, int l,
-                                   double* __restrict__ X, double* __restrict__ d0) {
+                                   double* __restrict__ X, double* __restrict__ d0, double* __restrict__ gpart) {
+  __shared__ double red[32];
+  double gg = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)l * l;
        i += (int64_t)gridDim.x * blockDim.x) {
     X[i] = (double)V32[i];
     if (i < l) d0[i] = G64[i * ldg + i];
+    const int r = (int)(i / l), c = (int)(i - (int64_t)r * l);
+    const double g = G64[(int64_t)r * ldg + c];
+    gg += g * g;
   }
+  gg = block_sum(gg, red);
+  if (threadIdx.x == 0) gpart[blockIdx.x] = gg;
 }
 
 __device__ double block_sum(double v, double* red) {
@@ -66,46 +94,46 @@ __device__ double block_sum(double v, double* red) {
   return s;
 }
 
-// lambda and delta from S = X^T G X and T = X^T X (one CTA: three l x l sums)
-__global__ void __launch_bounds__(1024) refine_norms_kernel(const double* __restrict__ S, const double* __restrict__ T,
-                                                            const double* __restrict__ G64, int64_t ldg, int l,
-                                                            double* __restrict__ lam, double* __restrict__ delta) {
+// E from S, T (lambda_i = s_ii / t_ii) and delta = 2 (||S - diag(lambda)||_F +
+// ||G||_F ||I - T||_F), whose sums each CTA first adds up from the partials
+// of the products (off-diagonal squares of S, squares of I - T per tile, and
+// of G per CTA of refine_init) plus the diagonal terms (s_ii - lambda_i)^2.
+// One thread per entry of E, over many CTAs; CTA 0 also writes lambda.
+__global__ void __launch_bounds__(256) refine_e_kernel(const double* __restrict__ S, const double* __restrict__ T,
+                                                       const double* __restrict__ spart,
+                                                       const double* __restrict__ tpart, int ntiles,
+                                                       const double* __restrict__ gpart, int ngpart, int l,
+                                                       double* __restrict__ lam_out, double* __restrict__ E) {
   __shared__ double red[32];
   __shared__ double lm[kMaxL];
+  __shared__ double delta_s;
+  double sd = 0.0, rr = 0.0, gg = 0.0;
   for (int i = threadIdx.x; i < l; i += blockDim.x) {
-    const double r = 1.0 - T[(int64_t)i * l + i];
-    lm[i] = S[(int64_t)i * l + i] / (1.0 - r);
+    const double sii = S[(int64_t)i * l + i];
+    const double li = sii / T[(int64_t)i * l + i];
+    lm[i] = li;
+    sd += (sii - li) * (sii - li);
   }
-  __syncthreads();
-  double sd = 0.0, gg = 0.0, rr = 0.0;
-  for (int64_t idx = threadIdx.x; idx < (int64_t)l * l; idx += blockDim.x) {
-    const int i = (int)(idx / l), j = (int)(idx - (int64_t)i * l);
-    const double s = S[idx] - (i == j ? lm[i] : 0.0);
-    const double r = (i == j ? 1.0 : 0.0) - T[idx];
-    const double g = G64[(int64_t)i * ldg + j];
-    sd += s * s;
-    rr += r * r;
-    gg += g * g;
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+    sd += spart[t];
+    rr += tpart[t];
   }
+  for (int t = threadIdx.x; t < ngpart; t += blockDim.x) gg += gpart[t];
   sd = block_sum(sd, red);
   rr = block_sum(rr, red);
   gg = block_sum(gg, red);
-  for (int i = threadIdx.x; i < l; i += blockDim.x) lam[i] = lm[i];
-  if (threadIdx.x == 0) *delta = 2.0 * (sqrt(sd) + sqrt(gg) * sqrt(rr));
-}
-
-// E from S, T, lambda and delta: one thread per entry, over many CTAs (the
-// FP64 divisions are the costly part on this part's FP64 units)
-__global__ void refine_e_kernel(const double* __restrict__ S, const double* __restrict__ T,
-                                const double* __restrict__ lam, const double* __restrict__ delta, int l,
-                                double* __restrict__ E) {
+  if (threadIdx.x == 0) delta_s = 2.0 * (sqrt(sd) + sqrt(gg) * sqrt(rr));
+  __syncthreads();
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i < l; i += blockDim.x) lam_out[i] = lm[i];
+  const double delta = delta_s;
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= (int64_t)l * l) return;
   const int i = (int)(idx / l), j = (int)(idx - (int64_t)i * l);
   const double r = (i == j ? 1.0 : 0.0) - T[idx];
   double e = 0.5 * r;
-  const double li = lam[i], lj = lam[j];
-  if (i != j && fabs(li - lj) > *delta) e = (S[idx] + lj * r) / (lj - li);
+  const double li = lm[i], lj = lm[j];
+  if (i != j && fabs(li - lj) > delta) e = (S[idx] + lj * r) / (lj - li);
   E[idx] = e;
 }
 
@@ -120,17 +148,25 @@ cudaError_t launch_refine_fp64(const double* G64, int64_t ldg, const float* V32,
   double* Sm = wk.X64 + 3 * LL;
   double* Tm = wk.X64 + 4 * LL;
   double* Em = wk.X64 + 5 * LL;
-  refine_init_kernel<<<(unsigned)ds_ceil_div((int64_t)l * l, 256), 256, 0, st>>>(V32, G64, ldg, l, Xa, wk.d0_64);
+  // partial sums of the residual norms: per tile of S and of T, per CTA of
+  // the init kernel for G (at most kRefineParts each, l <= 256)
+  const dim3 grid((unsigned)ds_ceil_div(l, kT), (unsigned)ds_ceil_div(l, kT));
+  const int ntiles = (int)(grid.x * grid.y);
+  const int ginit = (int)ds_ceil_div((int64_t)l * l, 256);
+  if (ntiles > kRefineParts || ginit > kRefineParts) return cudaErrorInvalidValue;
+  double* spart = wk.part64;
+  double* tpart = spart + kRefineParts;
+  double* gpart = tpart + kRefineParts;
+  refine_init_kernel<<<(unsigned)ginit, 256, 0, st>>>(V32, G64, ldg, l, Xa, wk.d0_64, gpart);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const dim3 grid((unsigned)ds_ceil_div(l, kT), (unsigned)ds_ceil_div(l, kT));
   for (int it = 0; it < iters; ++it) {
-    gemm64_kernel<false, false><<<grid, kT * kT, 0, st>>>(G64, ldg, Xa, l, nullptr, Pm, l);  // P = G X
-    gemm64_kernel<true, false><<<grid, kT * kT, 0, st>>>(Xa, l, Pm, l, nullptr, Sm, l);     // S = X^T P
-    gemm64_kernel<true, false><<<grid, kT * kT, 0, st>>>(Xa, l, Xa, l, nullptr, Tm, l);     // T = X^T X
-    refine_norms_kernel<<<1, 1024, 0, st>>>(Sm, Tm, G64, ldg, l, wk.lam64, wk.scal);
-    refine_e_kernel<<<(unsigned)ds_ceil_div((int64_t)l * l, 128), 128, 0, st>>>(Sm, Tm, wk.lam64, wk.scal, l, Em);
-    gemm64_kernel<false, true><<<grid, kT * kT, 0, st>>>(Xa, l, Em, l, Xa, Xb, l);  // X' = X + X E
+    gemm64_kernel<false, false, 0><<<grid, kT * kT, 0, st>>>(G64, ldg, Xa, l, nullptr, Pm, l, nullptr);  // P = G X
+    gemm64_kernel<true, false, 1><<<grid, kT * kT, 0, st>>>(Xa, l, Pm, l, nullptr, Sm, l, spart);     // S = X^T P
+    gemm64_kernel<true, false, 2><<<grid, kT * kT, 0, st>>>(Xa, l, Xa, l, nullptr, Tm, l, tpart);     // T = X^T X
+    refine_e_kernel<<<(unsigned)ds_ceil_div((int64_t)l * l, 256), 256, 0, st>>>(Sm, Tm, spart, tpart, ntiles, gpart,
+                                                                                 ginit, l, wk.lam64, Em);
+    gemm64_kernel<false, true, 0><<<grid, kT * kT, 0, st>>>(Xa, l, Em, l, Xa, Xb, l, nullptr);  // X' = X + X E
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     double* t = Xa;
     Xa = Xb;

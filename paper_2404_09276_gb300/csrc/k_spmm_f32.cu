@@ -51,15 +51,19 @@ cudaError_t launch_spmm_partition(const dashsvd_csr& A, SpmmPart& part, cudaStre
 
 cudaError_t launch_spmm(const dashsvd_csr& A, const SpmmPart& part, const float* X, int64_t ldx, int l, float* Y,
                         int64_t ldy, const double* alpha, const float* Q, int64_t ldq, int variant,
-                        const SpmmScratch& scr, int num_sms, cudaStream_t st, int* err) {
-  return dispatch<float, float, float>(A, part, X, ldx, l, Y, ldy, alpha, Q, ldq, variant, scr, num_sms, st, err);
+                        const SpmmScratch& scr, int num_sms, cudaStream_t st, int* err, const SpmmHints& hints) {
+  if (use_hints(A, variant, hints))
+    return launch_spmm_hinted(A, part, X, ldx, l, Y, ldy, alpha, Q, ldq, variant, scr, num_sms, st, err, hints);
+  return dispatch<float, float, float, false>(A, part, X, ldx, l, Y, ldy, alpha, Q, ldq, variant, scr, num_sms, st,
+                                              err, hints);
 }
 
 cudaError_t prepare_spmm() {
-  cudaError_t e = prepare_tma<16, float, float>();
-  if (e == cudaSuccess) e = prepare_tma<8, float, float>();
-  if (e == cudaSuccess) e = prepare_tma<16, float, NoShift>();
-  if (e == cudaSuccess) e = prepare_tma<8, float, NoShift>();
+  cudaError_t e = prepare_tma<16, float, float, false>();
+  if (e == cudaSuccess) e = prepare_tma<8, float, float, false>();
+  if (e == cudaSuccess) e = prepare_tma<16, float, NoShift, false>();
+  if (e == cudaSuccess) e = prepare_tma<8, float, NoShift, false>();
+  if (e == cudaSuccess) e = prepare_spmm_hinted();
   return e;
 }
 

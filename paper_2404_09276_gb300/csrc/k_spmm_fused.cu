@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(kThreads) spmm_fused_kernel(const int32_t* __r
                                                               float* __restrict__ Z, int64_t ldz, int l, int nslot) {
   const int lane = threadIdx.x & 31, g = lane >> 3, t = lane & 7;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const Pol<false> pl;
   for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < m; r += warps) {
     const int64_t b = rowptr[r], e = rowptr[r + 1];
     if (b == e) continue;
@@ -50,7 +51,7 @@ __global__ void __launch_bounds__(kThreads) spmm_fused_kernel(const int32_t* __r
       int c;
       float a;
       load_pairs(col, val, p, e, lane, c, a);
-      gather_chunk<V, 2, float>(c, a, (int)(e - p < 32 ? e - p : 32), Q, ldq, nslot, lane, acc);
+      gather_chunk<V, 2, float>(c, a, (int)(e - p < 32 ? e - p : 32), Q, ldq, nslot, lane, acc, pl);
     }
     team_reduce<V>(acc);  // every team holds y_r for its lanes' slots
 #pragma unroll

@@ -112,9 +112,13 @@ def _spmm_check(A, X, Y, l):
     assert med < 1e-6
 
 
+# 17, 19, 21, 22, 23: variants 1, 3, 5, 6, 7 with L2 eviction-priority hints
+HINTED = [17, 19, 21, 22, 23]
+
+
 @pytest.mark.parametrize("name", list(MATRICES))
 @pytest.mark.parametrize("l", [1, 7, 30, 150, 160, 220, 256])
-@pytest.mark.parametrize("variant", range(10))
+@pytest.mark.parametrize("variant", list(range(10)) + HINTED)
 def test_spmm_matches_fp64(ds, h, name, l, variant):
     A = MATRICES[name]()
     rng = np.random.default_rng(l)
@@ -127,7 +131,7 @@ def test_spmm_matches_fp64(ds, h, name, l, variant):
 
 
 @pytest.mark.parametrize("name", ["social", "mixed"])
-@pytest.mark.parametrize("variant", range(10))
+@pytest.mark.parametrize("variant", list(range(10)) + HINTED)
 def test_spmm_shift_matches_fp64(ds, h, name, variant):
     import torch
 
@@ -174,7 +178,7 @@ def test_spmm_fused_matches_fp64(ds, h, name, l):
 
 
 @pytest.mark.parametrize("name", ["social", "mixed"])
-@pytest.mark.parametrize("variant", [0, 1, 3, 5])
+@pytest.mark.parametrize("variant", [0, 1, 3, 5, 17, 21])
 def test_spmm_bf16_matches_fp64(ds, h, name, variant):
     """BF16 dense operands (precision form): the products are exact in FP32 and
     accumulated in FP32; a BF16 output adds one rounding of 2^-9."""

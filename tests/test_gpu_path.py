@@ -99,7 +99,7 @@ def test_graph_and_host_loop_agree(ds):
     np.testing.assert_allclose(a[1], b[1], rtol=1e-5)
 
 
-@pytest.mark.parametrize("variant", range(11))
+@pytest.mark.parametrize("variant", list(range(11)) + [17, 21, 22, 23])  # + 16: with L2 hints
 def test_forced_spmm_variants(ds, variant):
     A, prm = datagen.make_config(3, scale=0.005)
     k, s = 12, 6
