@@ -311,16 +311,24 @@ FORMS = {
 }
 
 
-def _launches_per_run(form, passes, var_fwd, var_bwd, setup_reused=True, fused=False):
-    kpv = lambda v: 2 if (v & 1) else 1  # noqa: E731  kernels per SpMM launch (merge path adds its fix-up)
-    eig = 3 if form == "plain" else 3 + 1 + 3 * 6  # Jacobi, replay, finish (+ 3 FP64 refinement steps)
-    # (the BF16-gather form tunes BF16 variants for the loop; its prologue and final product stay FP32)
-    # the matrix fingerprint, plus the CSR transpose and merge-path partitions unless kept from the last run
-    setup = 1 + (0 if setup_reused else 5 + 2)
-    prologue = 1 + kpv(var_bwd) + 2 + eig + 1
-    # a pass: both products (or the fused one: -alpha Q, then the scatter), Gram + reduce, eig, projection
-    per_pass = (2 if fused else kpv(var_fwd) + kpv(var_bwd)) + 2 + eig + 1
-    final = kpv(var_fwd) + 2 + eig + 2
+def _launches_per_run(form, passes, var_fwd, var_bwd, setup_reused=True, fused=False, overlap=True):
+    """Kernel launches of one dashsvd_run (the library's own kernels)."""
+    kpv = lambda v: 2 if (v & 1) or (v & 15) >= 6 else 1  # noqa: E731  merge path and bulk copy add their fix-up
+    # Jacobi, replay, finish; the precision form adds the refinement's init and
+    # three steps of P = G X, S = X^T P, T = X^T X, E, X' = X + X E
+    eig = 3 if form == "plain" else 3 + 1 + 3 * 5
+    # the matrix fingerprint with its structure check, plus (setup not kept) the
+    # CSR transpose, merge-path partitions, gather histograms, bitmaps and tagged ids
+    setup = 1 + (0 if setup_reused else 5 + 2 + 6)
+    if overlap:  # A Z beside each eigensolve, then Q = Z W and Y = (A Z) W
+        prologue = 1 + kpv(var_bwd) + kpv(var_fwd) + 2 + eig + 2
+        per_pass = kpv(var_bwd) + kpv(var_fwd) + 2 + eig + 2
+        final = 2 + eig + 2
+    else:
+        prologue = 1 + kpv(var_bwd) + 2 + eig + 1
+        # a pass: both products (or the fused one: -alpha Q, then the scatter), Gram + reduce, eig, projection
+        per_pass = (2 if fused else kpv(var_fwd) + kpv(var_bwd)) + 2 + eig + 1
+        final = kpv(var_fwd) + 2 + eig + 2
     return setup + prologue + passes * per_pass + final
 
 
@@ -522,13 +530,42 @@ def _measure_form(form, args, ds, torch, A, Ad, prm, stream, flush, barrier, wor
             "kernel_s_per_run": per_run, "kernel_launch_groups_per_run": per_run_launches,
             "in_loop_s_per_launch": in_loop_per_launch,
             "profiled_run": {"passes": prof_passes, "variants": list(prof_vars),
-                             "sum_s": sum(per_run.values()), "note": "host-driven loop, CUDA events after each "
-                             "group of launches; host_gap = the host's wait between passes"},
+                             "sum_s": sum(v for c, v in per_run.items() if c != "spmm_fwd_overlapped"),
+                             "note": "host-driven loop, CUDA events after each group of launches on the main "
+                             "stream (their sum is the run); host_gap = the host's wait between passes; "
+                             "spmm_fwd = the part of A Z the eigensolve did not hide; spmm_fwd_overlapped = "
+                             "the A Z products start to end on their own stream, during gram and eig"},
             "result_host": result_host,
             "spmm": dict(spmm, tuning_ms=tuning), "clocks": clk,
             "gpu_launches": _launches_per_run(form, passes, var_fwd, var_bwd, bool(info.setup_reused),
-                                              bool(fused)) * args.steps,
+                                              bool(fused), not fused and not gb) * args.steps,
             "bytes": {"spmm_fwd": bytes_fwd, "spmm_bwd": bytes_bwd}}
+
+
+def _time_serial(args, ds, torch, form, A, Ad, prm, stream, flush, barrier):
+    k, s, p_max, tol = prm["k"], prm["s"], prm["p_max"], prm["tol"]
+    fcode = ds.DASHSVD_FORM_PLAIN if form == "plain" else ds.DASHSVD_FORM_PRECISION
+    learned = 1 if form == "precision_learned" else 0
+    with ds.Handle(stream=stream, form=fcode, learned=learned, overlap=0, spmm_variant=args.spmm_variant,
+                   use_graph=0 if args.no_graph else 1) as h:
+        if learned:
+            from paper_2404_09276_gb300 import learn
+
+            h.load_mlp(learn.load_weights()[0])
+        for _ in range(args.warmup):
+            h.run(Ad, k, s, p_max, tol)
+        barrier()
+        ts, info = [], None
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = h.run(Ad, k, s, p_max, tol)[3]
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+    return {"value": statistics.median(ts), "passes": info.passes, "status": info.status,
+            "note": "the chosen form with options.overlap = 0 (A Q after each eigensolve)"}
 
 
 def _git_blob_sha1(path):
@@ -565,13 +602,17 @@ def _roofline(r, A, l, pk):
     of the profiled run (per-launch average over the run's launches of it)."""
     per_run, nl = r["kernel_s_per_run"], r["kernel_launch_groups_per_run"]
     kt = r["kernels_s"]
-    dom = max((c for c in per_run if c not in ("host_gap", "gaussian")), key=per_run.get)
+    dom = max((c for c in per_run if c not in ("host_gap", "gaussian", "spmm_fwd_overlapped")), key=per_run.get)
     fp32_peak = NUM_SMS_GB300 * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     t = per_run[dom]
     base = {"kernel": dom, "launches_per_run": nl[dom], "time_per_run_s": t,
             "timing": "in-loop: CUDA events around each launch group of one host-driven run"}
+    if dom == "spmm_fwd" and nl.get("spmm_fwd_overlapped"):  # the products' own durations, not the exposed part
+        t = per_run["spmm_fwd_overlapped"]
+        base = dict(base, launches_per_run=nl["spmm_fwd_overlapped"], time_per_run_s=t,
+                    timing="in-loop: CUDA events around each A Z product on its own stream")
     if dom in ("spmm_fwd", "spmm_bwd"):
-        n_launch = nl[dom]
+        n_launch = base["launches_per_run"]
         if dom == "spmm_fwd":
             total_bytes = n_launch * r["bytes"]["spmm_fwd"]
             var = r["profiled_run"]["variants"][0]
@@ -663,6 +704,9 @@ def ours(args):
         "kernel_s_per_run": chosen["kernel_s_per_run"], "spmm": chosen["spmm"], "e2e": chosen["e2e"],
         "gpu_launches": chosen["gpu_launches"], "clocks": chosen["clocks"],
     }
+    # the chosen form once more with the serial schedule (options.overlap = 0):
+    # what overlapping A Z with the eigensolve saves
+    line["serial_schedule"] = _time_serial(args, ds, torch, chosen["form"], A, Ad, prm, stream, flush, barrier)
     if "precision_bf16" in res:
         pb = res["precision_bf16"]
         line["precision_bf16_gathers"] = {"value": pb["value"], "passes": pb["passes"], "status": pb["status"],

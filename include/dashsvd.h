@@ -138,7 +138,13 @@ typedef struct {
                               runs agree to rounding, not bit for bit. */
   int32_t profile;         /* 1: the run uses the host-driven loop and records the device time
                               of each group of launches (dashsvd_get_profile); 0: off */
-  int32_t reserved[2];
+  int32_t overlap;         /* 1 (default): A Q of each new basis Q = Z W is computed as
+                              (A Z) W, with A Z on a second stream while the Gram and the
+                              l x l eigensolve (one SM) run, so the eigensolve no longer
+                              holds up the sparse product; the last pass's product is step
+                              9's B. Not with pve_mode = 1, gather_bf16 or the fused pass
+                              product (those keep the serial schedule). 0: serial. */
+  int32_t reserved[1];
 } dashsvd_options;
 
 typedef struct {
@@ -232,14 +238,17 @@ int dashsvd_get_trace(dashsvd_handle h, double* out, int64_t cap, int64_t* count
 int dashsvd_get_tuning(dashsvd_handle h, float* ms, int64_t cap);
 
 /* Device time per step of the last run made with options.profile = 1 (HOST
- * buffer of at least 14 doubles): ms[c] = total milliseconds and ms[7 + c] =
+ * buffer of at least 16 doubles): ms[c] = total milliseconds and ms[8 + c] =
  * number of timed launch groups of category c, where c is 0 the Gaussian block
- * (Alg. 5 step 1), 1 the products A Q (steps 4 and 9), 2 the products
+ * (Alg. 5 step 1), 1 the products A Q (steps 4 and 9; with the overlapped
+ * schedule, the part of A Z the eigensolve did not hide), 2 the products
  * A^T Y - alpha Q (and A^T Omega of step 2), 3 the Gram matrices, 4 the l x l
  * eigensolves with their control tail (Jacobi, eigenvector replay, FP64
  * refinement, conventions, steps 5-7), 5 the projections C W (steps 2, 4, 11),
- * 6 the host's waits between passes of the host-driven loop. The time of the
- * setup fingerprint is not included. */
+ * 6 the host's waits between passes of the host-driven loop, 7 the overlapped
+ * products A Z, start to end on their own stream (they run during categories
+ * 3 and 4, so they are not part of the sum of 0..6). The time of the setup
+ * fingerprint is not included. */
 int dashsvd_get_profile(dashsvd_handle h, double* ms, int64_t cap);
 
 /* ---- learned form --------------------------------------------------------

@@ -62,7 +62,7 @@ class dashsvd_options(C.Structure):
         ("alpha_prev_mode", C.c_int32), ("use_graph", C.c_int32), ("spmm_variant", C.c_int32),
         ("record_trace", C.c_int32), ("shift", C.c_int32), ("gather_bf16", C.c_int32),
         ("pve_mode", C.c_int32), ("trust_csr", C.c_int32), ("deterministic", C.c_int32),
-        ("profile", C.c_int32), ("reserved", C.c_int32 * 2),
+        ("profile", C.c_int32), ("overlap", C.c_int32), ("reserved", C.c_int32 * 1),
     ]
 
 
@@ -161,7 +161,8 @@ dashsvd_csr_check = _export("dashsvd_csr_check")
 dashsvd_eig_fp64 = _export("dashsvd_eig_fp64")
 dashsvd_get_profile = _export("dashsvd_get_profile")
 dashsvd_run_host = _export("dashsvd_run_host")
-PROFILE_CATEGORIES = ("gaussian", "spmm_fwd", "spmm_bwd", "gram", "eig", "project", "host_gap")
+PROFILE_CATEGORIES = ("gaussian", "spmm_fwd", "spmm_bwd", "gram", "eig", "project", "host_gap",
+                      "spmm_fwd_overlapped")
 DASHSVD_CSR_BAD_FIRST, DASHSVD_CSR_BAD_ORDER, DASHSVD_CSR_BAD_LAST, DASHSVD_CSR_BAD_COL = 1, 2, 4, 8
 dashsvd_mlp_forward = _export("dashsvd_mlp_forward")
 dashsvd_mlp_loss_grad = _export("dashsvd_mlp_loss_grad")
@@ -407,9 +408,10 @@ class Handle:
         run made with profile=1."""
         import numpy as np
 
-        buf = np.zeros(14, dtype=np.float64)
+        n = len(PROFILE_CATEGORIES)
+        buf = np.zeros(2 * n, dtype=np.float64)
         check(dashsvd_get_profile(self.h, buf.ctypes.data, buf.size), "dashsvd_get_profile")
-        return {c: (float(buf[i]), int(buf[7 + i])) for i, c in enumerate(PROFILE_CATEGORIES)}
+        return {c: (float(buf[i]), int(buf[n + i])) for i, c in enumerate(PROFILE_CATEGORIES)}
 
     def tuning(self):
         """The autotuner's last measurements: (5 products x 20 variants) ms, 0 = not

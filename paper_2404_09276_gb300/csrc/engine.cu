@@ -69,7 +69,7 @@ T* as(DevBuf& b) {
 }
 
 // categories of dashsvd_get_profile (the order of include/dashsvd.h)
-enum ProfCat : int { kPfGauss = 0, kPfFwd, kPfBwd, kPfGram, kPfEig, kPfProject, kPfGap, kProfCats };
+enum ProfCat : int { kPfGauss = 0, kPfFwd, kPfBwd, kPfGram, kPfEig, kPfProject, kPfGap, kPfFwdConc, kProfCats };
 
 struct GraphKey {
   dashsvd_csr A;
@@ -77,7 +77,7 @@ struct GraphKey {
   double tol;
   float *U, *S, *V;
   uint64_t seed;
-  int alpha_prev_mode, shift, record_trace, var_fwd, var_bwd, form, gather, learned, pve_mode;
+  int alpha_prev_mode, shift, record_trace, var_fwd, var_bwd, form, gather, learned, pve_mode, overlap;
   bool operator==(const GraphKey& o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
 };
 
@@ -91,11 +91,14 @@ struct dashsvd_handle_s {
   cudaStream_t stream = nullptr;
   cudaStream_t cap = nullptr;   // capture stream for the graph (the caller's may be the legacy stream)
   cudaStream_t side = nullptr;  // capture stream for the loop body
+  cudaStream_t aux = nullptr;   // second branch: the sparse product that overlaps the eigensolve
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int device = 0;
   int num_sms = 0;
   // workspace
   DevBuf rowptr_b, col_b, val_b, cursor, scan_tmp;  // the CSR built by transposition
   DevBuf Y, Z, Q, G, W, W2, partial, carry, carry_row, ctl, trace, eigw;
+  DevBuf Yp;  // A Z of the overlapped schedule (A Q = (A Z) W once W is known)
   DevBuf seg_fwd, seg_bwd;  // merge-path partitions of A and A^T (rows, nonzeros)
   DevBuf errw;              // device error word of the bounded-wait kernels
   DevBuf Qb, G64;           // precision form: BF16 basis, FP64 Gram
@@ -154,6 +157,8 @@ struct dashsvd_handle_s {
   std::vector<cudaEvent_t> prof_ev;
   std::vector<int> prof_cat;
   size_t prof_n = 0;
+  std::vector<cudaEvent_t> prof_aux;  // (start, end) pairs around the overlapped products
+  size_t prof_aux_n = 0;
   double prof_ms[kProfCats] = {};
   int prof_cnt[kProfCats] = {};
 };
@@ -183,6 +188,18 @@ cudaError_t tmark(dashsvd_handle h, int cat, cudaStream_t st) {
   return cudaEventRecord(h->prof_ev[h->prof_n++], st);
 }
 
+// Profiling event on the aux stream (start and end of an overlapped product).
+cudaError_t tmark_aux(dashsvd_handle h, cudaStream_t st) {
+  if (!h->prof_on) return cudaSuccess;
+  if (h->prof_aux_n == h->prof_aux.size()) {
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreate(&ev);
+    if (e != cudaSuccess) return e;
+    h->prof_aux.push_back(ev);
+  }
+  return cudaEventRecord(h->prof_aux[h->prof_aux_n++], st);
+}
+
 bool csr_ok(const dashsvd_csr* A) {
   if (!A || A->m < 1 || A->n < 1 || A->nnz < 0 || A->nnz >= (int64_t)1 << 31) return false;
   if (A->m >= (int64_t)1 << 31 || A->n >= (int64_t)1 << 31) return false;
@@ -209,6 +226,7 @@ struct RunPlan {
   int var_fwd, var_bwd;      // SpMM variants of the pass (BF16 operands in the precision form)
   int var_fwd32, var_bwd32;  // FP32 variants (prologue, final, plain form)
   bool fused = false;        // pass product as one fused A^T (A Q) - alpha Q (FP32 gathers only)
+  bool overlap = false;      // A Q as (A Z) W, with A Z running beside the eigensolve
   SpmmPart part_fwd, part_bwd;
   SpmmScratch scr;
   // L2 hints per product: A Q of a pass (gathers Q, stores Y that A^T Y gathers next),
@@ -296,6 +314,38 @@ cudaError_t project_basis_launch(dashsvd_handle h, const RunPlan& p, cudaStream_
                         h->num_sms, st);
 }
 
+// The overlapped schedule: once Z is written, Yp = A Z runs on the aux stream
+// beside the Gram and the eigensolve (one SM) of the main stream; after the
+// join, A Q of the new basis Q = Z W is Y = Yp W (A (Z W) = (A Z) W), a
+// projection like Q's own.
+cudaError_t fork_az(dashsvd_handle h, const RunPlan& p, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = cudaEventRecord(h->ev_fork, st)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(h->aux, h->ev_fork, 0)) != cudaSuccess) return e;
+  if ((e = tmark_aux(h, h->aux)) != cudaSuccess) return e;
+  if ((e = launch_spmm(p.Aw, p.part_fwd, as<float>(h->Z), p.ld, p.l, as<float>(h->Yp), p.ld, nullptr, nullptr, 0,
+                       p.var_fwd, p.scr, h->num_sms, h->aux, as<int>(h->errw), p.hf_final)) != cudaSuccess)
+    return e;
+  if ((e = tmark_aux(h, h->aux)) != cudaSuccess) return e;
+  return cudaEventRecord(h->ev_join, h->aux);
+}
+
+// Join the aux branch, then Q = Z W and Y = Yp W.
+cudaError_t join_and_project(dashsvd_handle h, const RunPlan& p, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = cudaStreamWaitEvent(st, h->ev_join, 0)) != cudaSuccess) return e;
+  if ((e = tmark(h, kPfFwd, st)) != cudaSuccess) return e;  // what of A Z the eigensolve did not hide
+  if ((e = project_basis_launch(h, p, st)) != cudaSuccess) return e;
+  if (precision(h))
+    e = launch_project_tc(as<float>(h->Yp), p.mw, p.l, p.ld, as<float>(h->W), p.ld, p.l, as<float>(h->Y), p.ld,
+                          nullptr, 0, nullptr, as<int>(h->errw), h->num_sms, st);
+  else
+    e = launch_project(as<float>(h->Yp), p.mw, p.l, p.ld, as<float>(h->W), p.ld, p.l, as<float>(h->Y), p.ld,
+                       h->num_sms, st);
+  if (e != cudaSuccess) return e;
+  return tmark(h, kPfProject, st);
+}
+
 cudaError_t launch_prologue(dashsvd_handle h, const RunPlan& p, unsigned long long cond, cudaStream_t st) {
   cudaError_t e;
   // Alg. 5 step 1: Omega (mw x l) into Y
@@ -307,6 +357,11 @@ cudaError_t launch_prologue(dashsvd_handle h, const RunPlan& p, unsigned long lo
                        p.var_bwd32, p.scr, h->num_sms, st, as<int>(h->errw), p.hb)) != cudaSuccess ||
       (e = tmark(h, kPfBwd, st)) != cudaSuccess)
     return e;
+  if (p.overlap) {
+    if ((e = fork_az(h, p, st)) != cudaSuccess) return e;
+    if ((e = eigsvd_step(h, p, as<float>(h->Z), p.nw, kModeInit, cond, st)) != cudaSuccess) return e;
+    return join_and_project(h, p, st);
+  }
   if ((e = eigsvd_step(h, p, as<float>(h->Z), p.nw, kModeInit, cond, st)) != cudaSuccess) return e;
   if ((e = project_basis(h, p, st)) != cudaSuccess) return e;
   if (!direct_pve(h)) return cudaSuccess;
@@ -352,6 +407,15 @@ cudaError_t launch_pass(dashsvd_handle h, const RunPlan& p, unsigned long long c
                                st)) != cudaSuccess ||
         (e = tmark(h, kPfBwd, st)) != cudaSuccess)
       return e;
+  } else if (p.overlap) {  // Y = A Q is there already (the last join); A Z of this pass runs beside the eig
+    if ((e = launch_spmm(p.AwT, p.part_bwd, as<float>(h->Y), p.ld, p.l, as<float>(h->Z), p.ld, &ctl->alpha,
+                         as<float>(h->Q), p.ld, p.var_bwd, p.scr, h->num_sms, st, as<int>(h->errw), p.hb)) !=
+            cudaSuccess ||
+        (e = tmark(h, kPfBwd, st)) != cudaSuccess)
+      return e;
+    if ((e = fork_az(h, p, st)) != cudaSuccess) return e;
+    if ((e = eigsvd_step(h, p, as<float>(h->Z), p.nw, kModePass, cond, st)) != cudaSuccess) return e;
+    return join_and_project(h, p, st);
   } else {
     if ((e = launch_spmm(p.Aw, p.part_fwd, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld, nullptr, nullptr, 0,
                          p.var_fwd, p.scr, h->num_sms, st, as<int>(h->errw), p.hf)) != cudaSuccess ||
@@ -371,7 +435,8 @@ cudaError_t launch_final(dashsvd_handle h, const RunPlan& p, cudaStream_t st) {
   cudaError_t e;
   // step 9: B = A Q (into Y), from the FP32 basis in both forms (already
   // there when the PVE control works on B directly)
-  if (!direct_pve(h) && ((e = launch_spmm(p.Aw, p.part_fwd, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld,
+  if (!direct_pve(h) && !p.overlap &&
+      ((e = launch_spmm(p.Aw, p.part_fwd, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld,
                                           nullptr, nullptr, 0, p.var_fwd32, p.scr, h->num_sms, st,
                                           as<int>(h->errw), p.hf_final)) != cudaSuccess ||
                          (e = tmark(h, kPfFwd, st)) != cudaSuccess))
@@ -637,6 +702,7 @@ int dashsvd_options_init(dashsvd_options* opt) {
   opt->record_trace = 0;
   opt->shift = 1;
   opt->pve_mode = 0;
+  opt->overlap = 1;
   return DASHSVD_OK;
 }
 
@@ -682,6 +748,9 @@ int dashsvd_create(dashsvd_handle* out, const dashsvd_options* opt, void* cuda_s
   h->l2_bytes = l2;
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = prepare_project();
   if (e == cudaSuccess) e = prepare_eig();
   if (e == cudaSuccess) e = prepare_spmm();
@@ -689,6 +758,9 @@ int dashsvd_create(dashsvd_handle* out, const dashsvd_options* opt, void* cuda_s
   if (e == cudaSuccess) e = prepare_project_tc();
   if (e != cudaSuccess) {
     set_last_error("dashsvd_create", e, __FILE__, __LINE__);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->aux) cudaStreamDestroy(h->aux);
     if (h->side) cudaStreamDestroy(h->side);
     if (h->cap) cudaStreamDestroy(h->cap);
     delete h;
@@ -704,7 +776,7 @@ int dashsvd_destroy(dashsvd_handle h) {
   drop_graph(h);
   DevBuf* bufs[] = {&h->rowptr_b, &h->col_b, &h->val_b, &h->cursor, &h->scan_tmp, &h->Y,       &h->Z,
                     &h->Q,        &h->G,     &h->W,     &h->W2,     &h->partial,  &h->carry, &h->carry_row,
-                    &h->ctl,      &h->trace, &h->eigw,   &h->seg_fwd, &h->seg_bwd, &h->errw, &h->Qb, &h->G64,
+                    &h->ctl,      &h->trace, &h->eigw, &h->Yp,  &h->seg_fwd, &h->seg_bwd, &h->errw, &h->Qb, &h->G64,
                     &h->mlpw, &h->mlp_part, &h->fpw, &h->det_work, &h->h_rowptr, &h->h_col, &h->h_val, &h->h_U,
                     &h->h_S, &h->h_V, &h->hot_fwd, &h->hot_bwd, &h->hot_hist,
                     &h->tag_fwd, &h->tag_bwd, &h->st_counts, &h->st_hot, &h->st_tag, &h->mt_rowptr, &h->mt_col, &h->mt_val, &h->mt_cursor,
@@ -713,6 +785,10 @@ int dashsvd_destroy(dashsvd_handle h) {
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   for (cudaEvent_t ev : h->prof_ev) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : h->prof_aux) cudaEventDestroy(ev);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->aux) cudaStreamDestroy(h->aux);
   if (h->side) cudaStreamDestroy(h->side);
   if (h->cap) cudaStreamDestroy(h->cap);
   delete h;
@@ -971,6 +1047,8 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
   }
   if (forced < 0 && !h->opt.deterministic && (rc = autotune_spmm(h, p, *A)) != DASHSVD_OK) return rc;
   if (direct_pve(h)) p.fused = false;  // B = A Q is stored every pass
+  p.overlap = h->opt.overlap && !direct_pve(h) && !bf16_gathers(h) && !p.fused;
+  if (p.overlap && (rc = ensure(h->Yp, sizeof(float) * (size_t)(p.mw * p.ld), &moved))) return rc;
   DS_CUDA(cudaMemsetAsync(h->errw.p, 0, sizeof(int), st));
 
   if (h->opt.use_graph && !h->opt.profile) {
@@ -994,6 +1072,7 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
     key.gather = h->opt.gather_bf16;
     key.learned = h->opt.learned;
     key.pve_mode = h->opt.pve_mode;
+    key.overlap = p.overlap ? 1 : 0;
     if (moved || !h->have_graph || !(key == h->key)) {
       if ((rc = build_graph(h, p)) != DASHSVD_OK) return rc;
       h->key = key;
@@ -1002,6 +1081,7 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
   } else {
     h->prof_on = h->opt.profile != 0;
     h->prof_n = 0;
+    h->prof_aux_n = 0;
     std::memset(h->prof_ms, 0, sizeof(h->prof_ms));
     std::memset(h->prof_cnt, 0, sizeof(h->prof_cnt));
     const int rc_loop = [&]() -> int {
@@ -1026,6 +1106,12 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
         h->prof_ms[h->prof_cat[i]] += ms;
         h->prof_cnt[h->prof_cat[i]] += 1;
       }
+      for (size_t i = 0; i + 1 < h->prof_aux_n; i += 2) {  // the overlapped products, start to end
+        float ms = 0.f;
+        DS_CUDA(cudaEventElapsedTime(&ms, h->prof_aux[i], h->prof_aux[i + 1]));
+        h->prof_ms[kPfFwdConc] += ms;
+        h->prof_cnt[kPfFwdConc] += 1;
+      }
     }
     h->prof_on = false;
     if (rc_loop != DASHSVD_OK) return rc_loop;
@@ -1048,7 +1134,7 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
     int64_t ws = 0;
     DevBuf* bufs[] = {&h->rowptr_b, &h->col_b, &h->val_b, &h->cursor, &h->scan_tmp, &h->Y,       &h->Z,
                       &h->Q,        &h->G,     &h->W,     &h->W2,     &h->partial,  &h->carry, &h->carry_row,
-                      &h->ctl,      &h->trace, &h->eigw,   &h->seg_fwd, &h->seg_bwd, &h->errw, &h->Qb, &h->G64,
+                      &h->ctl,      &h->trace, &h->eigw, &h->Yp,  &h->seg_fwd, &h->seg_bwd, &h->errw, &h->Qb, &h->G64,
                     &h->mlpw, &h->mlp_part, &h->fpw, &h->det_work, &h->h_rowptr, &h->h_col, &h->h_val, &h->h_U,
                     &h->h_S, &h->h_V, &h->hot_fwd, &h->hot_bwd, &h->hot_hist,
                     &h->tag_fwd, &h->tag_bwd, &h->st_counts, &h->st_hot, &h->st_tag, &h->mt_rowptr, &h->mt_col, &h->mt_val, &h->mt_cursor,

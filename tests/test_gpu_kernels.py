@@ -68,11 +68,24 @@ def _mixed_matrix(seed=3):
     return datagen.Csr(m, n, A.indptr.astype(np.int32), A.indices.astype(np.int32), A.data.astype(np.float32))
 
 
+_CACHE = {}
+
+
+def _cached(name, make):
+    # the matrices are generated once per session (read-only in every test)
+    def get():
+        if name not in _CACHE:
+            _CACHE[name] = make()
+        return _CACHE[name]
+
+    return get
+
+
 MATRICES = {
-    "cfg1x0.1": lambda: datagen.make_config(1, scale=0.1)[0],
-    "social": lambda: datagen.make_config(2, scale=0.003)[0],
-    "termdoc": lambda: datagen.make_config(3, scale=0.01)[0],
-    "mixed": _mixed_matrix,
+    "cfg1x0.1": _cached("cfg1x0.1", lambda: datagen.make_config(1, scale=0.1)[0]),
+    "social": _cached("social", lambda: datagen.make_config(2, scale=0.003)[0]),
+    "termdoc": _cached("termdoc", lambda: datagen.make_config(3, scale=0.01)[0]),
+    "mixed": _cached("mixed", _mixed_matrix),
 }
 
 

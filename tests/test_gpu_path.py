@@ -389,3 +389,36 @@ def test_full_size_gaussian_block_sampled(ds):
             Y = h.gaussian(0x5EED, 128, 150, row0).cpu().numpy()
             ref = oracle.gaussian_block(0x5EED, 128, 150, row0)
             np.testing.assert_allclose(Y[:, :150], ref, rtol=1e-5, atol=2e-6)
+
+
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("use_graph", [1, 0])
+def test_overlapped_schedule_matches_serial(ds, form, use_graph):
+    """options.overlap computes A Q of each new basis as (A Z) W with A Z on a
+    second stream beside the eigensolve; against the serial schedule (and the
+    oracle) on the same matrix and Omega: the same stop pass and sigma to
+    FP32 rounding, on the graph loop and on the host-driven loop."""
+    A, prm = datagen.make_config(2, scale=0.01)  # 10 000 x 10 000 power-law graph
+    k, s = 20, 10
+    a = _run(ds, A, k, s, 8, 1e-2, form=form, use_graph=use_graph, overlap=1)
+    b = _run(ds, A, k, s, 8, 1e-2, form=form, use_graph=use_graph, overlap=0)
+    assert a[3].passes == b[3].passes and a[3].status == b[3].status
+    np.testing.assert_allclose(a[1], b[1], rtol=2e-5)
+    ref = oracle.dashsvd(A.to_scipy(), k, s, p_max=a[3].passes, tol=0.0, seed=0x5EED)
+    _compare(a[0], a[1], a[2], ref, k, sig_tol=1e-4 if form == 0 else 1e-3)
+
+
+def test_overlapped_schedule_profile(ds):
+    """The profiled host-driven run reports the overlapped products A Z on
+    their own stream: one per eigensolve but the final one."""
+    import torch
+
+    A, prm = datagen.make_config(2, scale=0.01)
+    with ds.Handle(profile=1) as h:
+        U, S, V, info = h.run(ds.CsrDevice.from_host(A), 20, 10, 5, 0.0)
+        torch.cuda.synchronize()
+        prof = h.profile()
+    assert prof["spmm_fwd_overlapped"][1] == info.passes + 1  # prologue and every pass
+    assert prof["spmm_bwd"][1] == info.passes + 1
+    assert prof["eig"][1] == info.passes + 2
+    assert all(ms >= 0.0 for ms, _ in prof.values())
