@@ -67,8 +67,8 @@ def _args():
                     help="both: time the plain FP32 form, the precision form and (when its validation let "
                          "it ship) the precision form with the learned network; the last is the chosen form")
     ap.add_argument("--spmm-variant", type=int, default=-1,
-                    help="force one SpMM variant for both products (-1: autotuned; profiling under ncu, whose "
-                         "serialised launches mislead the autotuner)")
+                    help="force the SpMM variants (-1: autotuned; a variant code for both products, or "
+                         "fwd | bwd << 8; for profiling under ncu, whose serialised launches mislead the autotuner)")
     ap.add_argument("--with-bf16-gathers", action="store_true",
                     help="also time the precision form with BF16 gathered operands")
     ap.add_argument("--no-graph", action="store_true",

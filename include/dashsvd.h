@@ -101,7 +101,9 @@ typedef struct {
                               hints (the rows a product gathers most are kept in L2 with
                               evict_last; the CSR, the -alpha Q operand and the outputs
                               the next product does not gather stream with evict_first;
-                              see k_hot.cu); other v + 16 run without hints */
+                              see k_hot.cu); other v + 16 run without hints; a pair
+                              f | b << 8 (values of 256 and up) forces f for A Q and b
+                              for A^T Y - alpha Q */
   int32_t record_trace;    /* 1: keep the per-pass Shat / shift history (get_trace) */
   int32_t shift;           /* 1: dynamic shifts (dashSVD, Alg. 5 step 6); 0: alpha = 0 (the
                               basic randomized SVD, Alg. 1 form); 2: the shift of the first

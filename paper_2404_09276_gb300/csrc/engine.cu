@@ -68,6 +68,9 @@ T* as(DevBuf& b) {
   return reinterpret_cast<T*>(b.p);
 }
 
+constexpr int kSpmmVariantsAll = 10;  // SpMM variant codes 0..9 (+ 16: with L2 hints)
+constexpr int kSpmmFusedCode = 10;    // options.spmm_variant value of the fused pass product
+
 // categories of dashsvd_get_profile (the order of include/dashsvd.h)
 enum ProfCat : int { kPfGauss = 0, kPfFwd, kPfBwd, kPfGram, kPfEig, kPfProject, kPfGap, kPfFwdConc, kProfCats };
 
@@ -91,14 +94,19 @@ struct dashsvd_handle_s {
   cudaStream_t stream = nullptr;
   cudaStream_t cap = nullptr;   // capture stream for the graph (the caller's may be the legacy stream)
   cudaStream_t side = nullptr;  // capture stream for the loop body
-  cudaStream_t aux = nullptr;   // second branch: the sparse product that overlaps the eigensolve
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // second branch: the sparse product that overlaps the eigensolve. A stream
+  // belongs to one capture sequence at a time, so the loop body (captured into
+  // the conditional node's graph while the outer capture is still open) forks
+  // to its own stream and events.
+  cudaStream_t aux = nullptr, aux_body = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork_body = nullptr, ev_join_body = nullptr;
   int device = 0;
   int num_sms = 0;
   // workspace
   DevBuf rowptr_b, col_b, val_b, cursor, scan_tmp;  // the CSR built by transposition
   DevBuf Y, Z, Q, G, W, W2, partial, carry, carry_row, ctl, trace, eigw;
-  DevBuf Yp;  // A Z of the overlapped schedule (A Q = (A Z) W once W is known)
+  DevBuf Yp;      // A Z of the overlapped schedule (A Q = (A Z) W once W is known)
+  DevBuf seg_ctr; // segment counter of the overlapped A Z
   DevBuf seg_fwd, seg_bwd;  // merge-path partitions of A and A^T (rows, nonzeros)
   DevBuf errw;              // device error word of the bounded-wait kernels
   DevBuf Qb, G64;           // precision form: BF16 basis, FP64 Gram
@@ -258,6 +266,16 @@ EigArgs eig_args(dashsvd_handle h, const RunPlan& p, int mode, unsigned long lon
 }
 
 bool precision(dashsvd_handle h) { return h->opt.form == DASHSVD_FORM_PRECISION; }
+
+// options.spmm_variant: -1, kSpmmFused, a variant code (0..9, or 16 + v), or
+// a pair (A Q code) | (A^T Y code) << 8 with both codes of that kind
+bool one_variant_ok(int v) { return (v >= 0 && v < kSpmmVariantsAll) || ((v & kSpmmHintFlag) && (v & ~kSpmmHintFlag) < kSpmmVariantsAll); }
+bool forced_variant_ok(int v) {
+  if (v == -1 || v == kSpmmFusedCode) return true;
+  if (v < 0) return false;
+  if (v < 256) return one_variant_ok(v);
+  return (v >> 16) == 0 && one_variant_ok(v & 0xFF) && one_variant_ok((v >> 8) & 0xFF);
+}
 // BF16 storage of the gathered operands Q and Y (an option of the precision form)
 bool bf16_gathers(dashsvd_handle h) { return precision(h) && h->opt.gather_bf16; }
 // PVE control on sigma(A Q) of every pass instead of the surrogate
@@ -268,16 +286,20 @@ bool direct_pve(dashsvd_handle h) { return h->opt.pve_mode == 1; }
 constexpr int kRefineIters = 3;
 constexpr double kEpsBf16x3 = 1.52587890625e-05;  // 2^-16
 
+cudaError_t fork_az(dashsvd_handle h, const RunPlan& p, cudaStream_t st);
+
 // eigSVD of C (rows x l): Gram, eigensolve with the control tail (the
-// projection C W follows separately)
+// projection C W follows separately). With `fork`, the overlapped product A Z
+// is forked once the Gram is written, so it runs beside the eigensolve only.
 cudaError_t eigsvd_step(dashsvd_handle h, const RunPlan& p, const float* C, int64_t rows, int mode,
-                        unsigned long long cond, cudaStream_t st) {
+                        unsigned long long cond, cudaStream_t st, bool fork = false) {
   cudaError_t e;
   if (precision(h)) {
     if ((e = launch_gram_tc(C, rows, p.l, p.ld, as<double>(h->G64), p.ld, as<float>(h->G), p.ld,
                             as<float>(h->partial), as<int>(h->errw), h->num_sms, st)) != cudaSuccess ||
         (e = tmark(h, kPfGram, st)) != cudaSuccess)
       return e;
+    if (fork && (e = fork_az(h, p, st)) != cudaSuccess) return e;
     if ((e = launch_eig_refined(as<float>(h->G), p.ld, as<double>(h->G64), p.ld, kEpsBf16x3, kRefineIters,
                                 eig_args(h, p, mode, cond), eig_work_view(h->eigw.p), st)) != cudaSuccess)
       return e;
@@ -287,6 +309,7 @@ cudaError_t eigsvd_step(dashsvd_handle h, const RunPlan& p, const float* C, int6
           cudaSuccess ||
       (e = tmark(h, kPfGram, st)) != cudaSuccess)
     return e;
+  if (fork && (e = fork_az(h, p, st)) != cudaSuccess) return e;
   if ((e = launch_eig_f32(as<float>(h->G), p.ld, eig_args(h, p, mode, cond), eig_work_view(h->eigw.p), st)) !=
       cudaSuccess)
     return e;
@@ -318,22 +341,55 @@ cudaError_t project_basis_launch(dashsvd_handle h, const RunPlan& p, cudaStream_
 // beside the Gram and the eigensolve (one SM) of the main stream; after the
 // join, A Q of the new basis Q = Z W is Y = Yp W (A (Z W) = (A Z) W), a
 // projection like Q's own.
+// SMs kept free of the overlapped product for the eigensolve's kernels (the
+// one-CTA Jacobi and the small multi-CTA replay, refinement and finish).
+constexpr int kOverlapReservedSMs = 8;
+
+// The loop body is captured on h->side and forks to its own stream and events.
+struct Branch {
+  cudaStream_t aux;
+  cudaEvent_t fork, join;
+};
+Branch branch_of(dashsvd_handle h, cudaStream_t st) {
+  if (st == h->side) return {h->aux_body, h->ev_fork_body, h->ev_join_body};
+  return {h->aux, h->ev_fork, h->ev_join};
+}
+
 cudaError_t fork_az(dashsvd_handle h, const RunPlan& p, cudaStream_t st) {
+  const Branch b = branch_of(h, st);
   cudaError_t e;
-  if ((e = cudaEventRecord(h->ev_fork, st)) != cudaSuccess) return e;
-  if ((e = cudaStreamWaitEvent(h->aux, h->ev_fork, 0)) != cudaSuccess) return e;
-  if ((e = tmark_aux(h, h->aux)) != cudaSuccess) return e;
+  // the branch stream may only join the capture sequence of st (or none)
+  cudaStreamCaptureStatus cs_st = cudaStreamCaptureStatusNone, cs_aux = cudaStreamCaptureStatusNone;
+  unsigned long long id_st = 0, id_aux = 0;
+  if ((e = cudaStreamGetCaptureInfo(st, &cs_st, &id_st)) != cudaSuccess) return e;
+  if ((e = cudaStreamGetCaptureInfo(b.aux, &cs_aux, &id_aux)) != cudaSuccess) return e;
+  if (cs_aux == cudaStreamCaptureStatusActive && (cs_st != cudaStreamCaptureStatusActive || id_aux != id_st))
+    return cudaErrorStreamCaptureMerge;
+  if ((e = cudaEventRecord(b.fork, st)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(b.aux, b.fork, 0)) != cudaSuccess) return e;
+  if ((e = tmark_aux(h, b.aux)) != cudaSuccess) return e;
+  // the merge-path and bulk-copy variants (one launch each) leave the first
+  // kOverlapReservedSMs SMs to the eigensolve: their warps then take segments
+  // from a counter, so CTAs that leave on those SMs lose no work
+  SpmmScratch scr = p.scr;
+  const int base = p.var_fwd & ~kSpmmHintFlag;
+  if (base == 1 || base == 3 || base == 5 || base == 6 || base == 7) {
+    if ((e = cudaMemsetAsync(h->seg_ctr.p, 0, sizeof(int32_t), b.aux)) != cudaSuccess) return e;
+    scr.seg_counter = as<int32_t>(h->seg_ctr);
+    scr.reserve_sms = kOverlapReservedSMs;
+  }
   if ((e = launch_spmm(p.Aw, p.part_fwd, as<float>(h->Z), p.ld, p.l, as<float>(h->Yp), p.ld, nullptr, nullptr, 0,
-                       p.var_fwd, p.scr, h->num_sms, h->aux, as<int>(h->errw), p.hf_final)) != cudaSuccess)
+                       p.var_fwd, scr, h->num_sms, b.aux, as<int>(h->errw), p.hf_final)) != cudaSuccess)
     return e;
-  if ((e = tmark_aux(h, h->aux)) != cudaSuccess) return e;
-  return cudaEventRecord(h->ev_join, h->aux);
+  if ((e = tmark_aux(h, b.aux)) != cudaSuccess) return e;
+  return cudaEventRecord(b.join, b.aux);
 }
 
 // Join the aux branch, then Q = Z W and Y = Yp W.
 cudaError_t join_and_project(dashsvd_handle h, const RunPlan& p, cudaStream_t st) {
+  const Branch b = branch_of(h, st);
   cudaError_t e;
-  if ((e = cudaStreamWaitEvent(st, h->ev_join, 0)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(st, b.join, 0)) != cudaSuccess) return e;
   if ((e = tmark(h, kPfFwd, st)) != cudaSuccess) return e;  // what of A Z the eigensolve did not hide
   if ((e = project_basis_launch(h, p, st)) != cudaSuccess) return e;
   if (precision(h))
@@ -358,8 +414,7 @@ cudaError_t launch_prologue(dashsvd_handle h, const RunPlan& p, unsigned long lo
       (e = tmark(h, kPfBwd, st)) != cudaSuccess)
     return e;
   if (p.overlap) {
-    if ((e = fork_az(h, p, st)) != cudaSuccess) return e;
-    if ((e = eigsvd_step(h, p, as<float>(h->Z), p.nw, kModeInit, cond, st)) != cudaSuccess) return e;
+    if ((e = eigsvd_step(h, p, as<float>(h->Z), p.nw, kModeInit, cond, st, true)) != cudaSuccess) return e;
     return join_and_project(h, p, st);
   }
   if ((e = eigsvd_step(h, p, as<float>(h->Z), p.nw, kModeInit, cond, st)) != cudaSuccess) return e;
@@ -413,8 +468,7 @@ cudaError_t launch_pass(dashsvd_handle h, const RunPlan& p, unsigned long long c
             cudaSuccess ||
         (e = tmark(h, kPfBwd, st)) != cudaSuccess)
       return e;
-    if ((e = fork_az(h, p, st)) != cudaSuccess) return e;
-    if ((e = eigsvd_step(h, p, as<float>(h->Z), p.nw, kModePass, cond, st)) != cudaSuccess) return e;
+    if ((e = eigsvd_step(h, p, as<float>(h->Z), p.nw, kModePass, cond, st, true)) != cudaSuccess) return e;
     return join_and_project(h, p, st);
   } else {
     if ((e = launch_spmm(p.Aw, p.part_fwd, as<float>(h->Q), p.ld, p.l, as<float>(h->Y), p.ld, nullptr, nullptr, 0,
@@ -734,9 +788,7 @@ int dashsvd_create(dashsvd_handle* out, const dashsvd_options* opt, void* cuda_s
   else
     dashsvd_options_init(&h->opt);
   if ((h->opt.alpha_prev_mode != 0 && h->opt.alpha_prev_mode != 1) || h->opt.shift < 0 || h->opt.shift > 2 ||
-      h->opt.spmm_variant < -1 ||
-      (h->opt.spmm_variant > kSpmmFused && !(h->opt.spmm_variant & kSpmmHintFlag)) ||
-      (h->opt.spmm_variant & kSpmmHintFlag && (h->opt.spmm_variant & ~kSpmmHintFlag) >= kSpmmVariants)) {
+      !forced_variant_ok(h->opt.spmm_variant)) {
     delete h;
     return DASHSVD_EINVAL;
   }
@@ -749,8 +801,11 @@ int dashsvd_create(dashsvd_handle* out, const dashsvd_options* opt, void* cuda_s
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->aux_body, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork_body, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join_body, cudaEventDisableTiming);
   if (e == cudaSuccess) e = prepare_project();
   if (e == cudaSuccess) e = prepare_eig();
   if (e == cudaSuccess) e = prepare_spmm();
@@ -758,8 +813,11 @@ int dashsvd_create(dashsvd_handle* out, const dashsvd_options* opt, void* cuda_s
   if (e == cudaSuccess) e = prepare_project_tc();
   if (e != cudaSuccess) {
     set_last_error("dashsvd_create", e, __FILE__, __LINE__);
+    if (h->ev_join_body) cudaEventDestroy(h->ev_join_body);
+    if (h->ev_fork_body) cudaEventDestroy(h->ev_fork_body);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->aux_body) cudaStreamDestroy(h->aux_body);
     if (h->aux) cudaStreamDestroy(h->aux);
     if (h->side) cudaStreamDestroy(h->side);
     if (h->cap) cudaStreamDestroy(h->cap);
@@ -776,7 +834,7 @@ int dashsvd_destroy(dashsvd_handle h) {
   drop_graph(h);
   DevBuf* bufs[] = {&h->rowptr_b, &h->col_b, &h->val_b, &h->cursor, &h->scan_tmp, &h->Y,       &h->Z,
                     &h->Q,        &h->G,     &h->W,     &h->W2,     &h->partial,  &h->carry, &h->carry_row,
-                    &h->ctl,      &h->trace, &h->eigw, &h->Yp,  &h->seg_fwd, &h->seg_bwd, &h->errw, &h->Qb, &h->G64,
+                    &h->ctl,      &h->trace, &h->eigw, &h->Yp, &h->seg_ctr, &h->seg_fwd, &h->seg_bwd, &h->errw, &h->Qb, &h->G64,
                     &h->mlpw, &h->mlp_part, &h->fpw, &h->det_work, &h->h_rowptr, &h->h_col, &h->h_val, &h->h_U,
                     &h->h_S, &h->h_V, &h->hot_fwd, &h->hot_bwd, &h->hot_hist,
                     &h->tag_fwd, &h->tag_bwd, &h->st_counts, &h->st_hot, &h->st_tag, &h->mt_rowptr, &h->mt_col, &h->mt_val, &h->mt_cursor,
@@ -786,8 +844,11 @@ int dashsvd_destroy(dashsvd_handle h) {
     if (b->p) cudaFree(b->p);
   for (cudaEvent_t ev : h->prof_ev) cudaEventDestroy(ev);
   for (cudaEvent_t ev : h->prof_aux) cudaEventDestroy(ev);
+  if (h->ev_join_body) cudaEventDestroy(h->ev_join_body);
+  if (h->ev_fork_body) cudaEventDestroy(h->ev_fork_body);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->aux_body) cudaStreamDestroy(h->aux_body);
   if (h->aux) cudaStreamDestroy(h->aux);
   if (h->side) cudaStreamDestroy(h->side);
   if (h->cap) cudaStreamDestroy(h->cap);
@@ -889,7 +950,8 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
   if (l > mn || l > DASHSVD_MAX_L) return DASHSVD_EINVAL;
   if (h->opt.gather_bf16 && !precision(h)) return DASHSVD_EINVAL;
   if (h->opt.gather_bf16 && h->opt.spmm_variant >= 0 &&
-      (h->opt.spmm_variant & ~kSpmmHintFlag) >= kSpmmVariantsBf16)
+      (((h->opt.spmm_variant & 0xFF) & ~kSpmmHintFlag) >= kSpmmVariantsBf16 ||
+       (((h->opt.spmm_variant >> 8) & 0xFF) & ~kSpmmHintFlag) >= kSpmmVariantsBf16))
     return DASHSVD_EINVAL;
   if (h->opt.learned && (!h->mlp_loaded || h->opt.shift != 1)) return DASHSVD_EINVAL;
   if (h->opt.pve_mode < 0 || h->opt.pve_mode > 1) return DASHSVD_EINVAL;
@@ -972,8 +1034,10 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
   // summation order from run to run)
   const int dflt = h->opt.deterministic ? 5 : 1;
   const bool forced_var = forced >= 0 && forced != kSpmmFused;  // 0..9, or 16..25 (with L2 hints)
-  p.var_fwd = p.var_fwd32 = forced_var ? forced : dflt;
-  p.var_bwd = p.var_bwd32 = forced_var ? forced : dflt;
+  const int forced_fwd = forced >= 256 ? (forced & 0xFF) : forced;
+  const int forced_bwd = forced >= 256 ? ((forced >> 8) & 0xFF) : forced;
+  p.var_fwd = p.var_fwd32 = forced_var ? forced_fwd : dflt;
+  p.var_bwd = p.var_bwd32 = forced_var ? forced_bwd : dflt;
   p.fused = forced == kSpmmFused;
 
   cudaStream_t st = h->stream;
@@ -1048,7 +1112,9 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
   if (forced < 0 && !h->opt.deterministic && (rc = autotune_spmm(h, p, *A)) != DASHSVD_OK) return rc;
   if (direct_pve(h)) p.fused = false;  // B = A Q is stored every pass
   p.overlap = h->opt.overlap && !direct_pve(h) && !bf16_gathers(h) && !p.fused;
-  if (p.overlap && (rc = ensure(h->Yp, sizeof(float) * (size_t)(p.mw * p.ld), &moved))) return rc;
+  if (p.overlap && ((rc = ensure(h->Yp, sizeof(float) * (size_t)(p.mw * p.ld), &moved)) ||
+                    (rc = ensure(h->seg_ctr, 16, &moved))))
+    return rc;
   DS_CUDA(cudaMemsetAsync(h->errw.p, 0, sizeof(int), st));
 
   if (h->opt.use_graph && !h->opt.profile) {
@@ -1134,7 +1200,7 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
     int64_t ws = 0;
     DevBuf* bufs[] = {&h->rowptr_b, &h->col_b, &h->val_b, &h->cursor, &h->scan_tmp, &h->Y,       &h->Z,
                       &h->Q,        &h->G,     &h->W,     &h->W2,     &h->partial,  &h->carry, &h->carry_row,
-                      &h->ctl,      &h->trace, &h->eigw, &h->Yp,  &h->seg_fwd, &h->seg_bwd, &h->errw, &h->Qb, &h->G64,
+                      &h->ctl,      &h->trace, &h->eigw, &h->Yp, &h->seg_ctr, &h->seg_fwd, &h->seg_bwd, &h->errw, &h->Qb, &h->G64,
                     &h->mlpw, &h->mlp_part, &h->fpw, &h->det_work, &h->h_rowptr, &h->h_col, &h->h_val, &h->h_U,
                     &h->h_S, &h->h_V, &h->hot_fwd, &h->hot_bwd, &h->hot_hist,
                     &h->tag_fwd, &h->tag_bwd, &h->st_counts, &h->st_hot, &h->st_tag, &h->mt_rowptr, &h->mt_col, &h->mt_val, &h->mt_cursor,

@@ -93,6 +93,12 @@ struct SpmmScratch {
   int32_t* carry_row = nullptr;  // 2 * max_segments
   int64_t max_segments = 0;
   int ldc = 0;                   // carry row stride (floats, >= l rounded up to 4)
+  // merge-path and bulk-copy variants only: when seg_counter is given (zeroed
+  // before the launch), warps take segments from it one at a time instead of
+  // a fixed stride, and CTAs that land on an SM with id < reserve_sms leave at
+  // once, so those SMs stay free for work running beside the product
+  int32_t* seg_counter = nullptr;
+  int reserve_sms = 0;
 };
 // L2 hints of a product (variant | kSpmmHintFlag): bitmaps over the gathered
 // rows (kept: evict_last) and over the output rows (stored evict_last).

@@ -372,6 +372,28 @@ __global__ void __launch_bounds__(kThreads, MINB) spmm_rows_kernel(const int32_t
   }
 }
 
+// Segment scheduling of the merge-path kernels: a fixed stride over all
+// warps, or (ctr given) the next index from a counter, one per warp. A CTA
+// on a reserved SM (id < reserve) takes no segment.
+__device__ __forceinline__ bool on_reserved_sm(int reserve) {
+  if (reserve <= 0) return false;
+  uint32_t smid;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+  return (int)smid < reserve;
+}
+__device__ __forceinline__ int64_t first_segment(int32_t* ctr, int64_t static_first, int lane) {
+  if (!ctr) return static_first;
+  int v = 0;
+  if (lane == 0) v = atomicAdd(ctr, 1);
+  return __shfl_sync(kFull, v, 0);
+}
+__device__ __forceinline__ int64_t next_segment(int32_t* ctr, int64_t cur, int64_t stride, int lane) {
+  if (!ctr) return cur + stride;
+  int v = 0;
+  if (lane == 0) v = atomicAdd(ctr, 1);
+  return __shfl_sync(kFull, v, 0);
+}
+
 // (rows completed, nonzeros consumed) at merge-path diagonal d.
 __device__ __forceinline__ void merge_search(int64_t d, const int32_t* __restrict__ rowptr, int64_t m, int64_t nnz,
                                              int64_t& i, int64_t& j) {
@@ -408,13 +430,16 @@ __global__ void __launch_bounds__(kThreads, MINB) spmm_merge_kernel(const int32_
                                                               const TIn* __restrict__ X, int64_t ldx,
                                                               TOut* __restrict__ Y, int64_t ldy, int nslot,
                                                               Epilogue<TQ> ep, SpmmPart part, float* __restrict__ carry,
-                                                              int32_t* __restrict__ carry_row, int ldc) {
+                                                              int32_t* __restrict__ carry_row, int ldc,
+                                                              int32_t* __restrict__ seg_ctr, int reserve) {
+  if (on_reserved_sm(reserve)) return;
   const int lane = threadIdx.x & 31;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const float alpha = ep.alpha ? (float)*ep.alpha : 0.f;
   const int ldc4 = ldc >> 2;
   const Pol<H> pl = make_pol<H>();
-  for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < part.segments; w += warps) {
+  for (int64_t w = first_segment(seg_ctr, (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5, lane);
+       w < part.segments; w = next_segment(seg_ctr, w, warps, lane)) {
     const int64_t r0 = part.seg_row[w], k0 = part.seg_nnz[w];
     const int64_t r1 = part.seg_row[w + 1], k1 = part.seg_nnz[w + 1];
     const bool split_head = r0 < m && (int64_t)rowptr[r0] < k0;  // row r0 began in an earlier segment
@@ -578,7 +603,9 @@ __global__ void __launch_bounds__(kTmaWarps * 32, R <= 8 ? 4 : 2) spmm_tma_kerne
                                                                   Epilogue<TQ> ep, SpmmPart part,
                                                                   float* __restrict__ carry,
                                                                   int32_t* __restrict__ carry_row, int ldc,
-                                                                  int* __restrict__ err) {
+                                                                  int* __restrict__ err, int32_t* __restrict__ seg_ctr,
+                                                                  int reserve) {
+  if (on_reserved_sm(reserve)) return;
   extern __shared__ __align__(128) unsigned char tsm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t rowbytes = (uint32_t)nslot * 16;
@@ -595,7 +622,8 @@ __global__ void __launch_bounds__(kTmaWarps * 32, R <= 8 ? 4 : 2) spmm_tma_kerne
   uint32_t cnt = 0;                    // nonzeros consumed by this warp so far (ring position)
   uint32_t issued = 0;                 // bulk copies issued by this warp so far
   bool ok = true;
-  for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < part.segments && ok; w += warps) {
+  for (int64_t w = first_segment(seg_ctr, (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5, lane);
+       w < part.segments && ok; w = next_segment(seg_ctr, w, warps, lane)) {
     const int64_t r0 = part.seg_row[w], k0 = part.seg_nnz[w];
     const int64_t r1 = part.seg_row[w + 1], k1 = part.seg_nnz[w + 1];
     const bool split_head = r0 < m && (int64_t)rowptr[r0] < k0;
@@ -744,7 +772,8 @@ cudaError_t launch_tma(const dashsvd_csr& A, const SpmmPart& part, const float* 
   const int64_t need = ds_ceil_div(part.segments * 32, kTmaWarps * 32);
   const int64_t grid = (int64_t)num_sms * 4;
   spmm_tma_kernel<R, TOut, TQ, H><<<(unsigned)(need < grid ? need : grid), kTmaWarps * 32, smem, st>>>(
-      A.rowptr, A.colidx, A.val, A.m, X, ldx, Y, ldy, nslot, ep, part, scr.carry, scr.carry_row, scr.ldc, err);
+      A.rowptr, A.colidx, A.val, A.m, X, ldx, Y, ldy, nslot, ep, part, scr.carry, scr.carry_row, scr.ldc, err,
+      scr.seg_counter, scr.reserve_sms);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   spmm_fixup_kernel<TOut, TQ, H><<<(unsigned)ds_ceil_div(2 * part.segments * 32, kThreads), kThreads, 0, st>>>(
@@ -769,7 +798,8 @@ cudaError_t launch_vc(const dashsvd_csr& A, const SpmmPart& part, const TIn* X, 
   if (part.segments > scr.max_segments || scr.ldc < ((l + 3) / 4) * 4) return cudaErrorInvalidValue;
   const int64_t need = ds_ceil_div(part.segments * 32, kThreads);
   spmm_merge_kernel<V, U, MINB, TIn, TOut, TQ, H><<<(unsigned)(need < grid ? need : grid), kThreads, 0, st>>>(
-      A.rowptr, A.colidx, A.val, A.m, X, ldx, Y, ldy, nslot, ep, part, scr.carry, scr.carry_row, scr.ldc);
+      A.rowptr, A.colidx, A.val, A.m, X, ldx, Y, ldy, nslot, ep, part, scr.carry, scr.carry_row, scr.ldc,
+      scr.seg_counter, scr.reserve_sms);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   spmm_fixup_kernel<TOut, TQ, H><<<(unsigned)ds_ceil_div(2 * part.segments * 32, kThreads), kThreads, 0, st>>>(

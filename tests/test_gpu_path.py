@@ -391,8 +391,8 @@ def test_full_size_gaussian_block_sampled(ds):
             np.testing.assert_allclose(Y[:, :150], ref, rtol=1e-5, atol=2e-6)
 
 
+@pytest.mark.parametrize("use_graph", [0, 1])
 @pytest.mark.parametrize("form", [0, 1])
-@pytest.mark.parametrize("use_graph", [1, 0])
 def test_overlapped_schedule_matches_serial(ds, form, use_graph):
     """options.overlap computes A Q of each new basis as (A Z) W with A Z on a
     second stream beside the eigensolve; against the serial schedule (and the
