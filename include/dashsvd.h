@@ -140,12 +140,15 @@ typedef struct {
                               runs agree to rounding, not bit for bit. */
   int32_t profile;         /* 1: the run uses the host-driven loop and records the device time
                               of each group of launches (dashsvd_get_profile); 0: off */
-  int32_t overlap;         /* 1 (default): A Q of each new basis Q = Z W is computed as
-                              (A Z) W, with A Z on a second stream while the Gram and the
-                              l x l eigensolve (one SM) run, so the eigensolve no longer
-                              holds up the sparse product; the last pass's product is step
-                              9's B. Not with pve_mode = 1, gather_bf16 or the fused pass
-                              product (those keep the serial schedule). 0: serial. */
+  int32_t overlap;         /* 1: A Q of each new basis Q = Z W is computed as (A Z) W, with
+                              A Z on a second stream while the l x l eigensolve runs (the
+                              product leaves a few SMs to the eigensolve's kernels), so the
+                              eigensolve no longer holds up the sparse product; the last
+                              pass's product is step 9's B. Not with pve_mode = 1,
+                              gather_bf16 or the fused pass product (those keep the serial
+                              schedule). 0: serial. -1 (default): 1 in the precision form
+                              (tensor-core projections), 0 in the plain form (its FP32
+                              projection of A Z costs more than the eigensolve it hides). */
   int32_t reserved[1];
 } dashsvd_options;
 

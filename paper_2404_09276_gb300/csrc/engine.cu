@@ -756,7 +756,7 @@ int dashsvd_options_init(dashsvd_options* opt) {
   opt->record_trace = 0;
   opt->shift = 1;
   opt->pve_mode = 0;
-  opt->overlap = 1;
+  opt->overlap = -1;
   return DASHSVD_OK;
 }
 
@@ -1111,7 +1111,11 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
   }
   if (forced < 0 && !h->opt.deterministic && (rc = autotune_spmm(h, p, *A)) != DASHSVD_OK) return rc;
   if (direct_pve(h)) p.fused = false;  // B = A Q is stored every pass
-  p.overlap = h->opt.overlap && !direct_pve(h) && !bf16_gathers(h) && !p.fused;
+  // overlap -1 (default): on in the precision form, whose tensor-core
+  // projection makes the extra (A Z) W cheap; the plain form's FP32 projection
+  // costs more than the eigensolve it would hide
+  const bool want_overlap = h->opt.overlap > 0 || (h->opt.overlap < 0 && precision(h));
+  p.overlap = want_overlap && !direct_pve(h) && !bf16_gathers(h) && !p.fused;
   if (p.overlap && ((rc = ensure(h->Yp, sizeof(float) * (size_t)(p.mw * p.ld), &moved)) ||
                     (rc = ensure(h->seg_ctr, 16, &moved))))
     return rc;

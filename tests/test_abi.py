@@ -66,6 +66,7 @@ def test_options_defaults(ds):
     assert o.form == ds.DASHSVD_FORM_PLAIN and o.learned == 0
     assert o.seed == 0x5EED and o.alpha_prev_mode == 0
     assert o.use_graph == 1 and o.spmm_variant == -1 and o.shift == 1
+    assert o.overlap == -1 and o.trust_csr == 0 and o.deterministic == 0 and o.profile == 0
 
 
 def test_status_strings(ds):

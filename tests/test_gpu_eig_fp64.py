@@ -65,7 +65,7 @@ def _check(ds, h, G, iters=3, clusters=()):
 
 
 def _shifted_pass_grams():
-    A, _ = datagen.make_config(2, scale=0.02)  # 20 000 x 20 000 power-law graph
+    A, _ = datagen.make_config(2, scale=0.01)  # 10 000 x 10 000 power-law graph
     r = oracle.dashsvd(A.to_scipy(), 100, 50, p_max=3, tol=0.0, seed=0x5EED, keep_q=True)
     As = A.to_scipy().astype(np.float64)
     At = As.T.tocsr()

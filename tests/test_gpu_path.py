@@ -414,7 +414,7 @@ def test_overlapped_schedule_profile(ds):
     import torch
 
     A, prm = datagen.make_config(2, scale=0.01)
-    with ds.Handle(profile=1) as h:
+    with ds.Handle(profile=1, overlap=1) as h:
         U, S, V, info = h.run(ds.CsrDevice.from_host(A), 20, 10, 5, 0.0)
         torch.cuda.synchronize()
         prof = h.profile()
