@@ -243,16 +243,17 @@ int dashsvd_get_trace(dashsvd_handle h, double* out, int64_t cap, int64_t* count
 int dashsvd_get_tuning(dashsvd_handle h, float* ms, int64_t cap);
 
 /* Device time per step of the last run made with options.profile = 1 (HOST
- * buffer of at least 16 doubles): ms[c] = total milliseconds and ms[8 + c] =
+ * buffer of at least 20 doubles): ms[c] = total milliseconds and ms[10 + c] =
  * number of timed launch groups of category c, where c is 0 the Gaussian block
  * (Alg. 5 step 1), 1 the products A Q (steps 4 and 9; with the overlapped
  * schedule, the part of A Z the eigensolve did not hide), 2 the products
- * A^T Y - alpha Q (and A^T Omega of step 2), 3 the Gram matrices, 4 the l x l
- * eigensolves with their control tail (Jacobi, eigenvector replay, FP64
- * refinement, conventions, steps 5-7), 5 the projections C W (steps 2, 4, 11),
- * 6 the host's waits between passes of the host-driven loop, 7 the overlapped
- * products A Z, start to end on their own stream (they run during categories
- * 3 and 4, so they are not part of the sum of 0..6). The time of the setup
+ * A^T Y - alpha Q (and A^T Omega of step 2), 3 the Gram matrices, 4 the end of
+ * each l x l eigensolve (eigSVD's conventions and the control tail, steps
+ * 5-7), 5 the projections C W (steps 2, 4, 11), 6 the host's waits between
+ * passes of the host-driven loop, 7 the overlapped products A Z, start to end
+ * on their own stream (they run during categories 4, 8 and 9, so they are not
+ * part of the sum of the others), 8 the Jacobi sweeps with the eigenvector
+ * replay, 9 the FP64 refinement (precision form). The time of the setup
  * fingerprint is not included. */
 int dashsvd_get_profile(dashsvd_handle h, double* ms, int64_t cap);
 

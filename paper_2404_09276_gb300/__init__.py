@@ -162,7 +162,7 @@ dashsvd_eig_fp64 = _export("dashsvd_eig_fp64")
 dashsvd_get_profile = _export("dashsvd_get_profile")
 dashsvd_run_host = _export("dashsvd_run_host")
 PROFILE_CATEGORIES = ("gaussian", "spmm_fwd", "spmm_bwd", "gram", "eig", "project", "host_gap",
-                      "spmm_fwd_overlapped")
+                      "spmm_fwd_overlapped", "eig_jacobi", "eig_refine")
 DASHSVD_CSR_BAD_FIRST, DASHSVD_CSR_BAD_ORDER, DASHSVD_CSR_BAD_LAST, DASHSVD_CSR_BAD_COL = 1, 2, 4, 8
 dashsvd_mlp_forward = _export("dashsvd_mlp_forward")
 dashsvd_mlp_loss_grad = _export("dashsvd_mlp_loss_grad")

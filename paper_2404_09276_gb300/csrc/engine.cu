@@ -72,7 +72,9 @@ constexpr int kSpmmVariantsAll = 10;  // SpMM variant codes 0..9 (+ 16: with L2 
 constexpr int kSpmmFusedCode = 10;    // options.spmm_variant value of the fused pass product
 
 // categories of dashsvd_get_profile (the order of include/dashsvd.h)
-enum ProfCat : int { kPfGauss = 0, kPfFwd, kPfBwd, kPfGram, kPfEig, kPfProject, kPfGap, kPfFwdConc, kProfCats };
+enum ProfCat : int {
+  kPfGauss = 0, kPfFwd, kPfBwd, kPfGram, kPfEig, kPfProject, kPfGap, kPfFwdConc, kPfJacobi, kPfRefine, kProfCats
+};
 
 struct GraphKey {
   dashsvd_csr A;
@@ -288,6 +290,26 @@ constexpr double kEpsBf16x3 = 1.52587890625e-05;  // 2^-16
 
 cudaError_t fork_az(dashsvd_handle h, const RunPlan& p, cudaStream_t st);
 
+// Profiling marks between the stages of an eigensolve (Jacobi + replay, FP64
+// refinement; the finish kernel goes to kPfEig).
+struct EigMarkCtx {
+  dashsvd_handle h;
+  cudaStream_t st;
+};
+thread_local EigMarkCtx g_eig_mark_ctx;
+cudaError_t eig_mark_fn(void* ctx, int stage) {
+  const EigMarkCtx* c = static_cast<const EigMarkCtx*>(ctx);
+  return tmark(c->h, stage == 0 ? kPfJacobi : kPfRefine, c->st);
+}
+EigMarks eig_marks(dashsvd_handle h, cudaStream_t st) {
+  EigMarks m;
+  if (!h->prof_on) return m;
+  g_eig_mark_ctx = {h, st};
+  m.fn = eig_mark_fn;
+  m.ctx = &g_eig_mark_ctx;
+  return m;
+}
+
 // eigSVD of C (rows x l): Gram, eigensolve with the control tail (the
 // projection C W follows separately). With `fork`, the overlapped product A Z
 // is forked once the Gram is written, so it runs beside the eigensolve only.
@@ -301,7 +323,8 @@ cudaError_t eigsvd_step(dashsvd_handle h, const RunPlan& p, const float* C, int6
       return e;
     if (fork && (e = fork_az(h, p, st)) != cudaSuccess) return e;
     if ((e = launch_eig_refined(as<float>(h->G), p.ld, as<double>(h->G64), p.ld, kEpsBf16x3, kRefineIters,
-                                eig_args(h, p, mode, cond), eig_work_view(h->eigw.p), st)) != cudaSuccess)
+                                eig_args(h, p, mode, cond), eig_work_view(h->eigw.p), st, eig_marks(h, st))) !=
+        cudaSuccess)
       return e;
     return tmark(h, kPfEig, st);
   }
@@ -310,8 +333,8 @@ cudaError_t eigsvd_step(dashsvd_handle h, const RunPlan& p, const float* C, int6
       (e = tmark(h, kPfGram, st)) != cudaSuccess)
     return e;
   if (fork && (e = fork_az(h, p, st)) != cudaSuccess) return e;
-  if ((e = launch_eig_f32(as<float>(h->G), p.ld, eig_args(h, p, mode, cond), eig_work_view(h->eigw.p), st)) !=
-      cudaSuccess)
+  if ((e = launch_eig_f32(as<float>(h->G), p.ld, eig_args(h, p, mode, cond), eig_work_view(h->eigw.p), st,
+                          eig_marks(h, st))) != cudaSuccess)
     return e;
   return tmark(h, kPfEig, st);
 }

@@ -187,9 +187,18 @@ constexpr int kRefineParts = 256;  // (256 / 16)^2 tiles of an l x l product at 
 int eig_max_l_f32();
 size_t eig_work_bytes();
 EigWork eig_work_view(void* base);
-cudaError_t launch_eig_f32(const float* G, int64_t ldg, const EigArgs& a, const EigWork& wk, cudaStream_t st);
+// Optional hook between the stages of an eigensolve (stage 0: after the
+// Jacobi sweeps and the eigenvector replay; 1: after the FP64 refinement),
+// used to time them.
+struct EigMarks {
+  cudaError_t (*fn)(void* ctx, int stage) = nullptr;
+  void* ctx = nullptr;
+};
+cudaError_t launch_eig_f32(const float* G, int64_t ldg, const EigArgs& a, const EigWork& wk, cudaStream_t st,
+                           const EigMarks& mk = EigMarks());
 cudaError_t launch_eig_refined(const float* G32, int64_t ldg32, const double* G64, int64_t ldg64, double eps_null,
-                               int iters, const EigArgs& a, const EigWork& wk, cudaStream_t st);
+                               int iters, const EigArgs& a, const EigWork& wk, cudaStream_t st,
+                               const EigMarks& mk = EigMarks());
 // The precision form's eigensolver alone: FP64 eigenpairs of an FP64 Gram
 // (descending, signed), after `iters` refinement steps (0: FP32 Jacobi only).
 cudaError_t launch_eig_fp64(const double* G, int64_t ldg, int l, int iters, float* G32, int64_t ld32, double* D,

@@ -615,7 +615,8 @@ cudaError_t prepare_eig() {
                               (int)jacobi_smem(kMaxL));
 }
 
-cudaError_t launch_eig_f32(const float* G, int64_t ldg, const EigArgs& a, const EigWork& wk, cudaStream_t st) {
+cudaError_t launch_eig_f32(const float* G, int64_t ldg, const EigArgs& a, const EigWork& wk, cudaStream_t st,
+                           const EigMarks& mk) {
   if (a.l < 1 || a.l > kMaxL) return cudaErrorInvalidValue;
   jacobi_f32_kernel<<<1, kJacThreads, jacobi_smem(a.l), st>>>(G, ldg, a.l, wk, kEps32);
   cudaError_t e = cudaGetLastError();
@@ -623,6 +624,7 @@ cudaError_t launch_eig_f32(const float* G, int64_t ldg, const EigArgs& a, const 
   eigvec_replay_kernel<<<(unsigned)ds_ceil_div(a.l, kReplayWarps), kReplayWarps * 32, 0, st>>>(wk, a.l);
   const unsigned blocks = (unsigned)ds_ceil_div(a.l, kVecWarps);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (mk.fn && (e = mk.fn(mk.ctx, 0)) != cudaSuccess) return e;
   finish_kernel<float><<<blocks, kVecWarps * 32, 0, st>>>(wk.d, wk.V32, wk.d0, (double)kEps32, wk.hdr, a);
   return cudaGetLastError();
 }
@@ -630,7 +632,7 @@ cudaError_t launch_eig_f32(const float* G, int64_t ldg, const EigArgs& a, const 
 // FP32 Jacobi on G32 for a starting basis, FP64 refinement against G64, then
 // the conventions and control on the refined FP64 eigenpairs.
 cudaError_t launch_eig_refined(const float* G32, int64_t ldg32, const double* G64, int64_t ldg64, double eps_null,
-                               int iters, const EigArgs& a, const EigWork& wk, cudaStream_t st) {
+                               int iters, const EigArgs& a, const EigWork& wk, cudaStream_t st, const EigMarks& mk) {
   if (a.l < 1 || a.l > kMaxL) return cudaErrorInvalidValue;
   // the Jacobi sweeps run to FP32 rounding, as in the plain form: the
   // refinement's first-order corrections are only taken for pairs whose
@@ -644,8 +646,10 @@ cudaError_t launch_eig_refined(const float* G32, int64_t ldg32, const double* G6
   eigvec_replay_kernel<<<(unsigned)ds_ceil_div(a.l, kReplayWarps), kReplayWarps * 32, 0, st>>>(wk, a.l);
   const unsigned blocks = (unsigned)ds_ceil_div(a.l, kVecWarps);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (mk.fn && (e = mk.fn(mk.ctx, 0)) != cudaSuccess) return e;
   const double* X = nullptr;
   if ((e = launch_refine_fp64(G64, ldg64, wk.V32, a.l, iters, wk, &X, st)) != cudaSuccess) return e;
+  if (mk.fn && (e = mk.fn(mk.ctx, 1)) != cudaSuccess) return e;
   finish_kernel<double><<<blocks, kVecWarps * 32, 0, st>>>(wk.lam64, X, wk.d0_64, eps_null, wk.hdr, a);
   return cudaGetLastError();
 }

@@ -422,3 +422,21 @@ def test_overlapped_schedule_profile(ds):
     assert prof["spmm_bwd"][1] == info.passes + 1
     assert prof["eig"][1] == info.passes + 2
     assert all(ms >= 0.0 for ms, _ in prof.values())
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_eigensolve_stage_profile(ds, form):
+    """The eigensolve's time splits into the Jacobi sweeps (with the
+    eigenvector replay), the FP64 refinement (precision form only) and the
+    finish: one timed group of each per eigensolve."""
+    import torch
+
+    A, prm = datagen.make_config(2, scale=0.01)
+    with ds.Handle(profile=1, form=form, overlap=0) as h:
+        U, S, V, info = h.run(ds.CsrDevice.from_host(A), 20, 10, 5, 0.0)
+        torch.cuda.synchronize()
+        prof = h.profile()
+    n = info.passes + 2
+    assert prof["eig"][1] == n and prof["eig_jacobi"][1] == n
+    assert prof["eig_refine"][1] == (n if form == 1 else 0)
+    assert prof["eig_jacobi"][0] > 0.0 and (form == 0 or prof["eig_refine"][0] > 0.0)
