@@ -708,7 +708,8 @@ def ours(args):
         "passes": chosen["passes"], "status": chosen["status"], "pve_surrogate": chosen["pve_surrogate"],
         "accuracy": chosen["accuracy"], "setup": chosen["setup"],
         "trace": chosen["trace"], "roofline": _roofline(chosen, A, l, pk), "kernels_s": chosen["kernels_s"],
-        "kernel_s_per_run": chosen["kernel_s_per_run"], "spmm": chosen["spmm"], "e2e": chosen["e2e"],
+        "kernel_s_per_run": chosen["kernel_s_per_run"], "profiled_run": chosen["profiled_run"],
+        "in_loop_s_per_launch": chosen["in_loop_s_per_launch"], "spmm": chosen["spmm"], "e2e": chosen["e2e"],
         "gpu_launches": chosen["gpu_launches"], "clocks": chosen["clocks"],
     }
     # the chosen form once more with the serial schedule (options.overlap = 0):
