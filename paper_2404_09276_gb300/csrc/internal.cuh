@@ -172,7 +172,7 @@ cudaError_t launch_project_tc(const float* C, int64_t rows, int l, int64_t ldc, 
 // conventions and the loop control. Work buffer: header, eigenvalues, log.
 constexpr int kMaxSweeps = 30;
 struct EigWork {
-  int* hdr;       // [0] sweeps to replay, [1] status bits, [2] sweeps run
+  int* hdr;       // [0] steps to replay, [1] status bits, [2] sweeps run
   double* scal;   // FP64 scalars of the refinement (header bytes 128..255)
   float* d;       // kMaxL eigenvalues (unsorted, FP32 Jacobi)
   float* d0;      // kMaxL diagonal entries of G before the iteration
@@ -181,7 +181,8 @@ struct EigWork {
   double* lam64;  // kMaxL refined eigenvalues
   double* d0_64;  // kMaxL diagonal of the FP64 Gram
   double* part64; // 3 x kRefineParts partial sums of the refinement's residual norms
-  float2* log;    // (c, s) per sweep x step x pair
+  float2* log;    // (c, s) per logged step x slot (hdr[0] steps)
+  ushort2* plog;  // the pair (p, q) of each logged rotation
 };
 constexpr int kRefineParts = 256;  // (256 / 16)^2 tiles of an l x l product at l = 256
 int eig_max_l_f32();

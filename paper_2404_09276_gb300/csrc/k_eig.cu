@@ -3,18 +3,21 @@
 //
 // Kernel 1 (one CTA, 1024 threads): cyclic two-sided Jacobi in parallel
 // (round-robin) order on the upper triangle of G, packed in shared memory.
-// With N = l rounded up to even (index l is a zero dummy when l is odd), step
-// t of a sweep pairs index N-1 with t, and (t + i) mod (N-1) with
-// (t - i) mod (N-1) for i = 1 .. N/2 - 1: every pair meets once per sweep and
-// the N/2 rotations of a step act on disjoint rows and columns. A rotation is
-// the symmetric Schur 2x2 rotation (Golub and Van Loan, Sec. 8.5):
+// A sweep works on the n indices that still have a pair above the skip
+// threshold (listed at its start, padded to an even count), numbered 0..n-1:
+// step t pairs n-1 with t, and (t + i) mod (n-1) with (t - i) mod (n-1) for
+// i = 1 .. n/2 - 1, so every pair of them meets once per sweep and the n/2
+// rotations of a step act on disjoint rows and columns (with N = l rounded up
+// to even, index l is a zero dummy when l is odd, used as the padding). A
+// rotation is the symmetric Schur 2x2 rotation (Golub and Van Loan, Sec. 8.5):
 // tau = (G_qq - G_pp) / (2 G_pq), t = sign(tau) / (|tau| + sqrt(1 + tau^2)),
 // c = 1 / sqrt(1 + t^2), s = t c; it is skipped when |G_pq| <= eps sqrt(G_pp G_qq)
 // (the relative criterion of Demmel and Veselic, which keeps small eigenvalues
 // of a positive semidefinite G accurate). The iteration ends when no pair is
-// above that threshold, which is checked before each sweep. Each step updates
-// the 2x2 blocks (I, J), I <= J, of G as J_I^T B J_J and appends its (c, s)
-// to a rotation log.
+// above that threshold, which is checked for every pair before each sweep
+// (pairs a sweep lifted above it bring their indices back into the next
+// sweep). Each step updates the 2x2 blocks (I, J), I <= J, of G as
+// J_I^T B J_J and appends its (c, s) and pairs (p, q) to a rotation log.
 //
 // Kernel 2 (one warp per eigenvector): V = J_1 J_2 ... J_T, so column c of V
 // is J_1 (J_2 (... (J_T e_c))): each warp replays the log backwards on e_c.
@@ -34,6 +37,8 @@ namespace {
 
 constexpr int kJacThreads = 1024;
 constexpr int kMaxN = kMaxL;  // N <= 256
+// log capacity: kMaxSweeps sweeps of at most N - 1 steps of N / 2 rotations
+constexpr size_t kLogEntries = (size_t)kMaxSweeps * (kMaxN - 1) * (kMaxN / 2);
 constexpr float kEps32 = 1.1920929e-07f;
 
 
@@ -64,7 +69,10 @@ struct __align__(16) PairRec {
 
 struct JacSmem {
   PairRec r[kMaxN / 2];
-  float d[kMaxN];  // diagonal of the iterate (eigenvalue estimates)
+  float d[kMaxN];      // diagonal of the iterate (eigenvalue estimates)
+  int act[kMaxN];      // sweep start: 1 if the index has a pair above the skip threshold
+  int list[kMaxN];     // the indices the sweep works on (active ones, padded to an even count)
+  int nlist;
   float gmax;
 };
 
@@ -114,54 +122,96 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_f32_kernel(const float* __
   __syncthreads();
   const float tiny = js.gmax * 1e-30f + 1e-35f;
   float2* log = wk.log;
-  int sweep = 0;
+  ushort2* plog = wk.plog;
+  int sweep = 0, t = 0;  // t: steps logged so far
   bool converged = false;
   for (; sweep <= kMaxSweeps; ++sweep) {
-    // convergence: no off-diagonal pair above the skip threshold
+    // convergence, and the indices that still have a pair above the skip
+    // threshold: the sweep runs the round robin over those only (the others'
+    // pairs are all below it); the test at the next sweep's start covers
+    // every pair again, so pairs that a sweep lifted above the threshold are
+    // taken up then
+    for (int a = tid; a < N; a += nt) js.act[a] = 0;
+    __syncthreads();
     int found = 0;
-    for (int idx = tid; idx < N * N && !found; idx += nt) {
+    for (int idx = tid; idx < N * N; idx += nt) {
       const int a = idx / N, b = idx - a * N;
       if (b <= a || b >= l) continue;
       const float g = fabsf(G[pk_off(a, N) + b]);
-      found = g > rel_tol * sqrtf(fabsf(d[a]) * fabsf(d[b])) && g > tiny;
+      if (g > rel_tol * sqrtf(fabsf(d[a]) * fabsf(d[b])) && g > tiny) {
+        found = 1;
+        js.act[a] = 1;
+        js.act[b] = 1;
+      }
     }
     if (!__syncthreads_or(found)) {
       converged = true;
       break;
     }
     if (sweep == kMaxSweeps) break;
-    for (int step = 0; step < M; ++step) {
+    if (tid < 32) {  // the active list in index order, padded to an even count
+      int n = 0, pad = -1;
+      for (int a0 = 0; a0 < N; a0 += 32) {
+        const int a = a0 + tid;
+        const bool on = a < N && js.act[a];
+        const unsigned m = __ballot_sync(0xffffffffu, on);
+        if (on) js.list[n + __popc(m & ((1u << tid) - 1u))] = a;
+        n += __popc(m);
+        // a padding index: l (the zero row) when l is odd, else the first index left out
+        const unsigned off = __ballot_sync(0xffffffffu, a < N && !on);
+        if (pad < 0 && off) pad = a0 + __ffs(off) - 1;
+      }
+      if (tid == 0) {
+        if (n & 1) js.list[n++] = (l & 1) ? l : pad;
+        js.nlist = n;
+      }
+    }
+    __syncthreads();
+    const int Ns = js.nlist, Ps = Ns / 2, Ms = Ns - 1, nblk_s = Ps * (Ps + 1) / 2;
+    for (int I = 0; I < Ps; ++I) {  // block table of this sweep, row-major over I <= J
+      const int base = I * Ps - ((I * (I - 1)) >> 1);
+      for (int J = I + tid; J < Ps; J += nt) blk[base + (J - I)] = I | (J << 16);
+    }
+    __syncthreads();
+    for (int step = 0; step < Ms; ++step, ++t) {
       if (tid < P) {
-        int p, q;
-        rr_pair_fast(tid, step, M, p, q);
-        const int op = pk_off(p, N), oq = pk_off(q, N);
         float c = 1.f, sn = 0.f;
-        if (p < l && q < l) {
-          const float app = d[p], aqq = d[q], apq = G[p < q ? op + q : oq + p];
-          const float thr = rel_tol * sqrtf(fabsf(app) * fabsf(aqq));
-          if (fabsf(apq) > thr && fabsf(apq) > tiny) {
-            // correctly rounded sqrt and division keep c^2 + s^2 = 1 to an ulp,
-            // so that rotations do not rescale G and V over many sweeps
-            const float tau = __fdiv_rn(aqq - app, 2.f * apq);
-            const float t = __fdiv_rn(tau >= 0.f ? 1.f : -1.f, fabsf(tau) + __fsqrt_rn(fmaf(tau, tau, 1.f)));
-            const float r = __fsqrt_rn(fmaf(t, t, 1.f));
-            c = __fdiv_rn(1.f, r);
-            sn = __fdiv_rn(t, r);
-            d[p] = app - t * apq;
-            d[q] = aqq + t * apq;
+        int p = 0, q = 0;
+        if (tid < Ps) {
+          int ip, iq;
+          rr_pair_fast(tid, step, Ms, ip, iq);
+          p = js.list[ip];
+          q = js.list[iq];
+          const int op = pk_off(p, N), oq = pk_off(q, N);
+          if (p < l && q < l) {
+            const float app = d[p], aqq = d[q], apq = G[p < q ? op + q : oq + p];
+            const float thr = rel_tol * sqrtf(fabsf(app) * fabsf(aqq));
+            if (fabsf(apq) > thr && fabsf(apq) > tiny) {
+              // correctly rounded sqrt and division keep c^2 + s^2 = 1 to an ulp,
+              // so that rotations do not rescale G and V over many sweeps
+              const float tau = __fdiv_rn(aqq - app, 2.f * apq);
+              const float tt = __fdiv_rn(tau >= 0.f ? 1.f : -1.f, fabsf(tau) + __fsqrt_rn(fmaf(tau, tau, 1.f)));
+              const float r = __fsqrt_rn(fmaf(tt, tt, 1.f));
+              c = __fdiv_rn(1.f, r);
+              sn = __fdiv_rn(tt, r);
+              d[p] = app - tt * apq;
+              d[q] = aqq + tt * apq;
+            }
           }
+          PairRec rec;
+          rec.c = c;
+          rec.s = sn;
+          rec.pq = p | (q << 16);
+          rec.off = op | (oq << 16);
+          js.r[tid] = rec;
         }
-        PairRec rec;
-        rec.c = c;
-        rec.s = sn;
-        rec.pq = p | (q << 16);
-        rec.off = op | (oq << 16);
-        js.r[tid] = rec;
-        log[((int64_t)sweep * M + step) * P + tid] = make_float2(c, sn);
+        // every slot of the step is logged (slots past this sweep's pairs as identities)
+        log[(int64_t)t * P + tid] = make_float2(c, sn);
+        plog[(int64_t)t * P + tid] = make_ushort2((unsigned short)p, (unsigned short)q);
       }
       __syncthreads();
       // G <- J^T G J on the 2x2 blocks (I, J), I <= J
-      for (int b = tid; b < nblk; b += nt) {
+      for (int b = tid; b < nblk_s; b += nt) {
         const int ij = blk[b];
         const int I = ij & 0xffff, J = ij >> 16;
         const PairRec ri = js.r[I], rj = js.r[J];
@@ -187,7 +237,7 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_f32_kernel(const float* __
   }
   for (int i = tid; i < l; i += nt) wk.d[i] = d[i];
   if (tid == 0) {
-    wk.hdr[0] = sweep;  // sweeps whose rotations the replay applies
+    wk.hdr[0] = t;  // steps whose rotations the replay applies
     wk.hdr[1] = converged ? 0 : kStatusNoConv;
     wk.hdr[2] = sweep;
   }
@@ -197,23 +247,25 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_f32_kernel(const float* __
 
 constexpr int kVecWarps = 8;     // finish kernel: one warp per eigenvector
 constexpr int kReplayWarps = 2;  // replay: few columns per CTA, so that about l / 2 SMs take part
-constexpr int kBatch = 16;       // log steps staged per batch
+constexpr int kBatch = 12;       // log steps staged per batch (both staging buffers within 48 KB of static shared memory)
 
 struct ReplaySmem {
   float x[kReplayWarps][kMaxN];
   float2 logb[2][kBatch * (kMaxN / 2)];
+  ushort2 pairb[2][kBatch * (kMaxN / 2)];
 };
 
 // Column c of V = J_1 (J_2 (... (J_T e_c))): each warp replays the log
 // backwards on e_c, in batches of kBatch steps staged in shared memory by the
-// whole CTA. Writes V row-major (V[j * l + c]).
+// whole CTA; each logged rotation carries its pair (p, q). Writes V row-major
+// (V[j * l + c]).
 __global__ void __launch_bounds__(kReplayWarps * 32) eigvec_replay_kernel(EigWork wk, int l) {
   __shared__ ReplaySmem rs;
   const int N = l + (l & 1);
   const int P = N / 2;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5;
-  const int nsteps = wk.hdr[0] * (N - 1);
+  const int nsteps = wk.hdr[0];
   const int c = blockIdx.x * kReplayWarps + warp;
   float* x = rs.x[warp];
   for (int j = lane; j < N; j += 32) x[j] = j == c ? 1.f : 0.f;
@@ -226,12 +278,18 @@ __global__ void __launch_bounds__(kReplayWarps * 32) eigvec_replay_kernel(EigWor
       const int t1 = nsteps - b * kBatch;
       const int t0 = t1 - kBatch > 0 ? t1 - kBatch : 0;
       const float2* src = wk.log + (int64_t)t0 * P;
+      const ushort2* psrc = wk.plog + (int64_t)t0 * P;
       float2* dst = rs.logb[buf];
+      ushort2* pdst = rs.pairb[buf];
       const int n = (t1 - t0) * P;
-      for (int i = tid; i < n; i += nt)
+      for (int i = tid; i < n; i += nt) {
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst + i)),
                      "l"(src + i)
                      : "memory");
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((uint32_t)__cvta_generic_to_shared(pdst + i)),
+                     "l"(psrc + i)
+                     : "memory");
+      }
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   };
@@ -243,10 +301,11 @@ __global__ void __launch_bounds__(kReplayWarps * 32) eigvec_replay_kernel(EigWor
     const int t1 = nsteps - b * kBatch;
     const int t0 = t1 - kBatch > 0 ? t1 - kBatch : 0;
     const float2* lg = rs.logb[b & 1];
+    const ushort2* pg = rs.pairb[b & 1];
     if (c < l) {
       for (int t = t1 - 1; t >= t0; --t) {
-        const int step = t % (N - 1);
         const float2* lgt = lg + (t - t0) * P;
+        const ushort2* pgt = pg + (t - t0) * P;
         // the pairs of a step are disjoint: load all of this lane's pairs
         // (up to 4) before any store, so their latencies overlap
         float2 cs[4];
@@ -256,7 +315,9 @@ __global__ void __launch_bounds__(kReplayWarps * 32) eigvec_replay_kernel(EigWor
         for (int u = 0; u < 4; ++u) {
           const int i = lane + 32 * u;
           cs[u] = i < P ? lgt[i] : make_float2(1.f, 0.f);
-          rr_pair_fast(i < P ? i : 0, step, N - 1, pp[u], qq[u]);
+          const ushort2 pq = i < P ? pgt[i] : make_ushort2(0, 0);
+          pp[u] = pq.x;
+          qq[u] = pq.y;
           xp[u] = x[pp[u]];
           xq[u] = x[qq[u]];
         }
@@ -582,7 +643,7 @@ int eig_max_l_f32() { return kMaxL; }
 size_t eig_work_bytes() {
   const size_t L = kMaxL;
   return 256 + 2 * sizeof(float) * L + sizeof(float) * L * L + 6 * sizeof(double) * L * L + 2 * sizeof(double) * L +
-         3 * sizeof(double) * kRefineParts + sizeof(float2) * (size_t)kMaxSweeps * (kMaxN - 1) * (kMaxN / 2);
+         3 * sizeof(double) * kRefineParts + (sizeof(float2) + sizeof(ushort2)) * kLogEntries;
 }
 
 EigWork eig_work_view(void* base) {
@@ -607,6 +668,8 @@ EigWork eig_work_view(void* base) {
   w.V32 = reinterpret_cast<float*>(p);
   p += sizeof(float) * L * L;
   w.log = reinterpret_cast<float2*>(p);
+  p += sizeof(float2) * kLogEntries;
+  w.plog = reinterpret_cast<ushort2*>(p);
   return w;
 }
 
