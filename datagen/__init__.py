@@ -112,27 +112,58 @@ class _ZipfSampler:
         return r
 
 
-def _distinct_targets(deg: np.ndarray, n: int, draw, rng, zipf_rounds: int = 12) -> np.ndarray:
+def _distinct_targets(deg: np.ndarray, n: int, draw, rng, zipf_rounds: int = 12,
+                      fill_exact: bool = False) -> np.ndarray:
     """Give row i exactly min(deg[i], n) distinct targets.
 
     Targets are drawn with ``draw(count, rng)``. Rows that lost draws to
     duplicates are topped up for ``zipf_rounds`` rounds; any deficit left after
     that (only very long rows, which have used up the popular targets) is
-    filled with uniformly drawn targets. Returns sorted keys row*n + col.
+    filled with uniformly drawn targets: by further rounds of draws with
+    replacement, or, with ``fill_exact``, in one step, each short row taking
+    its deficit as a uniform draw without replacement from the columns it
+    lacks (rows that need almost every column would otherwise take a round per
+    missing column, as in coupon collecting). Returns sorted keys row*n + col.
+
+    Rows that are complete are set aside after each round, so that the
+    top-up rounds (many, for rows that need almost every column) only sort
+    the keys of the rows still short; the draws and the result are the same
+    as when every round works on all keys.
     """
     m = deg.size
     deg = np.minimum(deg, n).astype(np.int64)
-    keys = np.empty(0, dtype=np.int64)
+    done = []  # sorted keys of complete rows
+    keys = np.empty(0, dtype=np.int64)  # sorted keys of the rows still short
     need = deg
     rnd = 0
     while True:
         rows = np.repeat(np.arange(m, dtype=np.int64), need)
         if rows.size == 0:
             break
+        if fill_exact and rnd == zipf_rounds:
+            fill = []
+            for r in np.nonzero(need)[0]:
+                lo, hi = np.searchsorted(keys, [r * n, (r + 1) * n])
+                lack = np.setdiff1d(np.arange(n, dtype=np.int64), keys[lo:hi] - r * n, assume_unique=True)
+                fill.append(r * n + np.sort(rng.choice(lack, int(need[r]), replace=False)))
+            done.append(keys)
+            done.extend(fill)
+            keys = np.empty(0, dtype=np.int64)
+            break
         cols = draw(rows.size, rng) if rnd < zipf_rounds else rng.integers(0, n, rows.size)
         keys = _dedup_sorted(np.concatenate([keys, _dedup_sorted(rows * n + cols)]))
-        need = np.maximum(deg - np.bincount(keys // n, minlength=m), 0)
+        have = np.bincount(keys // n, minlength=m)
+        short = np.zeros(m, dtype=bool)
+        short[np.nonzero(need)[0]] = True  # only rows drawn this round can be short or newly complete
+        need = np.where(short, np.maximum(deg - have, 0), 0)
+        complete = (keys // n)
+        sel = short[complete] & (need[complete] == 0)
+        if sel.any():
+            done.append(keys[sel])
+            keys = keys[~sel]
         rnd += 1
+    if done:
+        keys = _dedup_sorted(np.concatenate(done + [keys]))
     return keys
 
 
@@ -203,14 +234,17 @@ def term_document(
 def recommender(
     m: int, n: int, seed: int, mean_degree: float = 50.0, degree_tail: float = 1.2,
     popularity: float = 1.2, name: str = "recommender", max_degree: int | None = None,
+    fill_exact: bool = False,
 ) -> Csr:
     """User-item ratings: power-law user degrees (capped at ``max_degree``, default
-    n), distinct Zipf items through a permutation, ratings uniform in {1, ..., 5}."""
+    n), distinct Zipf items through a permutation, ratings uniform in {1, ..., 5}.
+    ``fill_exact``: see _distinct_targets (the benchmark workload, whose
+    longest rows need almost every column, uses it)."""
     rng = np.random.default_rng(seed)
     deg = _powerlaw_degrees(m, degree_tail, mean_degree, n if max_degree is None else min(max_degree, n), rng)
     perm = rng.permutation(n)
     zipf = _ZipfSampler(n, popularity)
-    keys = _distinct_targets(deg, n, lambda k, g: perm[zipf(k, g)], rng)
+    keys = _distinct_targets(deg, n, lambda k, g: perm[zipf(k, g)], rng, fill_exact=fill_exact)
     return _csr_from_keys(
         m, n, keys, lambda r, c, g: g.integers(1, 6, r.size).astype(np.float64), rng, name
     )
@@ -296,5 +330,5 @@ def make_config(cfg: int, scale: float = 1.0) -> tuple[Csr, dict]:
     elif kind == "term_document":
         A = term_document(m, n, seed, name=tag)
     else:
-        A = recommender(m, n, seed, name=tag)
+        A = recommender(m, n, seed, name=tag, fill_exact=True)
     return A, c
