@@ -58,3 +58,50 @@ def test_powerlaw_degree_bisection():
     rng = np.random.default_rng(1)
     d = datagen._powerlaw_degrees(100_000, 1.2, 50.0, 10_000, rng)
     assert abs(d.mean() - 50.0) < 0.5 and d.max() <= 10_000 and d.min() >= 1
+
+
+def _distinct_targets_every_round(deg, n, draw, rng, zipf_rounds=12):
+    """The redraw loop in its plain form: every round re-sorts all keys."""
+    m = deg.size
+    deg = np.minimum(deg, n).astype(np.int64)
+    keys = np.empty(0, dtype=np.int64)
+    need = deg
+    rnd = 0
+    while True:
+        rows = np.repeat(np.arange(m, dtype=np.int64), need)
+        if rows.size == 0:
+            break
+        cols = draw(rows.size, rng) if rnd < zipf_rounds else rng.integers(0, n, rows.size)
+        keys = np.unique(np.concatenate([keys, rows * n + cols]))
+        need = np.maximum(deg - np.bincount(keys // n, minlength=m), 0)
+        rnd += 1
+    return keys
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_redraw_rounds_set_complete_rows_aside(seed):
+    """The generator's redraw rounds set complete rows aside: the same draws
+    and the same keys as the plain loop, including rows that need every
+    column (uniform rounds after the Zipf ones)."""
+    m, n = 300, 40
+    rng0 = np.random.default_rng(seed)
+    deg = np.minimum(rng0.integers(0, 60, m), n)
+    deg[:5] = n
+    zipf = datagen._ZipfSampler(n, 1.2)
+    a = datagen._distinct_targets(deg, n, lambda k, g: zipf(k, g), np.random.default_rng(seed + 10))
+    b = _distinct_targets_every_round(deg, n, lambda k, g: zipf(k, g), np.random.default_rng(seed + 10))
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(np.bincount(a // n, minlength=m), np.minimum(deg, n))
+
+
+def test_exact_fill_gives_every_row_its_degree():
+    """fill_exact: rows still short after the Zipf rounds take their deficit
+    without replacement from the columns they lack (distinct, in range)."""
+    m, n = 200, 50
+    deg = np.full(m, 10)
+    deg[:20] = n
+    zipf = datagen._ZipfSampler(n, 1.4)
+    keys = datagen._distinct_targets(deg, n, lambda k, g: zipf(k, g), np.random.default_rng(5), fill_exact=True)
+    assert np.all(np.diff(keys) > 0)
+    np.testing.assert_array_equal(np.bincount(keys // n, minlength=m), deg)
+    assert keys.min() >= 0 and keys.max() < m * n
