@@ -323,12 +323,12 @@ def _launches_per_run(form, passes, var_fwd, var_bwd, setup_reused=True, fused=F
     if overlap:  # A Z beside each eigensolve, then Q = Z W and Y = (A Z) W
         prologue = 1 + kpv(var_bwd) + kpv(var_fwd) + 2 + eig + 2
         per_pass = kpv(var_bwd) + kpv(var_fwd) + 2 + eig + 2
-        final = 2 + eig + 2
+        final = 2 + eig + 2 + (0 if form == "plain" else 4)  # precision: U's column norms (4 kernels)
     else:
         prologue = 1 + kpv(var_bwd) + 2 + eig + 1
         # a pass: both products (or the fused one: -alpha Q, then the scatter), Gram + reduce, eig, projection
         per_pass = (2 if fused else kpv(var_fwd) + kpv(var_bwd)) + 2 + eig + 1
-        final = kpv(var_fwd) + 2 + eig + 2
+        final = kpv(var_fwd) + 2 + eig + 2 + (0 if form == "plain" else 4)
     return setup + prologue + passes * per_pass + final
 
 
@@ -694,8 +694,16 @@ def ours(args):
     sigma_ref = _sigma_ref(args.config, args.scale)
     res = {f: _measure_form(f, args, ds, torch, A, Ad, prm, stream, flush, barrier, world, local, sigma_ref)
            for f in forms}
-    # the chosen form: precision + the learned network when validation let it ship
-    chosen = next(res[f] for f in ("precision_learned", "precision", forms[0]) if f in res)
+    # the chosen form: precision + the learned network when validation let it
+    # ship, unless its runs miss the tolerance on this workload (true eps_PVE
+    # above tol after the halved-tolerance retries): then the plain rule ships
+    # here, as the learned form's fallback
+    def meets(r):
+        eps = r["accuracy"]["eps_pve"]
+        return eps is None or eps <= prm["tol"]
+
+    order = [f for f in ("precision_learned", "precision", forms[0]) if f in res]
+    chosen = next((res[f] for f in order if meets(res[f])), res[order[0]])
     pk = _peaks()
     line = {
         "metric": METRIC, "value": chosen["value"], "unit": "s", "n_gpus": world, "steps": args.steps,
@@ -715,6 +723,13 @@ def ours(args):
     # the chosen form once more with the serial schedule (options.overlap = 0):
     # what overlapping A Z with the eigensolve saves
     line["serial_schedule"] = _time_serial(args, ds, torch, chosen["form"], A, Ad, prm, stream, flush, barrier)
+    if "precision_learned" in res and chosen["form"] != "precision_learned":
+        lr = res["precision_learned"]
+        line["learned_form_missed_tol"] = {"value": lr["value"], "passes": lr["passes"], "status": lr["status"],
+                                           "accuracy": lr["accuracy"],
+                                           "note": "the learned stop ended the run before the true per-vector "
+                                                   "error met tol (even with tol halved twice); the plain rule "
+                                                   "ships on this workload"}
     if "precision_bf16" in res:
         pb = res["precision_bf16"]
         line["precision_bf16_gathers"] = {"value": pb["value"], "passes": pb["passes"], "status": pb["status"],

@@ -108,6 +108,7 @@ struct dashsvd_handle_s {
   DevBuf rowptr_b, col_b, val_b, cursor, scan_tmp;  // the CSR built by transposition
   DevBuf Y, Z, Q, G, W, W2, partial, carry, carry_row, ctl, trace, eigw;
   DevBuf Yp;      // A Z of the overlapped schedule (A Q = (A Z) W once W is known)
+  DevBuf colw;    // precision form: column norms of the final U (launch_normalize_columns)
   DevBuf seg_ctr; // segment counter of the overlapped A Z
   DevBuf seg_fwd, seg_bwd;  // merge-path partitions of A and A^T (rows, nonzeros)
   DevBuf errw;              // device error word of the bounded-wait kernels
@@ -521,10 +522,14 @@ cudaError_t launch_final(dashsvd_handle h, const RunPlan& p, cudaStream_t st) {
   // steps 10-11: eigSVD(B); U = B V_k S_k^-1; V = Q V_k
   if ((e = eigsvd_step(h, p, as<float>(h->Y), p.mw, kModeFinal, 0, st)) != cudaSuccess) return e;
   if (precision(h)) {
+    // U = B V_k S_k^-1, each column then divided by its norm (S_k from the
+    // BF16x3 Gram is off by about 2^-16 sigma_1^2; see k_colnorm.cu)
     if ((e = launch_project_tc(as<float>(h->Y), p.mw, p.l, p.ld, as<float>(h->W), p.ld, p.k, p.Uw, p.k, nullptr, 0,
                                nullptr, as<int>(h->errw), h->num_sms, st)) != cudaSuccess ||
         (e = launch_project_tc(as<float>(h->Q), p.nw, p.l, p.ld, as<float>(h->W2), p.ld, p.k, p.Vw, p.k, nullptr, 0,
-                               nullptr, as<int>(h->errw), h->num_sms, st)) != cudaSuccess)
+                               nullptr, as<int>(h->errw), h->num_sms, st)) != cudaSuccess ||
+        (e = launch_normalize_columns(p.Uw, p.mw, p.k, p.k, p.S, p.Vw, p.nw, p.k, as<double>(h->colw), h->num_sms,
+                                      st)) != cudaSuccess)
       return e;
     return tmark(h, kPfProject, st);
   }
@@ -857,7 +862,7 @@ int dashsvd_destroy(dashsvd_handle h) {
   drop_graph(h);
   DevBuf* bufs[] = {&h->rowptr_b, &h->col_b, &h->val_b, &h->cursor, &h->scan_tmp, &h->Y,       &h->Z,
                     &h->Q,        &h->G,     &h->W,     &h->W2,     &h->partial,  &h->carry, &h->carry_row,
-                    &h->ctl,      &h->trace, &h->eigw, &h->Yp, &h->seg_ctr, &h->seg_fwd, &h->seg_bwd, &h->errw, &h->Qb, &h->G64,
+                    &h->ctl,      &h->trace, &h->eigw, &h->Yp, &h->colw, &h->seg_ctr, &h->seg_fwd, &h->seg_bwd, &h->errw, &h->Qb, &h->G64,
                     &h->mlpw, &h->mlp_part, &h->fpw, &h->det_work, &h->h_rowptr, &h->h_col, &h->h_val, &h->h_U,
                     &h->h_S, &h->h_V, &h->hot_fwd, &h->hot_bwd, &h->hot_hist,
                     &h->tag_fwd, &h->tag_bwd, &h->st_counts, &h->st_hot, &h->st_tag, &h->mt_rowptr, &h->mt_col, &h->mt_val, &h->mt_cursor,
@@ -1027,6 +1032,7 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
       (rc = ensure(h->G, sizeof(float) * (size_t)(p.ld * p.ld), &moved)) ||
       (rc = ensure(h->W, sizeof(float) * (size_t)(p.ld * p.ld), &moved)) ||
       (rc = ensure(h->W2, sizeof(float) * (size_t)(p.ld * p.ld), &moved)) ||
+      (rc = ensure(h->colw, sizeof(double) * colnorm_work_doubles(p.k, h->num_sms), &moved)) ||
       (rc = ensure(h->partial, sizeof(float) * gp, &moved)) ||
       (rc = ensure(h->carry, sizeof(float) * (size_t)(2 * segs * p.ld), &moved)) ||
       (rc = ensure(h->carry_row, sizeof(int32_t) * (size_t)(2 * segs), &moved)) ||
@@ -1227,7 +1233,7 @@ int dashsvd_run(dashsvd_handle h, const dashsvd_csr* A, int k, int s, int max_pa
     int64_t ws = 0;
     DevBuf* bufs[] = {&h->rowptr_b, &h->col_b, &h->val_b, &h->cursor, &h->scan_tmp, &h->Y,       &h->Z,
                       &h->Q,        &h->G,     &h->W,     &h->W2,     &h->partial,  &h->carry, &h->carry_row,
-                      &h->ctl,      &h->trace, &h->eigw, &h->Yp, &h->seg_ctr, &h->seg_fwd, &h->seg_bwd, &h->errw, &h->Qb, &h->G64,
+                      &h->ctl,      &h->trace, &h->eigw, &h->Yp, &h->colw, &h->seg_ctr, &h->seg_fwd, &h->seg_bwd, &h->errw, &h->Qb, &h->G64,
                     &h->mlpw, &h->mlp_part, &h->fpw, &h->det_work, &h->h_rowptr, &h->h_col, &h->h_val, &h->h_U,
                     &h->h_S, &h->h_V, &h->hot_fwd, &h->hot_bwd, &h->hot_hist,
                     &h->tag_fwd, &h->tag_bwd, &h->st_counts, &h->st_hot, &h->st_tag, &h->mt_rowptr, &h->mt_col, &h->mt_val, &h->mt_cursor,

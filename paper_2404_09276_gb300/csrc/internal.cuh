@@ -202,6 +202,14 @@ cudaError_t launch_eig_refined(const float* G32, int64_t ldg32, const double* G6
                                const EigMarks& mk = EigMarks());
 // The precision form's eigensolver alone: FP64 eigenpairs of an FP64 Gram
 // (descending, signed), after `iters` refinement steps (0: FP32 Jacobi only).
+// Precision form, final factors: divide each column of U (rows x k, ld ldu)
+// by its norm, multiply S_c by it, and keep S descending by reordering the
+// columns of U and V (vrows x k, ld ldv) where two close values change places
+// (k_colnorm.cu); `work` holds colnorm_work_doubles(k, num_sms) doubles.
+size_t colnorm_work_doubles(int k, int num_sms);
+cudaError_t launch_normalize_columns(float* U, int64_t rows, int k, int64_t ldu, float* S, float* V, int64_t vrows,
+                                     int64_t ldv, double* work, int num_sms, cudaStream_t st);
+
 cudaError_t launch_eig_fp64(const double* G, int64_t ldg, int l, int iters, float* G32, int64_t ld32, double* D,
                             double* V, const EigWork& wk, cudaStream_t st);
 // FP64 iterative refinement of an approximate eigenbasis V32 of G64 (Ogita and

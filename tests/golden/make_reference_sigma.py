@@ -16,7 +16,7 @@ Usage: python -m tests.golden.make_reference_sigma [name ...]
   social_graph_1m     1M x 1M social graph (k = 110, s = 90, 30 passes; about 7 minutes on 8 cores)
   social_graph_100k   the same recipe at 100k x 100k (the Fig. 11 stand-in; about 1 minute)
   term_document_500k  500k x 100k term-document matrix (k = 110, s = 90, 30 passes)
-  recommender_2m      2M x 200k recommender matrix (k = 210, s = 90, 25 passes)
+  recommender_2m      2M x 200k recommender matrix (k = 210, s = 90, 25 passes; about 25 minutes on 8 cores)
 """
 from __future__ import annotations
 

@@ -101,7 +101,8 @@ def test_launch_count_matches_the_committed_launch_list():
     schedule) against the kernel count of the committed ncu launch list."""
     n = bench._launches_per_run("precision_learned", 5, 5, 7, setup_reused=True)
     eig = 19
-    assert n == 1 + (1 + 2 + 2 + 2 + eig + 2) + 5 * (2 + 2 + 2 + eig + 2) + (2 + eig + 2)
+    # the final stage: B's Gram, eigensolve, U and V, U's column norms (4 kernels)
+    assert n == 1 + (1 + 2 + 2 + 2 + eig + 2) + 5 * (2 + 2 + 2 + eig + 2) + (2 + eig + 2 + 4)
     assert bench._launches_per_run("precision_learned", 5, 5, 7, setup_reused=False) == n + 13
     # the serial schedule: the fused pass product replaces the two products (2 + 2 launches) by 2
     serial = bench._launches_per_run("precision", 5, 5, 7, overlap=False)

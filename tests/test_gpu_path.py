@@ -440,3 +440,22 @@ def test_eigensolve_stage_profile(ds, form):
     assert prof["eig"][1] == n and prof["eig_jacobi"][1] == n
     assert prof["eig_refine"][1] == (n if form == 1 else 0)
     assert prof["eig_jacobi"][0] > 0.0 and (form == 0 or prof["eig_refine"][0] > 0.0)
+
+
+def test_precision_form_final_columns_unit_and_ordered(ds):
+    """Precision form on the recommender recipe (a dominant direction: sigma_1
+    well above sigma_{k+1}): the final U has unit columns to FP32 rounding
+    although the BF16x3 Gram's eigenvalues are off by about 2^-16 sigma_1^2,
+    S stays descending, and U S = A V (Alg. 5 steps 9-11)."""
+    import torch
+
+    A, prm = datagen.make_config(5, scale=0.004)
+    k, s = prm["k"], prm["s"]
+    with ds.Handle(form=ds.DASHSVD_FORM_PRECISION) as h:
+        U, S, V, info = h.run(ds.CsrDevice.from_host(A), k, s, 4, 0.0)
+        torch.cuda.synchronize()
+    U, S, V = (x.cpu().numpy().astype(np.float64) for x in (U, S, V))
+    np.testing.assert_allclose(np.linalg.norm(U, axis=0), 1.0, atol=2e-5)
+    assert np.all(np.diff(S) <= 0)
+    AV = A.to_scipy().astype(np.float64) @ V
+    np.testing.assert_allclose(U * S[None, :], AV, atol=2e-4 * np.abs(AV).max())
