@@ -23,17 +23,48 @@ namespace {
 
 constexpr int kColThreads = 256;
 
-// part[b * k + c] = sum of squares of column c over row chunk b (FP64).
+// part[b * k + c] = sum of squares of column c over row chunk b (FP64). The
+// CTA's threads are g = 256 / k row lanes of k columns (g >= 1); each keeps
+// four independent sums (rows four lanes apart in flight at once), and the
+// lanes are added in shared memory.
 __global__ void __launch_bounds__(kColThreads) colsq_kernel(const float* __restrict__ U, int64_t rows, int k,
                                                              int64_t ldu, int64_t chunk, double* __restrict__ part) {
+  __shared__ double red[kColThreads];
+  const int g = kColThreads / k > 0 ? kColThreads / k : 1;
   const int64_t r0 = blockIdx.x * chunk, r1 = min(rows, r0 + chunk);
-  for (int c = threadIdx.x; c < k; c += blockDim.x) {
-    double acc = 0.0;
-    for (int64_t r = r0; r < r1; ++r) {
-      const double v = (double)U[r * ldu + c];
-      acc += v * v;
+  for (int c0 = 0; c0 < k; c0 += kColThreads) {  // k > 256: columns in slices of 256
+    const int c = c0 + (int)threadIdx.x % (g > 1 ? k : kColThreads);
+    const int lane = g > 1 ? (int)threadIdx.x / k : 0;
+    const bool on = (g > 1 ? lane < g : true) && c < k;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    if (on) {
+      int64_t r = r0 + lane;
+      for (; r + 3 * g < r1; r += 4 * g) {
+        const double v0 = U[r * ldu + c], v1 = U[(r + g) * ldu + c];
+        const double v2 = U[(r + 2 * g) * ldu + c], v3 = U[(r + 3 * g) * ldu + c];
+        a0 += v0 * v0;
+        a1 += v1 * v1;
+        a2 += v2 * v2;
+        a3 += v3 * v3;
+      }
+      for (; r < r1; r += g) {
+        const double v = U[r * ldu + c];
+        a0 += v * v;
+      }
     }
-    part[(int64_t)blockIdx.x * k + c] = acc;
+    red[threadIdx.x] = (a0 + a1) + (a2 + a3);
+    __syncthreads();
+    if (g > 1) {
+      if (threadIdx.x < k) {
+        double t = 0.0;
+        for (int q = 0; q < g; ++q) t += red[q * k + threadIdx.x];
+        part[(int64_t)blockIdx.x * k + threadIdx.x] = t;
+      }
+    } else if (c < k) {
+      part[(int64_t)blockIdx.x * k + c] = red[threadIdx.x];
+    }
+    __syncthreads();
+    if (g > 1) break;
   }
 }
 
@@ -104,7 +135,7 @@ size_t colnorm_work_doubles(int k, int num_sms) { return (size_t)(4 * num_sms + 
 cudaError_t launch_normalize_columns(float* U, int64_t rows, int k, int64_t ldu, float* S, float* V, int64_t vrows,
                                      int64_t ldv, double* work, int num_sms, cudaStream_t st) {
   if (rows <= 0 || k <= 0 || k > kMaxL) return cudaSuccess;
-  const int nb = (int)std::min<int64_t>(4 * (int64_t)num_sms, rows);
+  const int nb = (int)std::min<int64_t>((int64_t)num_sms, rows);
   const int64_t chunk = ds_ceil_div(rows, (int64_t)nb);
   const int nbu = (int)ds_ceil_div(rows, chunk);
   ColPlan pl;
