@@ -652,6 +652,21 @@ def _roofline(r, A, l, pk):
                 peak_source="latency-bound l x l eigensolver chain (no throughput roofline)")
 
 
+def _choose_form(res, forms, tol):
+    """The form the bench line reports: precision + the learned network when
+    validation let it ship, unless its runs miss the tolerance on this workload
+    (true eps_PVE above tol after the halved-tolerance retries): then the plain
+    shift rule ships here, as the learned form's fallback. A form without a
+    stored reference (eps_pve None) counts as meeting tol; when none meets it,
+    the first in that order is reported with its accuracy."""
+    def meets(r):
+        eps = r["accuracy"]["eps_pve"]
+        return eps is None or eps <= tol
+
+    order = [f for f in ("precision_learned", "precision", forms[0]) if f in res]
+    return next((res[f] for f in order if meets(res[f])), res[order[0]])
+
+
 def ours(args):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -694,16 +709,7 @@ def ours(args):
     sigma_ref = _sigma_ref(args.config, args.scale)
     res = {f: _measure_form(f, args, ds, torch, A, Ad, prm, stream, flush, barrier, world, local, sigma_ref)
            for f in forms}
-    # the chosen form: precision + the learned network when validation let it
-    # ship, unless its runs miss the tolerance on this workload (true eps_PVE
-    # above tol after the halved-tolerance retries): then the plain rule ships
-    # here, as the learned form's fallback
-    def meets(r):
-        eps = r["accuracy"]["eps_pve"]
-        return eps is None or eps <= prm["tol"]
-
-    order = [f for f in ("precision_learned", "precision", forms[0]) if f in res]
-    chosen = next((res[f] for f in order if meets(res[f])), res[order[0]])
+    chosen = _choose_form(res, forms, prm["tol"])
     pk = _peaks()
     line = {
         "metric": METRIC, "value": chosen["value"], "unit": "s", "n_gpus": world, "steps": args.steps,

@@ -1,6 +1,8 @@
 """Host-side pieces of the benchmark (no GPU): the clock sampler against a
-fake nvidia-smi, the roofline record, and the DRAM traffic looked up from the
-committed ncu summary only while the SpMM sources are unchanged."""
+fake nvidia-smi, the roofline record, the DRAM traffic looked up from the
+committed ncu summary only while the SpMM sources are unchanged, the launch
+count, the choice of the reported form and the accuracy record against the
+oracle (sigma errors, principal angles, spectral gap)."""
 import os
 import stat
 import sys
@@ -107,3 +109,74 @@ def test_launch_count_matches_the_committed_launch_list():
     # the serial schedule: the fused pass product replaces the two products (2 + 2 launches) by 2
     serial = bench._launches_per_run("precision", 5, 5, 7, overlap=False)
     assert bench._launches_per_run("precision", 5, 5, 7, fused=True, overlap=False) == serial - 5 * 2
+
+
+def _form(name, eps, value=1.0):
+    return {"form": name, "accuracy": {"eps_pve": eps}, "value": value}
+
+
+def test_chosen_form_falls_back_when_the_learned_stop_misses_tol():
+    """The learned form ships while its true eps_PVE meets tol; otherwise the
+    precision form with the plain shift rule; a form without a stored reference
+    counts as meeting tol; when none meets tol, the learned form is reported."""
+    forms = ["plain", "precision", "precision_learned"]
+    res = {"plain": _form("plain", 1.1e-3), "precision": _form("precision", 4e-3),
+           "precision_learned": _form("precision_learned", 2.8e-3)}
+    assert bench._choose_form(res, forms, 1e-2)["form"] == "precision_learned"
+    res["precision_learned"] = _form("precision_learned", 1.97e-2)
+    assert bench._choose_form(res, forms, 1e-2)["form"] == "precision"
+    res["precision"] = _form("precision", 1.2e-2)
+    assert bench._choose_form(res, forms, 1e-2)["form"] == "plain"
+    res["plain"] = _form("plain", 1.5e-2)
+    assert bench._choose_form(res, forms, 1e-2)["form"] == "precision_learned"
+    res["precision"] = _form("precision", None)
+    assert bench._choose_form(res, forms, 1e-2)["form"] == "precision"
+    # one form asked for: that form, whatever its accuracy
+    assert bench._choose_form({"plain": _form("plain", 0.5)}, ["plain"], 1e-2)["form"] == "plain"
+    # the boundary: eps == tol meets it
+    assert bench._choose_form({"precision_learned": _form("precision_learned", 1e-2),
+                               "precision": _form("precision", 1e-3)},
+                              ["precision", "precision_learned"], 1e-2)["form"] == "precision_learned"
+
+
+@pytest.mark.parametrize("theta", [0.0, 1e-3, 0.4, 1.2])
+def test_subspace_angle_of_a_rotated_plane(theta):
+    """span(e1, e2) against span(e1, cos t e2 + sin t e3), each given through a
+    non-orthogonal basis: the largest principal angle is t."""
+    import numpy as np
+
+    n = 7
+    X = np.zeros((n, 2))
+    X[0, 0] = X[1, 1] = 1.0
+    Y = np.zeros((n, 2))
+    Y[0, 0] = 1.0
+    Y[1, 1], Y[2, 1] = np.cos(theta), np.sin(theta)
+    mix = np.array([[2.0, 1.0], [0.5, 3.0]])
+    assert abs(bench._subspace_angle(X @ mix, Y @ mix.T) - theta) < 1e-7
+
+
+def test_vs_oracle_errors_and_gap():
+    """Relative sigma errors against the oracle's sigma, the principal angles of
+    U_k and V_k, and the gap from the oracle's last pass (sqrt(Shat + alpha))."""
+    import numpy as np
+
+    from oracle.dashsvd_ref import PassRecord, Result
+
+    rng = np.random.default_rng(5)
+    m, n, k = 40, 30, 3
+    U = np.linalg.qr(rng.standard_normal((m, k)))[0]
+    V = np.linalg.qr(rng.standard_normal((n, k)))[0]
+    S = np.array([4.0, 2.0, 1.0])
+    last = PassRecord(3, 0.5, np.array([15.5, 3.5, 0.5, 0.14]), 1e-3, True, 0.5)
+    ref = Result(U, S, V, 3, True, 0.5, False, [last])
+    out = bench._vs_oracle((U, S * np.array([1.0, 1.01, 0.98]), V), ref, k)
+    assert abs(out["sigma_rel_max"] - 0.02) < 1e-12
+    assert abs(out["sigma_rel_median"] - 0.01) < 1e-12
+    assert out["angle_U_rad"] < 1e-7 and out["angle_V_rad"] < 1e-7
+    # estimates sqrt(16, 4, 1, 0.64) = (4, 2, 1, 0.8): gap_3 = (1 - 0.8) / 1
+    assert abs(out["gap_k"] - 0.2) < 1e-12 and out["oracle_passes"] == 3
+    # a column of U turned towards the complement by 0.3 rad
+    W = np.linalg.qr(np.hstack([U, rng.standard_normal((m, 1))]))[0][:, k]
+    U2 = U.copy()
+    U2[:, 2] = np.cos(0.3) * U[:, 2] + np.sin(0.3) * W
+    assert abs(bench._vs_oracle((U2, S, V), ref, k)["angle_U_rad"] - 0.3) < 1e-7
