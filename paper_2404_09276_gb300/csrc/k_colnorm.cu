@@ -23,10 +23,13 @@ namespace {
 
 constexpr int kColThreads = 256;
 
-// part[b * k + c] = sum of squares of column c over row chunk b (FP64). The
-// CTA's threads are g = 256 / k row lanes of k columns (g >= 1); each keeps
-// four independent sums (rows four lanes apart in flight at once), and the
-// lanes are added in shared memory.
+// part[b * k + c] = sum of squares of column c over row chunk b. The CTA's
+// threads are g = 256 / k row lanes of k columns (g >= 1). A lane loads eight
+// of its rows at once (rows g apart), adds their squares in FP32 (at most
+// eight roundings, a relative error below 2^-21 of that group's sum) and the
+// group's sum to an FP64 total: one conversion and one FP64 add per eight
+// elements, since FP64 arithmetic is the slow pipe on this part. The lanes are
+// added in shared memory in a fixed order, so the sums are reproducible.
 __global__ void __launch_bounds__(kColThreads) colsq_kernel(const float* __restrict__ U, int64_t rows, int k,
                                                              int64_t ldu, int64_t chunk, double* __restrict__ part) {
   __shared__ double red[kColThreads];
@@ -36,23 +39,24 @@ __global__ void __launch_bounds__(kColThreads) colsq_kernel(const float* __restr
     const int c = c0 + (int)threadIdx.x % (g > 1 ? k : kColThreads);
     const int lane = g > 1 ? (int)threadIdx.x / k : 0;
     const bool on = (g > 1 ? lane < g : true) && c < k;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    double acc = 0.0;
     if (on) {
       int64_t r = r0 + lane;
-      for (; r + 3 * g < r1; r += 4 * g) {
-        const double v0 = U[r * ldu + c], v1 = U[(r + g) * ldu + c];
-        const double v2 = U[(r + 2 * g) * ldu + c], v3 = U[(r + 3 * g) * ldu + c];
-        a0 += v0 * v0;
-        a1 += v1 * v1;
-        a2 += v2 * v2;
-        a3 += v3 * v3;
+      for (; r + 7 * g < r1; r += 8 * g) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = U[(r + u * g) * ldu + c];
+        float t = v[0] * v[0];
+#pragma unroll
+        for (int u = 1; u < 8; ++u) t = fmaf(v[u], v[u], t);
+        acc += (double)t;
       }
       for (; r < r1; r += g) {
-        const double v = U[r * ldu + c];
-        a0 += v * v;
+        const double x = U[r * ldu + c];
+        acc += x * x;
       }
     }
-    red[threadIdx.x] = (a0 + a1) + (a2 + a3);
+    red[threadIdx.x] = acc;
     __syncthreads();
     if (g > 1) {
       if (threadIdx.x < k) {
@@ -75,14 +79,27 @@ struct ColPlan {
   int* pos;    // k new positions
   int* flag;
 };
-__global__ void __launch_bounds__(kColThreads) colnorm_kernel(const double* __restrict__ part, int nb, int k,
-                                                               float* __restrict__ S, ColPlan pl) {
+constexpr int kPlanThreads = 1024;
+__global__ void __launch_bounds__(kPlanThreads) colnorm_kernel(const double* __restrict__ part, int nb, int k,
+                                                                float* __restrict__ S, ColPlan pl) {
   __shared__ double snew[kMaxL];
+  __shared__ double lanes[kPlanThreads];
   __shared__ int moved;
   if (threadIdx.x == 0) moved = 0;
+  // the nb partial sums of column c: gq = 1024 / k lanes (k <= 256, so gq >= 4),
+  // lane q taking chunks q, q + gq, ...; the lanes are added in a fixed order
+  const int gq = (int)blockDim.x / k;
+  {
+    const int c = (int)threadIdx.x % k, q = (int)threadIdx.x / k;
+    double s = 0.0;
+    if (q < gq)
+      for (int b = q; b < nb; b += gq) s += part[(int64_t)b * k + c];
+    lanes[threadIdx.x] = s;
+  }
+  __syncthreads();
   for (int c = threadIdx.x; c < k; c += blockDim.x) {
     double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += part[(int64_t)b * k + c];
+    for (int q = 0; q < gq; ++q) s += lanes[q * k + c];
     const double nrm = sqrt(s);
     pl.fac[c] = nrm > 0.0 ? (float)(1.0 / nrm) : 0.f;
     snew[c] = (double)S[c] * nrm;
@@ -135,7 +152,7 @@ size_t colnorm_work_doubles(int k, int num_sms) { return (size_t)(4 * num_sms + 
 cudaError_t launch_normalize_columns(float* U, int64_t rows, int k, int64_t ldu, float* S, float* V, int64_t vrows,
                                      int64_t ldv, double* work, int num_sms, cudaStream_t st) {
   if (rows <= 0 || k <= 0 || k > kMaxL) return cudaSuccess;
-  const int nb = (int)std::min<int64_t>((int64_t)num_sms, rows);
+  const int nb = (int)std::min<int64_t>(4 * (int64_t)num_sms, rows);
   const int64_t chunk = ds_ceil_div(rows, (int64_t)nb);
   const int nbu = (int)ds_ceil_div(rows, chunk);
   ColPlan pl;
@@ -145,12 +162,12 @@ cudaError_t launch_normalize_columns(float* U, int64_t rows, int k, int64_t ldu,
   colsq_kernel<<<(unsigned)nbu, kColThreads, 0, st>>>(U, rows, k, ldu, chunk, work);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  colnorm_kernel<<<1, kColThreads, 0, st>>>(work, nbu, k, S, pl);
+  colnorm_kernel<<<1, kPlanThreads, 0, st>>>(work, nbu, k, S, pl);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  colapply_kernel<<<(unsigned)(4 * num_sms), kRowWarps * 32, 0, st>>>(U, rows, k, ldu, pl.fac, pl.pos, pl.flag, 0);
+  colapply_kernel<<<(unsigned)(8 * num_sms), kRowWarps * 32, 0, st>>>(U, rows, k, ldu, pl.fac, pl.pos, pl.flag, 0);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (V && vrows > 0)
-    colapply_kernel<<<(unsigned)(4 * num_sms), kRowWarps * 32, 0, st>>>(V, vrows, k, ldv, nullptr, pl.pos, pl.flag, 1);
+    colapply_kernel<<<(unsigned)(8 * num_sms), kRowWarps * 32, 0, st>>>(V, vrows, k, ldv, nullptr, pl.pos, pl.flag, 1);
   return cudaGetLastError();
 }
 
